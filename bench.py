@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Gridded + degridded visibilities per second for W-projection imaging on GB300.
+
+One step is one pass of the whole hot path over the full W-projection workload (351 baselines x
+2000 integrations x 64 channels 2-4 GHz x 4 pols = 179.7M visibilities, 64 w-planes with CF
+supports 8-64, oversampling 20, 4096 x 4096 x 4 grid):
+
+    plan_update          per-sample FP64 index, w-plane, CF, pixel/offset; tiled counting sort
+    grid_visibilities    G (Eq. IMAGE-MOD) into a zeroed grid, FP64 sum of weights
+    grid_normalize       taper / weight correction of the gridded plane (after the caller's FFT)
+    degrid_visibilities  D (Eq. ME-MOD-GRIDDED) from a model grid
+
+value = (gridded + degridded visibilities) / step time, summed over ranks.  The inputs (1.44 GB of
+visibilities, 0.72 GB of weights, a 0.54 GB model grid) are larger than the 129 MB L2, so no
+extra flush is needed between steps.  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+
+Multi-GPU (torchrun): every rank takes its own slice of integrations of a track N times as long
+(the same per-rank size, weak scaling) and the gridded planes are summed with one all-reduce per
+step, which is the accumulation of Eq. ResIm over time.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+CONFIG = "wproj"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-int", type=int, default=None, help="integrations per rank (default: the full 2000)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-every", type=int, default=40, help="oracle sample: every k-th integration")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def rank_workload(world: int, rank: int, n_int: int, device: str, with_vis=True):
+    """Rank `rank`'s slice of a track of world * n_int integrations (time-major rows)."""
+    full = synth.make_workload(CONFIG, with_vis=False, n_int=n_int * world)
+    r0, r1 = rank * n_int * full.n_bl, (rank + 1) * n_int * full.n_bl
+    wl = dataclasses.replace(full, uvw_m=full.uvw_m[r0:r1].copy(), pa_rad=full.pa_rad[r0:r1].copy(),
+                             pa_bin=full.pa_bin[r0:r1].copy(), n_int=n_int)
+    if with_vis:
+        synth.fill_visibilities(wl, device=device)
+    return wl
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_alu_peak_tflops(sms: int, mhz: float) -> float:
+    """Non-tensor FP32 FMA peak: SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def run_cpu_baseline(wl, every: int):
+    """Time the FP64 oracle (G and D, OpenMP over all cores) on every `every`-th integration."""
+    from oracle import cf as ocf
+    from oracle import index as oindex
+    from oracle import ops as oops
+    rows = np.concatenate([np.arange(t * wl.n_bl, (t + 1) * wl.n_bl) for t in range(0, wl.n_int, every)])
+    op = ocf.CFParams(grid_n=wl.grid_n, cell_rad=wl.cell_rad, oversampling=wl.oversampling,
+                      ps_support=wl.ps_support, use_w=wl.use_w, n_wplanes=wl.n_wplanes,
+                      w_max_lambda=wl.w_max_lambda, max_support=wl.max_support)
+    idx = oindex.sample_index(op, wl.uvw_m[rows], wl.freq_hz)
+    tabs = ocf.cf_set(op, which=set(np.unique(idx.cf[idx.valid]).tolist()))
+    buf, off, _ = ocf.flatten_cf_set(op, tabs)
+    vis = np.asarray(wl.vis)[rows].reshape(-1, wl.n_pol)
+    wt = np.asarray(wl.weight)[rows].reshape(-1, wl.n_pol)
+    threads = oops.default_threads()
+    t0 = time.perf_counter()
+    g, _ = oops.grid(idx, buf, off, wl.oversampling, wl.grid_n, vis, wt, nthreads=threads)
+    t1 = time.perf_counter()
+    oops.degrid(idx, buf, off, wl.oversampling, g, nthreads=threads)
+    t2 = time.perf_counter()
+    n_vis = int(idx.valid.size) * wl.n_pol
+    return {"value": 2 * n_vis / (t2 - t0), "unit": "visibilities/s", "cores": threads, "kind": "oracle",
+            "sample": f"every {every}th integration: {len(rows)} rows x {wl.n_chan} channels x {wl.n_pol} pols "
+                      f"= {n_vis} visibilities, gridded then degridded (grid {t1 - t0:.2f} s, degrid {t2 - t1:.2f} s)",
+            "seconds": t2 - t0}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = rank_workload(1, 0, args.n_int or synth.CONFIGS[CONFIG]["n_int"], "cpu")
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = run_cpu_baseline(wl, args.cpu_sample_every)
+        if i >= args.warmup:
+            times.append(info["seconds"])
+    per_step = statistics.mean(times)
+    value = info["value"] * info["seconds"] / per_step
+    line = {"impl": "reference", "metric": "gridded+degridded visibilities/s", "value": value,
+            "unit": "visibilities/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "W-projection, VLA A-array-like, 351 bl x 2000 int x 64 ch x 4 pol, "
+                                   "64 w-planes, supports 8-64, OS 20, 4096^2 x 4 grid (bounded sample per step)"},
+            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": value,
+                             "unit": "visibilities/s"},
+            "e2e": {"value": value, "unit": "visibilities/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2508_17187_gb300 as awg
+    from paper_2508_17187_gb300 import _lib
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    n_int = args.n_int or synth.CONFIGS[CONFIG]["n_int"]
+    wl = rank_workload(world, rank, n_int, dev)
+    N, P = wl.grid_n, wl.n_pol
+    R, C = wl.n_rows, wl.n_chan
+    lib = _lib.load()
+
+    cf = awg.cf_set_create(grid_n=N, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support,
+                           use_w=True, n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda,
+                           max_support=wl.max_support)
+    uvw = torch.as_tensor(wl.uvw_m, device=dev)
+    freq = torch.as_tensor(wl.freq_hz, device=dev)
+    vis, wt = wl.vis, wl.weight
+    plan = awg.plan_create(cf, uvw, freq)
+    kept, dropped, sum_taps = plan.stats()
+    grid = torch.zeros((N, N, P), dtype=torch.complex64, device=dev)
+    sumwt = torch.zeros(P, dtype=torch.float64, device=dev)
+    # model grid for the degridding half: F of a taper-corrected model image (one cuFFT call here,
+    # outside the timed region; the FFT is not part of the library)
+    model = torch.zeros((N, N, P), dtype=torch.complex64, device=dev)
+    ii = ((torch.as_tensor(wl.sky_m) / wl.cell_rad).round().long() + N // 2).clamp(0, N - 1)
+    jj = ((torch.as_tensor(wl.sky_l) / wl.cell_rad).round().long() + N // 2).clamp(0, N - 1)
+    for p in (0, P - 1):
+        model[ii.to(dev), jj.to(dev), p] = torch.as_tensor(wl.sky_flux, dtype=torch.complex64, device=dev)
+    awg.grid_normalize(cf, model, None, direction=1)
+    mgrid = torch.fft.fftshift(torch.fft.fft2(torch.fft.ifftshift(model, dim=(0, 1)), dim=(0, 1)), dim=(0, 1))
+    mgrid = mgrid.contiguous()
+    del model
+    vis_out = torch.empty_like(vis)
+    stream = torch.cuda.current_stream()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    op_ms = {"plan": [], "grid": [], "normalize": [], "degrid": []}
+
+    def step(record=False):
+        if record:
+            ev[0].record(stream)
+        plan.update(uvw, freq)
+        if record:
+            ev[1].record(stream)
+        grid.zero_()
+        sumwt.zero_()
+        awg.grid_visibilities(cf, plan, vis, wt, grid, sumwt)
+        if record:
+            ev[2].record(stream)
+        if world > 1:
+            dist.all_reduce(torch.view_as_real(grid))
+            dist.all_reduce(sumwt)
+        awg.grid_normalize(cf, grid, sumwt, direction=0)
+        if record:
+            ev[3].record(stream)
+        awg.degrid_visibilities(cf, plan, mgrid, vis_out)
+        if record:
+            ev[4].record(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+    # per-operator timing pass (events on the launching stream), outside the headline timing
+    for _ in range(args.steps):
+        step(record=True)
+        torch.cuda.synchronize()
+        op_ms["plan"].append(ev[0].elapsed_time(ev[1]))
+        op_ms["grid"].append(ev[1].elapsed_time(ev[2]))
+        op_ms["normalize"].append(ev[2].elapsed_time(ev[3]))
+        op_ms["degrid"].append(ev[3].elapsed_time(ev[4]))
+    barrier()
+    launches0 = lib.awg_kernel_launches()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step()
+        t_end.record(stream)
+        barrier()
+    launches = lib.awg_kernel_launches() - launches0
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    vis_per_step = 2 * R * C * P * world
+    value = vis_per_step / (ms / 1e3)
+
+    # end to end through the public API with host buffers: H2D of the step's inputs from pinned
+    # memory, the step, D2H of its results (degridded visibilities, gridded plane, weight sums)
+    e2e = None
+    if not args.no_e2e:
+        h_vis = vis.cpu().pin_memory()
+        h_wt = wt.cpu().pin_memory()
+        h_uvw = uvw.cpu().pin_memory()
+        h_freq = freq.cpu().pin_memory()
+        h_out = torch.empty(vis_out.shape, dtype=vis_out.dtype).pin_memory()
+        h_grid = torch.empty(grid.shape, dtype=grid.dtype).pin_memory()
+        h_sw = torch.empty(sumwt.shape, dtype=sumwt.dtype).pin_memory()
+
+        def e2e_step():
+            vis.copy_(h_vis, non_blocking=True)
+            wt.copy_(h_wt, non_blocking=True)
+            uvw.copy_(h_uvw, non_blocking=True)
+            freq.copy_(h_freq, non_blocking=True)
+            step()
+            h_out.copy_(vis_out, non_blocking=True)
+            h_grid.copy_(grid, non_blocking=True)
+            h_sw.copy_(sumwt, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        e_ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        h2d = vis.numel() * 8 + wt.numel() * 4 + uvw.numel() * 8 + freq.numel() * 8
+        d2h = vis_out.numel() * 8 + grid.numel() * 8 + sumwt.numel() * 8
+        e2e = {"value": vis_per_step / (e_ms / 1e3), "unit": "visibilities/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    cs = clocks.summary()
+    max_mhz = cs["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    peak_tf = fp32_alu_peak_tflops(sms, max_mhz)
+    flop = 8.0 * P * sum_taps          # one complex MAC = 4 FP32 FMA = 8 FLOP, per pol and tap
+    g_ms = statistics.mean(op_ms["grid"])
+    d_ms = statistics.mean(op_ms["degrid"])
+    dom, dom_ms = ("grid", g_ms) if g_ms >= d_ms else ("degrid", d_ms)
+    achieved = flop / (dom_ms / 1e3) / 1e12
+    line = {
+        "metric": "gridded+degridded visibilities/s", "value": value, "unit": "visibilities/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic VLA A-array-like uvw, 200 point sources + 1 mJy noise, natural weights",
+        "config": {"workload": "W-projection: 351 baselines x 2000 integrations x 64 channels (2-4 GHz) x 4 pols "
+                               "per rank, 64 w-planes, CF supports 8-64, oversampling 20, 4096x4096x4 c64 grid",
+                   "visibilities_per_step": vis_per_step, "kept_samples": kept, "dropped_samples": dropped,
+                   "mean_taps": sum_taps / max(kept, 1), "l2": "inputs larger than L2 (2.7 GB per step)",
+                   "parallelism": f"dp{world}" if world > 1 else "single GPU"},
+        "cf_gmac_per_s": 2 * P * sum_taps * world / (ms / 1e3) / 1e9,
+        "ops_ms": {k: statistics.mean(v) for k, v in op_ms.items()},
+        "roofline": {"bound": "alu", "kernel": f"{dom}_visibilities (all support classes)", "achieved": achieved,
+                     "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": None,
+                     "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)"},
+        "clocks": {k: cs[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        host_wl = dataclasses.replace(wl, vis=vis.cpu().numpy(), weight=wt.cpu().numpy())
+        cb = run_cpu_baseline(host_wl, args.cpu_sample_every)
+        cb.pop("seconds")
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * awgrid.h - C ABI of the GB300 (sm_103a) AW-projection gridding / degridding library.
+ *
+ * The library implements the convolutional resampling operators of the imaging
+ * measurement equation (arXiv 2508.17187, Sec. 2):
+ *   degridding  D(c_ij):  V_ij = D(c_ij) F[I]                      (Eq. ME-MOD-GRIDDED)
+ *   gridding    G(c_ij):  I    = F^dagger sum_ij G(c_ij) w_ij V_ij  (Eq. IMAGE-MOD)
+ * with the per-visibility kernel c_ij = CF_ij(nu, w, t) and the optional phase-gradient
+ * term of Eq. CIJ (Sec. 6), the CF being one of the Tab. AWP-CFSETUP configurations
+ * (PS, PS*W, PS*A, PS*A*W).  G is the exact adjoint of D (the residual image of Eq. ResIm
+ * is the chi^2 gradient of Eq. ImChisq only if it is).  The Fourier transform F itself is
+ * not part of this library; the caller runs it (cuFFT / torch.fft) between the calls.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers documented "device" point to memory of the current CUDA device; "host"
+ *    pointers to ordinary host memory.  The caller owns every buffer it passes; the
+ *    library owns the CF set and the plan it creates until the matching *_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Compute calls are asynchronous and stream-ordered: argument checks run on the host
+ *    before any launch and return a status synchronously; a fault in a kernel surfaces as
+ *    AWG_ERR_CUDA from a later call or from the caller's own synchronisation.
+ *  - Complex values are interleaved (re, im) float32 ("c64") unless stated otherwise.
+ *  - Layouts: uvw [R][3] float64 metres; freq [C] float64 Hz; visibilities and weights
+ *    [R][C][P] (row-major, pols innermost, P in {1, 2, 4}); grid and image [N][N][P] c64
+ *    (row = v, column = u; the uv origin and the image centre are pixel (N/2, N/2)).
+ *  - On a non-OK status nothing is launched and awg_last_error() describes the reason.
+ *  - Calls are thread-safe for distinct objects; one object must not be used from two
+ *    host threads at once.
+ */
+#ifndef AWGRID_H
+#define AWGRID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct awg_cf_set_s* awg_cf_set; /* device-resident CF cache (PreCompute, Sec. 4.1 / 6) */
+typedef struct awg_plan_s* awg_plan;     /* sorted, tiled sample index (PreSolvePrep, Sec. 5.2) */
+
+typedef enum {
+  AWG_OK = 0,
+  AWG_ERR_INVALID_ARG = 1, /* a NULL, out-of-range or inconsistent argument */
+  AWG_ERR_UNSUPPORTED = 2, /* a valid request this build does not handle (e.g. support > 64) */
+  AWG_ERR_OOM = 3,         /* a device or host allocation failed; nothing leaked */
+  AWG_ERR_CUDA = 4,        /* a CUDA runtime error (launch failure or an earlier fault) */
+  AWG_ERR_TIMEOUT = 5      /* a bounded device wait gave up (reported by a status word) */
+} awg_status;
+
+/* CF storage type. */
+enum { AWG_CF_FP32 = 0, AWG_CF_BF16 = 1 };
+
+/* grid_visibilities flags. */
+enum {
+  AWG_GRID_KAHAN = 1, /* compensated flush: rounding error of every flush add goes to grid_lo */
+  AWG_GRID_FP64 = 2   /* grid (and grid_lo unused) is complex128 [N][N][P]; flush adds in FP64 */
+};
+
+/*
+ * Parameters of a CF set (Tab. AWP-CFSETUP switches plus the imaging geometry).
+ * CF index: cf = (pa_bin * n_subbands + subband) * n_signed + ks, with n_signed = 2 n_wplanes - 1
+ * when use_w, else 1; signed w-plane ks = n_wplanes - 1 + k (w >= 0) or n_wplanes - 1 - k (w < 0),
+ * planes linear in |w|: w_k = k w_max / (n_wplanes - 1).
+ * CF of S taps: c(du, dv) = (1/M^2) sum_{i,j<M} screen(x_i, y_j) exp(-2 pi i (du (i - M/2) + dv (j - M/2)) / M),
+ * screen = T(x) T(y) [A(l, m; nu_sb, PA)] exp(-2 pi i w_k (sqrt(1 - l^2 - m^2) - 1)), x_i = (i - M/2) N / M
+ * image pixels, l = x cell, T(x) = psi_0(pi W / 2, 2x/N) / psi_0(pi W / 2, 0) (zeroth prolate spheroidal
+ * function, W = ps_support), M = the smallest power of two >= max(16, 2S).  Tap t of oversampling
+ * offset o sits at du = S/2 - t - o/OS; a table is stored offset-major [OS+1][OS+1][S][S] c64.
+ * Support schedule: without W every CF has max_support taps; with W, plane k has
+ * S_k = min(max_support, 8 ceil((8 + (max_support - 8) sqrt(k / (n_wplanes - 1))) / 8)), at least ps_support.
+ * A-term (synthetic; the paper gives none): Airy power pattern (2 J1(z)/z)^2, z = pi D rho nu / c,
+ * rho^2 = (l'/(1+eps))^2 + (m'/(1-eps))^2, (l', m') = (l, m) rotated by the bin's parallactic angle.
+ */
+typedef struct {
+  int grid_n;                       /* N: grid side in pixels, even, 16..65536 */
+  double cell_rad;                  /* image pixel size (rad); uv pixel du = 1 / (N cell) */
+  int oversampling;                 /* OS >= 1 */
+  int ps_support;                   /* W: PS kernel width in pixels (e.g. 7) */
+  int use_ps;                       /* 1: PS term on (T as above); 0: T = 1 */
+  int use_w;                        /* 1: W-projection planes */
+  int n_wplanes;                    /* >= 2 when use_w */
+  double w_max_lambda;              /* > 0 when use_w */
+  int use_a;                        /* 1: A-term on */
+  int n_pa_bins;                    /* >= 1 */
+  const double* pa_bin_centers_rad; /* host [n_pa_bins] (read when use_a) */
+  int n_subbands;                   /* >= 1 */
+  const double* subband_freq_hz;    /* host [n_subbands] (read when use_a) */
+  int max_support;                  /* 1..64 taps */
+  double dish_diameter_m;           /* A-term aperture (e.g. 25) */
+  double ellipticity;               /* A-term distortion (e.g. 0.05) */
+  int cf_dtype;                     /* AWG_CF_FP32 or AWG_CF_BF16 */
+} awg_cf_params;
+
+/*
+ * Build the CF set on the host in FP64 (PreCompute, Sec. 4.1 and Sec. 6 CFCache) and upload it,
+ * rounded to cf_dtype, to the current device.  Negative-w planes are the conjugate point
+ * reflections of the positive ones (screen(-w) = conj(screen(w))).  Blocking: returns once the
+ * tables are resident.  Errors: INVALID_ARG (bad params), UNSUPPORTED (max_support > 64), OOM.
+ */
+awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* out);
+
+/*
+ * Same, with caller-supplied tables instead of the built ones (e.g. a support-1 delta kernel).
+ * supports: host [n_cf] taps per CF (1..64); table: host c64, all CFs concatenated in CF-index
+ * order, each [OS+1][OS+1][S][S].  Only grid_n, oversampling, use_w, n_wplanes, w_max_lambda,
+ * n_pa_bins, n_subbands and cf_dtype of params are read.
+ */
+awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* supports,
+                                    const float* table, void* stream, awg_cf_set* out);
+
+awg_status cf_set_destroy(awg_cf_set cf);
+
+/* Number of CFs and total number of complex values held. */
+awg_status cf_set_info(awg_cf_set cf, int32_t* n_cf, int64_t* n_values);
+
+/* Host copy of the support of every CF: supports_out host [n_cf]. */
+awg_status cf_set_get_supports(awg_cf_set cf, int32_t* supports_out);
+
+/* Host copy of one CF table as c64 [OS+1][OS+1][S][S] (BF16 tables are widened). Blocking. */
+awg_status cf_set_copy_table(awg_cf_set cf, int32_t cf_index, float* table_out);
+
+/*
+ * Create a plan: per-visibility index and the tiled ordering of all R*C samples
+ * (PreSolvePrep re-ordering, Sec. 5.2 and Sec. 6.1).  For every (row r, channel c), in FP64 with
+ * no fused multiply-add: u_l = u_m (nu_c / c_light); x = u_l (N cell) + N/2 (same for v, y);
+ * w-plane k = floor(|w_l| (n_w - 1) / w_max + 1/2) (k > n_w - 1 drops the sample); cf as above;
+ * hx = x - S/2, first tap p0x = floor(hx) + 1, offset ox = floor((p0x - hx) OS + 1/2) in [0, OS].
+ * A sample is kept iff -1 <= hx < N - S and -1 <= hy < N - S; others are dropped and counted.
+ * uvw_m: device [R][3] f64; freq_hz: device [C] f64; pa_bin: device int32 [R] (needed when
+ * n_pa_bins > 1, else may be NULL); chan_subband: device int32 [C] (needed when n_subbands > 1);
+ * phase_shift: host f64 [2] (dl, dm) of the image centre from the phase centre, or NULL for none:
+ * G multiplies w V by exp(+2 pi i (u dl + v dm + w dn)), dn = sqrt(1 - dl^2 - dm^2) - 1, D by its
+ * conjugate (the phase term of Eq. CIJ).  The plan allocates device memory (about 44 bytes per
+ * sample) and keeps pointers to no caller buffer.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+awg_status plan_create(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const double* freq_hz,
+                       int32_t n_chan, const int32_t* pa_bin, const int32_t* chan_subband,
+                       const double* phase_shift, void* stream, awg_plan* out);
+
+/*
+ * Recompute the plan for new uvw / frequency / bin data of the same R and C (no allocation;
+ * stream-ordered; capturable in a CUDA graph).
+ */
+awg_status plan_update(awg_plan plan, const double* uvw_m, const double* freq_hz, const int32_t* pa_bin,
+                       const int32_t* chan_subband, void* stream);
+
+awg_status plan_destroy(awg_plan plan);
+
+/*
+ * Plan statistics (synchronises the plan's last stream): kept and dropped samples and
+ * sum over kept samples of S^2 (complex multiply-accumulates per pol for one G or D pass).
+ */
+awg_status plan_stats(awg_plan plan, int64_t* n_kept, int64_t* n_dropped, int64_t* sum_taps);
+
+/*
+ * Gridding G (Eq. IMAGE-MOD): for every kept sample s and pol p,
+ *   grid[p0y+ty][p0x+tx][p] += conj(CF_cf[oy][ox][ty][tx]) * weight[s][p] * vis[s][p] (* phasor),
+ * accumulated (+=) into the caller's grid; sumwt[p] += sum of weight[s][p] over kept samples (FP64).
+ * vis: device c64 [R][C][P]; weight: device f32 [R][C][P] (0 = flagged); grid: device c64
+ * [N][N][P] (complex128 with AWG_GRID_FP64); grid_lo: device c64 [N][N][P] compensation grid with
+ * AWG_GRID_KAHAN (the true sum is grid + grid_lo), else NULL; sumwt: device f64 [P].
+ * Accumulation is FP32 in registers and shared memory with one atomic flush per tile pixel;
+ * the summation order is not fixed, so results agree with an FP64 sum to FP32 rounding.
+ * Errors: INVALID_ARG (NULL pointer, P not in {1,2,4}, bad flags), CUDA.
+ */
+awg_status grid_visibilities(awg_cf_set cf, awg_plan plan, const void* vis, const float* weight,
+                             int32_t n_pol, void* grid, void* grid_lo, double* sumwt, int32_t flags,
+                             void* stream);
+
+/*
+ * Degridding D (Eq. ME-MOD-GRIDDED, Eq. VMod): for every sample s and pol p,
+ *   vis_out[s][p] = sum_{ty,tx} CF_cf[oy][ox][ty][tx] * grid[p0y+ty][p0x+tx][p] (* conj(phasor)),
+ * overwritten; dropped samples get 0.  grid: device c64 [N][N][P]; vis_out: device c64 [R][C][P].
+ * D is the adjoint of G with unit weights: <G V, X> = <V, D X>.  Errors: INVALID_ARG, CUDA.
+ */
+awg_status degrid_visibilities(awg_cf_set cf, awg_plan plan, const void* grid, void* vis_out,
+                               int32_t n_pol, int32_t flags, void* stream);
+
+/*
+ * Taper correction around the caller's FFT (Eq. IMAGE-MOD, PS term of Tab. AWP-CFSETUP):
+ * direction 0 (after F^dagger of a gridded grid): image[y][x][p] /= (sumwt[p] T(x - N/2) T(y - N/2));
+ * direction 1 (a model image before F and degridding): image[y][x][p] /= (T(x - N/2) T(y - N/2)).
+ * image: device c64 [N][N][P], in place; sumwt: device f64 [P] (direction 0; NULL means 1).
+ * Errors: INVALID_ARG, CUDA.
+ */
+awg_status grid_normalize(awg_cf_set cf, void* image, int32_t n_pol, const double* sumwt,
+                          int32_t direction, void* stream);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char* awg_last_error(void);
+
+/* Number of kernels this library has launched in the process so far (all threads, all devices).
+ * A diagnostic for benchmarks and tests; reading it has no side effect. */
+int64_t awg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AWGRID_H */

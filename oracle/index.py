@@ -43,7 +43,8 @@ class SampleIndex:
 
 
 def sample_index(p: CFParams, uvw_m, freq_hz, pa_bin=None, chan_subband=None,
-                 phase_shift=None) -> SampleIndex:
+                 phase_shift=None, supports=None) -> SampleIndex:
+    """Index every (row, channel) sample; `supports` overrides the schedule (caller-made tables)."""
     uvw_m = np.asarray(uvw_m, dtype=np.float64)
     freq_hz = np.asarray(freq_hz, dtype=np.float64)
     R, C = uvw_m.shape[0], freq_hz.shape[0]
@@ -69,7 +70,7 @@ def sample_index(p: CFParams, uvw_m, freq_hz, pa_bin=None, chan_subband=None,
     pa = np.zeros((R, 1), dtype=np.int64) if p.n_pa_bins == 1 else np.asarray(pa_bin, dtype=np.int64)[:, None]
     sb = np.zeros((1, C), dtype=np.int64) if p.n_subbands == 1 else np.asarray(chan_subband, dtype=np.int64)[None, :]
     cf = (pa * p.n_subbands + sb) * p.n_signed + ks
-    sup_tab = cf_supports(p)
+    sup_tab = cf_supports(p) if supports is None else np.asarray(supports, dtype=np.int32)
     S = sup_tab[cf].astype(np.float64)
     hx = x - S * 0.5
     hy = y - S * 0.5

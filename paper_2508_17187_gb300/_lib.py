@@ -1,0 +1,95 @@
+"""ctypes view of the awgrid C ABI (include/awgrid.h).  Marshalling only: every computation runs
+in libawgrid.so.  Importing this module never builds or falls back; a missing library raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libawgrid.so")
+
+AWG_OK = 0
+STATUS_NAMES = {0: "AWG_OK", 1: "AWG_ERR_INVALID_ARG", 2: "AWG_ERR_UNSUPPORTED", 3: "AWG_ERR_OOM",
+                4: "AWG_ERR_CUDA", 5: "AWG_ERR_TIMEOUT"}
+AWG_CF_FP32, AWG_CF_BF16 = 0, 1
+AWG_GRID_KAHAN, AWG_GRID_FP64 = 1, 2
+
+EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_get_supports",
+            "cf_set_copy_table", "plan_create", "plan_update", "plan_destroy", "plan_stats", "grid_visibilities",
+            "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches"]
+
+
+class AwgError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class CfParams(ctypes.Structure):
+    _fields_ = [
+        ("grid_n", ctypes.c_int),
+        ("cell_rad", ctypes.c_double),
+        ("oversampling", ctypes.c_int),
+        ("ps_support", ctypes.c_int),
+        ("use_ps", ctypes.c_int),
+        ("use_w", ctypes.c_int),
+        ("n_wplanes", ctypes.c_int),
+        ("w_max_lambda", ctypes.c_double),
+        ("use_a", ctypes.c_int),
+        ("n_pa_bins", ctypes.c_int),
+        ("pa_bin_centers_rad", ctypes.POINTER(ctypes.c_double)),
+        ("n_subbands", ctypes.c_int),
+        ("subband_freq_hz", ctypes.POINTER(ctypes.c_double)),
+        ("max_support", ctypes.c_int),
+        ("dish_diameter_m", ctypes.c_double),
+        ("ellipticity", ctypes.c_double),
+        ("cf_dtype", ctypes.c_int),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load the in-tree libawgrid.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2508_17187_gb300.build.build() "
+                               "(there is no fallback implementation)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f64p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        st = ctypes.c_int
+        sig = {
+            "cf_set_create": ([ctypes.POINTER(CfParams), vp, ctypes.POINTER(vp)], st),
+            "cf_set_create_from_table": ([ctypes.POINTER(CfParams), vp, vp, vp, ctypes.POINTER(vp)], st),
+            "cf_set_destroy": ([vp], st),
+            "cf_set_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], st),
+            "cf_set_get_supports": ([vp, vp], st),
+            "cf_set_copy_table": ([vp, i32, vp], st),
+            "plan_create": ([vp, vp, i64, vp, i32, vp, vp, vp, vp, ctypes.POINTER(vp)], st),
+            "plan_update": ([vp, vp, vp, vp, vp, vp], st),
+            "plan_destroy": ([vp], st),
+            "plan_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
+            "grid_visibilities": ([vp, vp, vp, vp, i32, vp, vp, vp, i32, vp], st),
+            "degrid_visibilities": ([vp, vp, vp, vp, i32, i32, vp], st),
+            "grid_normalize": ([vp, vp, i32, vp, i32, vp], st),
+            "awg_last_error": ([], ctypes.c_char_p),
+            "awg_kernel_launches": ([], ctypes.c_int64),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def check(status: int, where: str):
+    if status != AWG_OK:
+        msg = load().awg_last_error()
+        raise AwgError(status, where, msg.decode() if msg else "")

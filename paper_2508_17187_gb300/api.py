@@ -1,0 +1,241 @@
+"""Python binding of the awgrid C ABI with the same names (cf_set_create, plan_create,
+grid_visibilities, degrid_visibilities, grid_normalize).  It checks and marshals torch tensors
+and passes their device pointers; all arithmetic happens in libawgrid.so."""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import AWG_CF_BF16, AWG_CF_FP32, AWG_GRID_FP64, AWG_GRID_KAHAN, CfParams, check
+
+__all__ = ["CFSet", "Plan", "cf_set_create", "cf_set_create_from_table", "plan_create", "grid_visibilities",
+           "degrid_visibilities", "grid_normalize", "AWG_CF_FP32", "AWG_CF_BF16", "AWG_GRID_KAHAN", "AWG_GRID_FP64"]
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None else None)
+
+
+def _need(t: torch.Tensor, name: str, dtype, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class CFSet:
+    """Owns an awg_cf_set (device-resident CF tables)."""
+
+    def __init__(self, handle: ctypes.c_void_p, grid_n: int, oversampling: int, n_pa_bins: int, n_subbands: int):
+        self._h = handle
+        self.grid_n = grid_n
+        self.oversampling = oversampling
+        self.n_pa_bins = n_pa_bins
+        self.n_subbands = n_subbands
+        n_cf = ctypes.c_int32()
+        n_val = ctypes.c_int64()
+        check(_lib.load().cf_set_info(self._h, ctypes.byref(n_cf), ctypes.byref(n_val)), "cf_set_info")
+        self.n_cf = int(n_cf.value)
+        self.n_values = int(n_val.value)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("CF set already destroyed")
+        return self._h
+
+    def supports(self) -> np.ndarray:
+        out = np.zeros(self.n_cf, dtype=np.int32)
+        check(_lib.load().cf_set_get_supports(self.handle, out.ctypes.data_as(ctypes.c_void_p)), "cf_set_get_supports")
+        return out
+
+    def copy_table(self, cf_index: int) -> np.ndarray:
+        S = int(self.supports()[cf_index])
+        OS = self.oversampling
+        out = np.zeros((OS + 1, OS + 1, S, S, 2), dtype=np.float32)
+        check(_lib.load().cf_set_copy_table(self.handle, int(cf_index), out.ctypes.data_as(ctypes.c_void_p)),
+              "cf_set_copy_table")
+        return out[..., 0] + 1j * out[..., 1]
+
+    def close(self):
+        if self._h is not None:
+            check(_lib.load().cf_set_destroy(self._h), "cf_set_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _params(grid_n, cell_rad, oversampling=20, ps_support=7, use_ps=True, use_w=False, n_wplanes=1,
+            w_max_lambda=0.0, use_a=False, n_pa_bins=1, pa_bin_centers_rad=None, n_subbands=1,
+            subband_freq_hz=None, max_support=7, dish_diameter_m=25.0, ellipticity=0.05, cf_dtype=AWG_CF_FP32):
+    p = CfParams()
+    p.grid_n = int(grid_n)
+    p.cell_rad = float(cell_rad)
+    p.oversampling = int(oversampling)
+    p.ps_support = int(ps_support)
+    p.use_ps = int(bool(use_ps))
+    p.use_w = int(bool(use_w))
+    p.n_wplanes = int(n_wplanes)
+    p.w_max_lambda = float(w_max_lambda)
+    p.use_a = int(bool(use_a))
+    p.n_pa_bins = int(n_pa_bins)
+    p.n_subbands = int(n_subbands)
+    p.max_support = int(max_support)
+    p.dish_diameter_m = float(dish_diameter_m)
+    p.ellipticity = float(ellipticity)
+    p.cf_dtype = int(cf_dtype)
+    keep = []
+    if pa_bin_centers_rad is not None:
+        a = np.ascontiguousarray(pa_bin_centers_rad, dtype=np.float64)
+        keep.append(a)
+        p.pa_bin_centers_rad = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if subband_freq_hz is not None:
+        a = np.ascontiguousarray(subband_freq_hz, dtype=np.float64)
+        keep.append(a)
+        p.subband_freq_hz = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return p, keep
+
+
+def cf_set_create(stream=None, **params) -> CFSet:
+    """Build the CF set of Tab. AWP-CFSETUP on the host in FP64 and upload it (see awgrid.h)."""
+    p, keep = _params(**params)
+    h = ctypes.c_void_p()
+    check(_lib.load().cf_set_create(ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)), "cf_set_create")
+    del keep
+    return CFSet(h, p.grid_n, p.oversampling, p.n_pa_bins, p.n_subbands)
+
+
+def cf_set_create_from_table(supports: Sequence[int], table: np.ndarray, stream=None, **params) -> CFSet:
+    """CF set from caller tables: table complex, all CFs concatenated, each [OS+1][OS+1][S][S]."""
+    p, keep = _params(**params)
+    sup = np.ascontiguousarray(supports, dtype=np.int32)
+    tab = np.ascontiguousarray(np.stack([np.real(table), np.imag(table)], -1).astype(np.float32).reshape(-1))
+    h = ctypes.c_void_p()
+    check(_lib.load().cf_set_create_from_table(ctypes.byref(p), sup.ctypes.data_as(ctypes.c_void_p),
+                                               tab.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream),
+                                               ctypes.byref(h)), "cf_set_create_from_table")
+    del keep
+    return CFSet(h, p.grid_n, p.oversampling, p.n_pa_bins, p.n_subbands)
+
+
+class Plan:
+    """Owns an awg_plan: the per-sample index and tiled ordering of R x C samples."""
+
+    def __init__(self, cf: CFSet, uvw_m: torch.Tensor, freq_hz: torch.Tensor, pa_bin: Optional[torch.Tensor] = None,
+                 chan_subband: Optional[torch.Tensor] = None, phase_shift=None, stream=None):
+        _need(uvw_m, "uvw_m", torch.float64)
+        _need(freq_hz, "freq_hz", torch.float64)
+        if uvw_m.dim() != 2 or uvw_m.shape[1] != 3:
+            raise ValueError("uvw_m must be [R, 3]")
+        if pa_bin is not None:
+            _need(pa_bin, "pa_bin", torch.int32, (uvw_m.shape[0],))
+        if chan_subband is not None:
+            _need(chan_subband, "chan_subband", torch.int32, (freq_hz.shape[0],))
+        self.cf = cf
+        self.n_rows = int(uvw_m.shape[0])
+        self.n_chan = int(freq_hz.shape[0])
+        ph = None
+        if phase_shift is not None:
+            ph = np.ascontiguousarray(phase_shift, dtype=np.float64)
+        h = ctypes.c_void_p()
+        check(_lib.load().plan_create(cf.handle, _ptr(uvw_m), self.n_rows, _ptr(freq_hz), self.n_chan, _ptr(pa_bin),
+                                      _ptr(chan_subband),
+                                      ph.ctypes.data_as(ctypes.c_void_p) if ph is not None else None,
+                                      _stream_ptr(stream), ctypes.byref(h)), "plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan already destroyed")
+        return self._h
+
+    def update(self, uvw_m, freq_hz, pa_bin=None, chan_subband=None, stream=None):
+        _need(uvw_m, "uvw_m", torch.float64, (self.n_rows, 3))
+        _need(freq_hz, "freq_hz", torch.float64, (self.n_chan,))
+        check(_lib.load().plan_update(self.handle, _ptr(uvw_m), _ptr(freq_hz), _ptr(pa_bin), _ptr(chan_subband),
+                                      _stream_ptr(stream)), "plan_update")
+
+    def stats(self):
+        """(kept samples, dropped samples, sum over kept samples of S^2); synchronises."""
+        k, d, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(_lib.load().plan_stats(self.handle, ctypes.byref(k), ctypes.byref(d), ctypes.byref(t)), "plan_stats")
+        return int(k.value), int(d.value), int(t.value)
+
+    def close(self):
+        if self._h is not None:
+            check(_lib.load().plan_destroy(self._h), "plan_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_create(cf: CFSet, uvw_m, freq_hz, pa_bin=None, chan_subband=None, phase_shift=None, stream=None) -> Plan:
+    return Plan(cf, uvw_m, freq_hz, pa_bin, chan_subband, phase_shift, stream)
+
+
+def _pols(vis: torch.Tensor) -> int:
+    return int(vis.shape[-1])
+
+
+def grid_visibilities(cf: CFSet, plan: Plan, vis: torch.Tensor, weight: torch.Tensor, grid: torch.Tensor,
+                      sumwt: torch.Tensor, grid_lo: Optional[torch.Tensor] = None, flags: int = 0, stream=None):
+    """G (Eq. IMAGE-MOD): grid += sum conj(CF) * weight * vis; sumwt += sum weight (see awgrid.h)."""
+    R, C = plan.n_rows, plan.n_chan
+    P = _pols(vis)
+    N = cf.grid_n
+    _need(vis, "vis", torch.complex64, (R, C, P))
+    _need(weight, "weight", torch.float32, (R, C, P))
+    _need(grid, "grid", torch.complex128 if flags & AWG_GRID_FP64 else torch.complex64, (N, N, P))
+    _need(sumwt, "sumwt", torch.float64, (P,))
+    if grid_lo is not None:
+        _need(grid_lo, "grid_lo", torch.complex64, (N, N, P))
+    check(_lib.load().grid_visibilities(cf.handle, plan.handle, _ptr(vis), _ptr(weight), P, _ptr(grid), _ptr(grid_lo),
+                                        _ptr(sumwt), int(flags), _stream_ptr(stream)), "grid_visibilities")
+
+
+def degrid_visibilities(cf: CFSet, plan: Plan, grid: torch.Tensor, vis_out: torch.Tensor, stream=None):
+    """D (Eq. ME-MOD-GRIDDED): vis_out = sum CF * grid (overwritten; dropped samples get 0)."""
+    R, C = plan.n_rows, plan.n_chan
+    P = _pols(grid)
+    N = cf.grid_n
+    _need(grid, "grid", torch.complex64, (N, N, P))
+    _need(vis_out, "vis_out", torch.complex64, (R, C, P))
+    check(_lib.load().degrid_visibilities(cf.handle, plan.handle, _ptr(grid), _ptr(vis_out), P, 0,
+                                          _stream_ptr(stream)), "degrid_visibilities")
+
+
+def grid_normalize(cf: CFSet, image: torch.Tensor, sumwt: Optional[torch.Tensor] = None, direction: int = 0,
+                   stream=None):
+    """Divide by the PS taper T(x) T(y) (and by sumwt for direction 0), in place."""
+    N = cf.grid_n
+    P = _pols(image)
+    _need(image, "image", torch.complex64, (N, N, P))
+    if sumwt is not None:
+        _need(sumwt, "sumwt", torch.float64, (P,))
+    check(_lib.load().grid_normalize(cf.handle, _ptr(image), P, _ptr(sumwt), int(direction), _stream_ptr(stream)),
+          "grid_normalize")

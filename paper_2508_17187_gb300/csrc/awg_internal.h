@@ -1,0 +1,136 @@
+// Internal declarations of the awgrid library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "awgrid.h"
+
+namespace awg {
+
+constexpr double kCLight = 299792458.0;
+constexpr int kMaxSupport = 64;
+constexpr int kNumClasses = 6;
+constexpr int kItemChunk = 256;   // samples per work item at most (bounds the queue tail)
+
+// Kernel classes: supports in (smax of the previous class, smax] run in one template instance
+// with nt threads per CTA and tile x tile sample-start positions per work item.
+struct ClassCfg {
+  int smax, nt, tile;
+};
+constexpr ClassCfg kClasses[kNumClasses] = {
+    {8, 64, 32}, {16, 128, 32}, {24, 192, 32}, {32, 256, 32}, {48, 256, 16}, {64, 256, 16}};
+
+// Class of a support (the smax column of kClasses, spelled out so device code can call it).
+__host__ __device__ inline int class_of_support(int S) {
+  return S <= 8 ? 0 : S <= 16 ? 1 : S <= 24 ? 2 : S <= 32 ? 3 : S <= 48 ? 4 : S <= 64 ? 5 : -1;
+}
+
+// One kept sample in plan order (16 bytes, one vector load).
+struct __align__(16) SampleRec {
+  int32_t src;      // row * C + chan
+  int32_t cf;       // CF index
+  uint16_t p0x, p0y;  // first tap pixel
+  uint8_t ox, oy;   // oversampling offsets in [0, OS]
+  uint8_t S;        // taps per axis
+  uint8_t flags;
+};
+
+// One unit of the work queue: up to kItemChunk samples of one support whose first taps lie in
+// one tile x tile block of the grid.
+struct __align__(16) WorkItem {
+  int32_t start, count;
+  uint16_t tile_x, tile_y;
+  uint16_t S, cls;
+};
+
+// Distinct supports of a CF set, each with its own tiling of the sample-start positions.
+struct SlotTable {
+  int n;                       // number of distinct supports
+  int S[kMaxSupport];          // ascending
+  int tile[kMaxSupport];
+  int nt[kMaxSupport];         // tiles per axis
+  int base[kMaxSupport + 1];   // first bucket of the slot; base[n] = number of buckets
+  int slot_of_S[kMaxSupport + 1];
+};
+
+struct CfSetImpl {
+  awg_cf_params p{};
+  std::vector<double> pa_centers, sb_freqs;
+  int n_cf = 0, n_signed = 1;
+  std::vector<int32_t> supports;
+  std::vector<int64_t> offsets;   // element offset of each table
+  int64_t n_values = 0;
+  int device = 0;
+  void* d_data = nullptr;         // float2 or bf16x2 [n_values]
+  int64_t* d_off = nullptr;
+  int32_t* d_sup = nullptr;
+  float* d_inv_taper = nullptr;   // 1 / T(x - N/2), x in [0, N)
+  SlotTable slots{};
+};
+
+struct PlanImpl {
+  CfSetImpl* cf = nullptr;
+  int64_t R = 0;
+  int C = 0;
+  int64_t n = 0;
+  int has_phase = 0;
+  double dl = 0, dm = 0, dn = 0;
+  int device = 0;
+  int n_buckets = 0;
+  int64_t max_items = 0;
+  // device buffers
+  SampleRec* d_rec = nullptr;
+  SampleRec* d_rec_tmp = nullptr;
+  int32_t* d_key = nullptr;
+  int32_t* d_drop = nullptr;
+  int32_t* d_bcount = nullptr;    // [n_buckets]
+  int32_t* d_boff = nullptr;      // [n_buckets + 1]
+  int32_t* d_icount = nullptr;    // [n_buckets]
+  int32_t* d_ioff = nullptr;      // [n_buckets + 1]
+  int32_t* d_scan_tmp = nullptr;
+  WorkItem* d_items = nullptr;    // [max_items]
+  int32_t* d_class_range = nullptr;  // [kNumClasses + 1]
+  int32_t* d_queue = nullptr;        // [kNumClasses] work-queue heads
+  unsigned long long* d_counters = nullptr;  // [0] kept, [1] dropped, [2] sum of S^2
+  double* d_uvw = nullptr;        // plan-owned copies of uvw / freq (only with a phase shift,
+  double* d_freq = nullptr;       // whose phasor the compute kernels form per sample)
+  cudaStream_t last_stream = nullptr;
+};
+
+// Count of kernel launches made by the library (awg_kernel_launches).
+void count_launches(int n);
+
+// Error state (thread-local message).
+awg_status set_error(awg_status st, const std::string& msg);
+awg_status cuda_error(cudaError_t e, const char* where);
+
+#define AWG_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return awg::cuda_error(_e, #expr); \
+  } while (0)
+
+// Host CF construction (cf_build.cpp).
+int support_of_plane(const awg_cf_params& p, int ks);
+int screen_size(int S);
+void build_cf_table(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa,
+                    int sb, int ks, std::vector<double>& out /* 2 (OS+1)^2 S^2 */);
+void taper_image(const awg_cf_params& p, std::vector<double>& out /* N */);
+
+// Plan kernels (plan.cu).
+awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const int32_t* pa_bin,
+                      const int32_t* chan_sb, cudaStream_t st);
+
+// Compute launches (grid.cu, degrid.cu, normalize.cu).
+awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float* weight, int P,
+                       void* grid, void* grid_lo, double* sumwt, int flags, cudaStream_t st);
+awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vis_out, int P,
+                         cudaStream_t st);
+awg_status launch_normalize(CfSetImpl* cf, void* image, int P, const double* sumwt, int direction,
+                            cudaStream_t st);
+
+}  // namespace awg

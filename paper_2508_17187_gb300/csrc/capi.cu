@@ -1,0 +1,492 @@
+// C ABI entry points of awgrid: argument checks, object lifetimes, CF-set upload.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <omp.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "awg_internal.h"
+
+namespace awg {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+awg_status set_error(awg_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+awg_status cuda_error(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(AWG_ERR_OOM, std::string("device allocation failed in ") + where);
+  }
+  return set_error(AWG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static uint16_t f32_to_bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffff) ? 0x40 : 0));
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+static float bf16_to_f32(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+static awg_status check_params(const awg_cf_params* p, bool from_table) {
+  if (!p) return set_error(AWG_ERR_INVALID_ARG, "params is NULL");
+  if (p->grid_n < 16 || p->grid_n > 65536 || (p->grid_n & 1))
+    return set_error(AWG_ERR_INVALID_ARG, "grid_n must be even and in [16, 65536]");
+  if (p->oversampling < 1 || p->oversampling > 250)
+    return set_error(AWG_ERR_INVALID_ARG, "oversampling must be in [1, 250]");
+  if (p->n_pa_bins < 1 || p->n_subbands < 1 || p->n_pa_bins * p->n_subbands > 1 << 20)
+    return set_error(AWG_ERR_INVALID_ARG, "n_pa_bins and n_subbands must be >= 1");
+  if (p->use_w && (p->n_wplanes < 2 || !(p->w_max_lambda > 0.0)))
+    return set_error(AWG_ERR_INVALID_ARG, "use_w needs n_wplanes >= 2 and w_max_lambda > 0");
+  if (p->cf_dtype != AWG_CF_FP32 && p->cf_dtype != AWG_CF_BF16)
+    return set_error(AWG_ERR_INVALID_ARG, "cf_dtype must be AWG_CF_FP32 or AWG_CF_BF16");
+  if (from_table) return AWG_OK;
+  if (!(p->cell_rad > 0.0) || p->cell_rad * p->grid_n >= 2.0)
+    return set_error(AWG_ERR_INVALID_ARG, "cell_rad must be > 0 with the field inside the sky");
+  if (p->use_ps && p->ps_support < 1) return set_error(AWG_ERR_INVALID_ARG, "ps_support must be >= 1");
+  if (p->max_support < 1) return set_error(AWG_ERR_INVALID_ARG, "max_support must be >= 1");
+  if (p->max_support > kMaxSupport) return set_error(AWG_ERR_UNSUPPORTED, "max_support > 64 is not supported");
+  if (p->use_ps && p->ps_support > p->max_support)
+    return set_error(AWG_ERR_INVALID_ARG, "ps_support must not exceed max_support");
+  if (p->use_a) {
+    if (!p->pa_bin_centers_rad || !p->subband_freq_hz)
+      return set_error(AWG_ERR_INVALID_ARG, "use_a needs pa_bin_centers_rad and subband_freq_hz");
+    if (!(p->dish_diameter_m > 0.0) || !(std::fabs(p->ellipticity) < 0.5))
+      return set_error(AWG_ERR_INVALID_ARG, "dish_diameter_m must be > 0 and |ellipticity| < 0.5");
+  }
+  return AWG_OK;
+}
+
+static void fill_slots(CfSetImpl* cf) {
+  bool present[kMaxSupport + 1] = {false};
+  for (int s : cf->supports) present[s] = true;
+  SlotTable& st = cf->slots;
+  st = SlotTable{};
+  for (int s = 0; s <= kMaxSupport; ++s) st.slot_of_S[s] = -1;
+  const int N = cf->p.grid_n;
+  int base = 0;
+  for (int s = 1; s <= kMaxSupport; ++s) {
+    if (!present[s]) continue;
+    const int i = st.n++;
+    st.S[i] = s;
+    st.tile[i] = kClasses[class_of_support(s)].tile;
+    const int span = N - s + 1;    // possible first-tap positions per axis
+    st.nt[i] = span > 0 ? (span + st.tile[i] - 1) / st.tile[i] : 0;
+    st.base[i] = base;
+    st.slot_of_S[s] = i;
+    base += st.nt[i] * st.nt[i];
+  }
+  st.base[st.n] = base;
+}
+
+static void free_cf(CfSetImpl* cf) {
+  if (!cf) return;
+  cudaFree(cf->d_data);
+  cudaFree(cf->d_off);
+  cudaFree(cf->d_sup);
+  cudaFree(cf->d_inv_taper);
+  delete cf;
+}
+
+// Upload the host tables of one batch (FP64 interleaved) into the device array at their offsets.
+static awg_status upload_tables(CfSetImpl* cf, const std::vector<int>& idx, const std::vector<std::vector<double>>& tabs,
+                                cudaStream_t st) {
+  const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
+  for (size_t j = 0; j < idx.size(); ++j) {
+    const int ci = idx[j];
+    const int64_t nv = (int64_t)tabs[j].size() / 2;
+    if (bf16) {
+      std::vector<uint16_t> h((size_t)nv * 2);
+      for (int64_t i = 0; i < 2 * nv; ++i) h[i] = f32_to_bf16_rne((float)tabs[j][i]);
+      AWG_CUDA_TRY(cudaMemcpyAsync((uint16_t*)cf->d_data + 2 * cf->offsets[ci], h.data(), 4 * nv,
+                                   cudaMemcpyHostToDevice, st));
+      AWG_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+      std::vector<float> h((size_t)nv * 2);
+      for (int64_t i = 0; i < 2 * nv; ++i) h[i] = (float)tabs[j][i];
+      AWG_CUDA_TRY(cudaMemcpyAsync((float*)cf->d_data + 2 * cf->offsets[ci], h.data(), 8 * nv,
+                                   cudaMemcpyHostToDevice, st));
+      AWG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+  }
+  return AWG_OK;
+}
+
+static awg_status alloc_cf(CfSetImpl* cf, cudaStream_t st) {
+  cf->n_signed = cf->p.use_w ? 2 * cf->p.n_wplanes - 1 : 1;
+  cf->offsets.resize(cf->n_cf);
+  int64_t off = 0;
+  const int64_t per = (int64_t)(cf->p.oversampling + 1) * (cf->p.oversampling + 1);
+  for (int i = 0; i < cf->n_cf; ++i) {
+    cf->offsets[i] = off;
+    off += per * cf->supports[i] * cf->supports[i];
+  }
+  cf->n_values = off;
+  const size_t bytes = (size_t)off * (cf->p.cf_dtype == AWG_CF_BF16 ? 4 : 8);
+  size_t free_b = 0, total_b = 0;
+  AWG_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  if (bytes + (size_t)(256u << 20) > free_b)
+    return set_error(AWG_ERR_OOM, "CF set of " + std::to_string(bytes >> 20) + " MiB does not fit in device memory");
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_data, bytes));
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_off, sizeof(int64_t) * cf->n_cf));
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_off, cf->offsets.data(), sizeof(int64_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sup, cf->supports.data(), sizeof(int32_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
+  std::vector<double> taper;
+  taper_image(cf->p, taper);
+  std::vector<float> inv(cf->p.grid_n);
+  for (int i = 0; i < cf->p.grid_n; ++i) inv[i] = (float)(1.0 / taper[i]);
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_inv_taper, inv.data(), sizeof(float) * cf->p.grid_n, cudaMemcpyHostToDevice, st));
+  AWG_CUDA_TRY(cudaStreamSynchronize(st));
+  fill_slots(cf);
+  return AWG_OK;
+}
+
+}  // namespace awg
+
+using namespace awg;
+
+extern "C" {
+
+const char* awg_last_error(void) { return g_last_error.c_str(); }
+
+int64_t awg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* out) {
+  if (!out) return set_error(AWG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  awg_status s = check_params(params, false);
+  if (s != AWG_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  CfSetImpl* cf = new (std::nothrow) CfSetImpl();
+  if (!cf) return set_error(AWG_ERR_OOM, "host allocation failed");
+  cf->p = *params;
+  if (params->use_a) {
+    cf->pa_centers.assign(params->pa_bin_centers_rad, params->pa_bin_centers_rad + params->n_pa_bins);
+    cf->sb_freqs.assign(params->subband_freq_hz, params->subband_freq_hz + params->n_subbands);
+  }
+  cf->p.pa_bin_centers_rad = nullptr;
+  cf->p.subband_freq_hz = nullptr;
+  cudaGetDevice(&cf->device);
+  const int n_signed = params->use_w ? 2 * params->n_wplanes - 1 : 1;
+  cf->n_cf = params->n_pa_bins * params->n_subbands * n_signed;
+  cf->supports.resize(cf->n_cf);
+  for (int pa = 0; pa < params->n_pa_bins; ++pa)
+    for (int sb = 0; sb < params->n_subbands; ++sb)
+      for (int ks = 0; ks < n_signed; ++ks)
+        cf->supports[(pa * params->n_subbands + sb) * n_signed + ks] = support_of_plane(cf->p, ks);
+  s = alloc_cf(cf, st);
+  if (s != AWG_OK) { free_cf(cf); return s; }
+  // Build the non-negative planes (the others are their conjugate point reflections) in batches
+  // of bounded host memory, OpenMP over CFs within a batch.
+  const int n_w = params->use_w ? params->n_wplanes : 1;
+  const int n_pos = params->n_pa_bins * params->n_subbands * n_w;
+  const int64_t per = (int64_t)(params->oversampling + 1) * (params->oversampling + 1);
+  const int64_t budget = (int64_t)1 << 31;   // FP64 values per batch (16 GiB of host memory)
+  int j0 = 0;
+  while (j0 < n_pos) {
+    std::vector<int> jobs;
+    int64_t used = 0;
+    for (int j = j0; j < n_pos; ++j) {
+      const int k = j % n_w;
+      const int ks = params->use_w ? params->n_wplanes - 1 + k : 0;
+      const int S = support_of_plane(cf->p, ks);
+      const int64_t need = 2 * per * S * S * (params->use_w && k > 0 ? 2 : 1);
+      if (!jobs.empty() && used + need > budget) break;
+      jobs.push_back(j);
+      used += need;
+    }
+    std::vector<std::vector<double>> tabs(jobs.size());
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int q = 0; q < (int)jobs.size(); ++q) {
+      const int j = jobs[q];
+      const int k = j % n_w, pasb = j / n_w;
+      const int pa = pasb / params->n_subbands, sb = pasb % params->n_subbands;
+      const int ks = params->use_w ? params->n_wplanes - 1 + k : 0;
+      build_cf_table(cf->p, cf->pa_centers.data(), cf->sb_freqs.data(), pa, sb, ks, tabs[q]);
+    }
+    std::vector<int> idx;
+    std::vector<std::vector<double>> all;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      const int j = jobs[q];
+      const int k = j % n_w, pasb = j / n_w;
+      const int ks = params->use_w ? params->n_wplanes - 1 + k : 0;
+      const bool has_neg = params->use_w && k > 0;
+      std::vector<double> neg;
+      if (has_neg) {
+        // table(-w)[o][t] = conj(table(+w)[OS - o][S - 1 - t]): the flat array reversed, conjugated.
+        const std::vector<double>& t = tabs[q];
+        const size_t nv = t.size() / 2;
+        neg.resize(t.size());
+        for (size_t i = 0; i < nv; ++i) {
+          neg[2 * i] = t[2 * (nv - 1 - i)];
+          neg[2 * i + 1] = -t[2 * (nv - 1 - i) + 1];
+        }
+      }
+      idx.push_back(pasb * n_signed + ks);
+      all.push_back(std::move(tabs[q]));
+      if (has_neg) {
+        idx.push_back(pasb * n_signed + (params->n_wplanes - 1 - k));
+        all.push_back(std::move(neg));
+      }
+    }
+    s = upload_tables(cf, idx, all, st);
+    if (s != AWG_OK) { free_cf(cf); return s; }
+    j0 += (int)jobs.size();
+  }
+  *out = (awg_cf_set)cf;
+  return AWG_OK;
+}
+
+awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* supports, const float* table,
+                                    void* stream, awg_cf_set* out) {
+  if (!out) return set_error(AWG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  awg_status s = check_params(params, true);
+  if (s != AWG_OK) return s;
+  if (!supports || !table) return set_error(AWG_ERR_INVALID_ARG, "supports and table must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  CfSetImpl* cf = new (std::nothrow) CfSetImpl();
+  if (!cf) return set_error(AWG_ERR_OOM, "host allocation failed");
+  cf->p = *params;
+  cf->p.pa_bin_centers_rad = nullptr;
+  cf->p.subband_freq_hz = nullptr;
+  cf->p.use_ps = 0;
+  cf->p.use_a = 0;
+  cudaGetDevice(&cf->device);
+  const int n_signed = params->use_w ? 2 * params->n_wplanes - 1 : 1;
+  cf->n_cf = params->n_pa_bins * params->n_subbands * n_signed;
+  cf->supports.assign(supports, supports + cf->n_cf);
+  for (int v : cf->supports) {
+    if (v < 1) { delete cf; return set_error(AWG_ERR_INVALID_ARG, "supports must be >= 1"); }
+    if (v > kMaxSupport) { delete cf; return set_error(AWG_ERR_UNSUPPORTED, "support > 64 is not supported"); }
+    if (v > params->grid_n) { delete cf; return set_error(AWG_ERR_INVALID_ARG, "support exceeds grid_n"); }
+  }
+  s = alloc_cf(cf, st);
+  if (s != AWG_OK) { free_cf(cf); return s; }
+  std::vector<int> idx;
+  std::vector<std::vector<double>> all;
+  for (int ci = 0; ci < cf->n_cf; ++ci) {
+    const int64_t nv = (int64_t)(params->oversampling + 1) * (params->oversampling + 1) * cf->supports[ci] * cf->supports[ci];
+    const float* src = table + 2 * cf->offsets[ci];
+    idx.push_back(ci);
+    all.emplace_back(src, src + 2 * nv);
+    if (all.size() >= 64 || ci == cf->n_cf - 1) {
+      s = upload_tables(cf, idx, all, st);
+      if (s != AWG_OK) { free_cf(cf); return s; }
+      idx.clear();
+      all.clear();
+    }
+  }
+  *out = (awg_cf_set)cf;
+  return AWG_OK;
+}
+
+awg_status cf_set_destroy(awg_cf_set h) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
+  free_cf((CfSetImpl*)h);
+  return AWG_OK;
+}
+
+awg_status cf_set_info(awg_cf_set h, int32_t* n_cf, int64_t* n_values) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  if (n_cf) *n_cf = cf->n_cf;
+  if (n_values) *n_values = cf->n_values;
+  return AWG_OK;
+}
+
+awg_status cf_set_get_supports(awg_cf_set h, int32_t* out) {
+  if (!h || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  std::memcpy(out, cf->supports.data(), sizeof(int32_t) * cf->n_cf);
+  return AWG_OK;
+}
+
+awg_status cf_set_copy_table(awg_cf_set h, int32_t ci, float* out) {
+  if (!h || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  if (ci < 0 || ci >= cf->n_cf) return set_error(AWG_ERR_INVALID_ARG, "cf index out of range");
+  const int64_t nv = (int64_t)(cf->p.oversampling + 1) * (cf->p.oversampling + 1) * cf->supports[ci] * cf->supports[ci];
+  if (cf->p.cf_dtype == AWG_CF_BF16) {
+    std::vector<uint16_t> h16((size_t)2 * nv);
+    AWG_CUDA_TRY(cudaMemcpy(h16.data(), (uint16_t*)cf->d_data + 2 * cf->offsets[ci], 4 * nv, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < 2 * nv; ++i) out[i] = bf16_to_f32(h16[i]);
+  } else {
+    AWG_CUDA_TRY(cudaMemcpy(out, (float*)cf->d_data + 2 * cf->offsets[ci], 8 * nv, cudaMemcpyDeviceToHost));
+  }
+  return AWG_OK;
+}
+
+static awg_status plan_free(PlanImpl* pl) {
+  if (!pl) return AWG_OK;
+  cudaFree(pl->d_rec);
+  cudaFree(pl->d_rec_tmp);
+  cudaFree(pl->d_key);
+  cudaFree(pl->d_drop);
+  cudaFree(pl->d_bcount);
+  cudaFree(pl->d_boff);
+  cudaFree(pl->d_icount);
+  cudaFree(pl->d_ioff);
+  cudaFree(pl->d_scan_tmp);
+  cudaFree(pl->d_items);
+  cudaFree(pl->d_class_range);
+  cudaFree(pl->d_queue);
+  cudaFree(pl->d_counters);
+  cudaFree(pl->d_uvw);
+  cudaFree(pl->d_freq);
+  delete pl;
+  return AWG_OK;
+}
+
+awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const double* freq_hz, int32_t n_chan,
+                       const int32_t* pa_bin, const int32_t* chan_subband, const double* phase_shift, void* stream,
+                       awg_plan* out) {
+  if (!out) return set_error(AWG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  if (n_rows > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
+  if (n_rows < 0 || n_chan < 1) return set_error(AWG_ERR_INVALID_ARG, "n_rows must be >= 0 and n_chan >= 1");
+  if ((int64_t)n_rows * n_chan > ((int64_t)1 << 31) - 1)
+    return set_error(AWG_ERR_UNSUPPORTED, "more than 2^31 - 1 samples per plan");
+  if (cf->p.n_pa_bins > 1 && !pa_bin) return set_error(AWG_ERR_INVALID_ARG, "pa_bin is required with n_pa_bins > 1");
+  if (cf->p.n_subbands > 1 && !chan_subband)
+    return set_error(AWG_ERR_INVALID_ARG, "chan_subband is required with n_subbands > 1");
+  PlanImpl* pl = new (std::nothrow) PlanImpl();
+  if (!pl) return set_error(AWG_ERR_OOM, "host allocation failed");
+  pl->cf = cf;
+  pl->R = n_rows;
+  pl->C = n_chan;
+  pl->n = n_rows * n_chan;
+  cudaGetDevice(&pl->device);
+  if (phase_shift) {
+    const double dl = phase_shift[0], dm = phase_shift[1];
+    if (!(dl * dl + dm * dm < 1.0)) { delete pl; return set_error(AWG_ERR_INVALID_ARG, "phase shift outside the sky"); }
+    pl->has_phase = 1;
+    pl->dl = dl;
+    pl->dm = dm;
+    pl->dn = std::sqrt(1.0 - dl * dl - dm * dm) - 1.0;
+  }
+  pl->n_buckets = cf->slots.base[cf->slots.n];
+  pl->max_items = (int64_t)pl->n_buckets + pl->n / kItemChunk + 1;
+  const size_t n = (size_t)std::max<int64_t>(pl->n, 1);
+  const size_t nb = (size_t)pl->n_buckets + 1;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  A((void**)&pl->d_rec, n * sizeof(SampleRec));
+  A((void**)&pl->d_rec_tmp, n * sizeof(SampleRec));
+  A((void**)&pl->d_key, n * sizeof(int32_t));
+  A((void**)&pl->d_drop, n * sizeof(int32_t));
+  A((void**)&pl->d_bcount, nb * sizeof(int32_t));
+  A((void**)&pl->d_boff, nb * sizeof(int32_t));
+  A((void**)&pl->d_icount, nb * sizeof(int32_t));
+  A((void**)&pl->d_ioff, nb * sizeof(int32_t));
+  A((void**)&pl->d_scan_tmp, ((nb + 1023) / 1024 + 1024) * sizeof(int32_t));
+  A((void**)&pl->d_items, (size_t)pl->max_items * sizeof(WorkItem));
+  A((void**)&pl->d_class_range, (kNumClasses + 1) * sizeof(int32_t));
+  A((void**)&pl->d_queue, kNumClasses * sizeof(int32_t));
+  A((void**)&pl->d_counters, 4 * sizeof(unsigned long long));
+  if (pl->has_phase) {
+    A((void**)&pl->d_uvw, (size_t)std::max<int64_t>(pl->R, 1) * 3 * sizeof(double));
+    A((void**)&pl->d_freq, (size_t)pl->C * sizeof(double));
+  }
+  if (e != cudaSuccess) {
+    plan_free(pl);
+    return cuda_error(e, "plan_create allocation");
+  }
+  awg_status s = plan_build(pl, uvw_m, freq_hz, pa_bin, chan_subband, (cudaStream_t)stream);
+  if (s != AWG_OK) {
+    plan_free(pl);
+    return s;
+  }
+  *out = (awg_plan)pl;
+  return AWG_OK;
+}
+
+awg_status plan_update(awg_plan h, const double* uvw_m, const double* freq_hz, const int32_t* pa_bin,
+                       const int32_t* chan_subband, void* stream) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "plan is NULL");
+  PlanImpl* pl = (PlanImpl*)h;
+  if (pl->n > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
+  if (pl->cf->p.n_pa_bins > 1 && !pa_bin) return set_error(AWG_ERR_INVALID_ARG, "pa_bin is required");
+  if (pl->cf->p.n_subbands > 1 && !chan_subband) return set_error(AWG_ERR_INVALID_ARG, "chan_subband is required");
+  return plan_build(pl, uvw_m, freq_hz, pa_bin, chan_subband, (cudaStream_t)stream);
+}
+
+awg_status plan_destroy(awg_plan h) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "plan is NULL");
+  return plan_free((PlanImpl*)h);
+}
+
+awg_status plan_stats(awg_plan h, int64_t* n_kept, int64_t* n_dropped, int64_t* sum_taps) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "plan is NULL");
+  PlanImpl* pl = (PlanImpl*)h;
+  unsigned long long c[4];
+  AWG_CUDA_TRY(cudaStreamSynchronize(pl->last_stream));
+  AWG_CUDA_TRY(cudaMemcpy(c, pl->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+  if (n_kept) *n_kept = (int64_t)c[0];
+  if (n_dropped) *n_dropped = (int64_t)c[1];
+  if (sum_taps) *sum_taps = (int64_t)c[2];
+  return AWG_OK;
+}
+
+awg_status grid_visibilities(awg_cf_set hc, awg_plan hp, const void* vis, const float* weight, int32_t n_pol,
+                             void* grid, void* grid_lo, double* sumwt, int32_t flags, void* stream) {
+  if (!hc || !hp) return set_error(AWG_ERR_INVALID_ARG, "cf set and plan must not be NULL");
+  CfSetImpl* cf = (CfSetImpl*)hc;
+  PlanImpl* pl = (PlanImpl*)hp;
+  if (pl->cf != cf) return set_error(AWG_ERR_INVALID_ARG, "plan was made for another cf set");
+  if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
+  if (flags & ~(AWG_GRID_KAHAN | AWG_GRID_FP64)) return set_error(AWG_ERR_INVALID_ARG, "unknown flags");
+  if ((flags & AWG_GRID_KAHAN) && (flags & AWG_GRID_FP64))
+    return set_error(AWG_ERR_INVALID_ARG, "AWG_GRID_KAHAN and AWG_GRID_FP64 are exclusive");
+  if ((flags & AWG_GRID_KAHAN) && !grid_lo) return set_error(AWG_ERR_INVALID_ARG, "AWG_GRID_KAHAN needs grid_lo");
+  if (pl->n > 0 && (!vis || !weight)) return set_error(AWG_ERR_INVALID_ARG, "vis and weight must not be NULL");
+  if (!grid || !sumwt) return set_error(AWG_ERR_INVALID_ARG, "grid and sumwt must not be NULL");
+  return launch_grid(cf, pl, vis, weight, n_pol, grid, grid_lo, sumwt, flags, (cudaStream_t)stream);
+}
+
+awg_status degrid_visibilities(awg_cf_set hc, awg_plan hp, const void* grid, void* vis_out, int32_t n_pol,
+                               int32_t flags, void* stream) {
+  if (!hc || !hp) return set_error(AWG_ERR_INVALID_ARG, "cf set and plan must not be NULL");
+  CfSetImpl* cf = (CfSetImpl*)hc;
+  PlanImpl* pl = (PlanImpl*)hp;
+  if (pl->cf != cf) return set_error(AWG_ERR_INVALID_ARG, "plan was made for another cf set");
+  if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
+  if (flags != 0) return set_error(AWG_ERR_INVALID_ARG, "degrid_visibilities takes no flags");
+  if (!grid || (pl->n > 0 && !vis_out)) return set_error(AWG_ERR_INVALID_ARG, "grid and vis_out must not be NULL");
+  return launch_degrid(cf, pl, grid, vis_out, n_pol, (cudaStream_t)stream);
+}
+
+awg_status grid_normalize(awg_cf_set hc, void* image, int32_t n_pol, const double* sumwt, int32_t direction,
+                          void* stream) {
+  if (!hc || !image) return set_error(AWG_ERR_INVALID_ARG, "cf set and image must not be NULL");
+  if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
+  if (direction != 0 && direction != 1) return set_error(AWG_ERR_INVALID_ARG, "direction must be 0 or 1");
+  return launch_normalize((CfSetImpl*)hc, image, n_pol, sumwt, direction, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+"""Shared test helpers: one workload description feeds both the oracle and the library."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import cf as ocf
+
+
+def oracle_params(wl, **over) -> ocf.CFParams:
+    p = dict(grid_n=wl.grid_n, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support,
+             use_w=wl.use_w, n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda, use_a=wl.use_a,
+             n_pa_bins=wl.n_pa_bins, pa_bin_centers=list(wl.pa_bin_centers), n_subbands=wl.n_subbands,
+             subband_freq_hz=list(wl.subband_freq_hz), max_support=wl.max_support)
+    p.update(over)
+    return ocf.CFParams(**p)
+
+
+def library_params(op: ocf.CFParams, cf_dtype: int = 0) -> dict:
+    return dict(grid_n=op.grid_n, cell_rad=op.cell_rad, oversampling=op.oversampling, ps_support=op.ps_support,
+                use_ps=op.use_ps, use_w=op.use_w, n_wplanes=op.n_wplanes, w_max_lambda=op.w_max_lambda,
+                use_a=op.use_a, n_pa_bins=op.n_pa_bins,
+                pa_bin_centers_rad=(np.asarray(op.pa_bin_centers, dtype=np.float64) if op.pa_bin_centers is not None else None),
+                n_subbands=op.n_subbands,
+                subband_freq_hz=(np.asarray(op.subband_freq_hz, dtype=np.float64) if op.subband_freq_hz is not None else None),
+                max_support=op.max_support, dish_diameter_m=op.dish_diameter_m, ellipticity=op.ellipticity,
+                cf_dtype=cf_dtype)
+
+
+def rel_rms(a, b) -> float:
+    a = np.asarray(a)
+    b = np.asarray(b)
+    den = np.sqrt(np.sum(np.abs(b) ** 2))
+    return float(np.sqrt(np.sum(np.abs(a - b) ** 2)) / den) if den > 0 else float(np.sqrt(np.sum(np.abs(a) ** 2)))
+
+
+def inner_half(img):
+    """Central N/2 x N/2 of an [N, N, ...] image: the region where the PS taper is >= 0.25.
+
+    Outside it the taper correction divides by T(x) T(y) down to ~1e-7 at the corners, which
+    magnifies any FP32 rounding by up to 1e7; dirty-image errors are gated on this region.
+    """
+    N = img.shape[0]
+    return img[N // 4:3 * N // 4, N // 4:3 * N // 4]
