@@ -95,6 +95,8 @@ struct GridLayout {
   static constexpr size_t bytes = tile_bytes + kStage * (P * sizeof(float2) + sizeof(long long) + sizeof(int));
 };
 
+// Add the P pols of one window pixel into the global grid; g is the complex-element index of
+// pol 0 of the pixel ((y N + x) P), so the pixel's floats start at 2 g.
 template <int P>
 __device__ __forceinline__ void flush_pixel(const GridArgs& a, size_t g, const float2 (&v)[P]) {
   if (a.flags & AWG_GRID_FP64) {
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(NT) k_grid(const GridArgs a, const int cls) {
         v[p] = tile[i * P + p];
         nz |= (v[p].x != 0.f) || (v[p].y != 0.f);
       }
-      if (nz) flush_pixel<P>(a, (size_t)gy * a.N + gx, v);
+      if (nz) flush_pixel<P>(a, ((size_t)gy * a.N + gx) * P, v);   // complex-element index of pol 0
     }
   }
   // sum of weights: warp, then block, then one FP64 atomic per pol
