@@ -187,6 +187,32 @@ awg_status degrid_visibilities(awg_cf_set cf, awg_plan plan, const void* grid, v
 awg_status grid_normalize(awg_cf_set cf, void* image, int32_t n_pol, const double* sumwt,
                           int32_t direction, void* stream);
 
+/*
+ * Gridding without any device allocation (the paper has no counterpart: this is a service for
+ * callers of the library).  Some callers cannot allocate device memory once they are running:
+ * real-time pipelines that reserve all of the GPU's memory at start-up and forbid allocation
+ * afterwards, and hosts whose own allocator owns the device, where a raw cudaMalloc would fail or
+ * break that allocator's pool.  This call does what plan_create followed by grid_visibilities
+ * (flags 0, no phase shift) does, but keeps the plan in one fixed array of about 4.7 MB of device
+ * memory that belongs to the loaded library (every GPU that loads the library holds it until the
+ * process exits); it calls no cudaMalloc, cudaFree or allocating library routine.
+ * Limits: at most 65536 samples (n_rows x n_chan) per call and at most 65536 (support, tile)
+ * buckets for the CF set and grid size (small grids, e.g. N = 512 with a few supports); larger
+ * requests return AWG_ERR_INVALID_ARG with the limit in awg_last_error() and launch nothing.
+ * Arguments: as plan_create (uvw_m, freq_hz, pa_bin, chan_subband: device) and grid_visibilities
+ * (vis, weight, grid, sumwt: device, accumulated).
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture on the device.
+ * Every call on a device shares the one array and it keeps what the last call left there; each
+ * call clears what it accumulates into before use, so sequential calls are independent, but calls
+ * whose work overlaps on the GPU (different streams, not ordered by events) race and corrupt each
+ * other's results: order them on one stream.
+ */
+awg_status grid_visibilities_noalloc(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const double* freq_hz,
+                                     int32_t n_chan, const int32_t* pa_bin, const int32_t* chan_subband,
+                                     const void* vis, const float* weight, int32_t n_pol, void* grid,
+                                     double* sumwt, void* stream);
+
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* awg_last_error(void);
 

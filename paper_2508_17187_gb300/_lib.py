@@ -17,7 +17,8 @@ AWG_GRID_KAHAN, AWG_GRID_FP64 = 1, 2
 
 EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_get_supports",
             "cf_set_copy_table", "plan_create", "plan_update", "plan_destroy", "plan_stats", "grid_visibilities",
-            "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches"]
+            "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
+            "grid_visibilities_noalloc"]
 
 
 class AwgError(RuntimeError):
@@ -80,6 +81,7 @@ def load():
             "grid_normalize": ([vp, vp, i32, vp, i32, vp], st),
             "awg_last_error": ([], ctypes.c_char_p),
             "awg_kernel_launches": ([], ctypes.c_int64),
+            "grid_visibilities_noalloc": ([vp, vp, i64, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
