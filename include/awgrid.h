@@ -90,12 +90,18 @@ typedef struct {
   double dish_diameter_m;           /* A-term aperture (e.g. 25) */
   double ellipticity;               /* A-term distortion (e.g. 0.05) */
   int cf_dtype;                     /* AWG_CF_FP32 or AWG_CF_BF16 */
+  int separable;                    /* 1: store each CF as an outer product fy[oy][ty] fx[ox][tx] when
+                                       every CF of the set fits one to 1e-7 of its peak (PS and
+                                       W-projection CFs do; A-terms do not); 0: always full tables */
 } awg_cf_params;
 
 /*
  * Build the CF set on the host in FP64 (PreCompute, Sec. 4.1 and Sec. 6 CFCache) and upload it,
  * rounded to cf_dtype, to the current device.  Negative-w planes are the conjugate point
- * reflections of the positive ones (screen(-w) = conj(screen(w))).  Blocking: returns once the
+ * reflections of the positive ones (screen(-w) = conj(screen(w))).  With params->separable and FP32
+ * storage, each table seen as a ((OS+1) S)^2 matrix is fitted as g f^T (alternating least squares);
+ * if every fit is within 1e-7 of the table's peak only the factors are kept (2 (OS+1) S values per
+ * CF instead of ((OS+1) S)^2), otherwise the full tables are.  Blocking: returns once the
  * tables are resident.  Errors: INVALID_ARG (bad params), UNSUPPORTED (max_support > 64), OOM.
  */
 awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* out);
@@ -111,13 +117,14 @@ awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* 
 
 awg_status cf_set_destroy(awg_cf_set cf);
 
-/* Number of CFs and total number of complex values held. */
-awg_status cf_set_info(awg_cf_set cf, int32_t* n_cf, int64_t* n_values);
+/* Number of CFs, complex values held (2-D tables or factors) and whether the set is separable. */
+awg_status cf_set_info(awg_cf_set cf, int32_t* n_cf, int64_t* n_values, int32_t* separable);
 
 /* Host copy of the support of every CF: supports_out host [n_cf]. */
 awg_status cf_set_get_supports(awg_cf_set cf, int32_t* supports_out);
 
-/* Host copy of one CF table as c64 [OS+1][OS+1][S][S] (BF16 tables are widened). Blocking. */
+/* Host copy of one CF table as c64 [OS+1][OS+1][S][S] (BF16 tables are widened; a separable CF
+ * is expanded as the FP32 product fy fx). Blocking. */
 awg_status cf_set_copy_table(awg_cf_set cf, int32_t cf_index, float* table_out);
 
 /*
@@ -212,6 +219,26 @@ awg_status grid_visibilities_noalloc(awg_cf_set cf, const double* uvw_m, int64_t
                                      int32_t n_chan, const int32_t* pa_bin, const int32_t* chan_subband,
                                      const void* vis, const float* weight, int32_t n_pol, void* grid,
                                      double* sumwt, void* stream);
+
+/*
+ * Plain FP64 baseline of G and D (the straightforward port the batched kernels are measured
+ * against): one launch per channel in [chan_begin, chan_end), one thread per row, the index rules
+ * of plan_create evaluated inline, FP32 table values widened to FP64, FP64 multiply-adds, and for
+ * G one FP64 atomic per tap and pol into a complex128 grid.  No plan, no sort, no allocation.
+ * The CF set must hold full FP32 tables (created with separable = 0).  freq_hz_host and
+ * chan_subband_host are HOST arrays [n_chan]; uvw_m, pa_bin, vis, weight: device as above;
+ * grid64: device complex128 [N][N][P] (accumulated); sumwt: device f64 [P] (accumulated);
+ * vis_out: device c64 [R][C][P], written for the channels in range (dropped samples get 0).
+ * Errors: INVALID_ARG, UNSUPPORTED (separable or BF16 CF set), CUDA.
+ */
+awg_status grid_visibilities_plain_fp64(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const double* freq_hz_host,
+                                        int32_t n_chan, int32_t chan_begin, int32_t chan_end, const int32_t* pa_bin,
+                                        const int32_t* chan_subband_host, const void* vis, const float* weight,
+                                        int32_t n_pol, void* grid64, double* sumwt, void* stream);
+awg_status degrid_visibilities_plain_fp64(awg_cf_set cf, const double* uvw_m, int64_t n_rows,
+                                          const double* freq_hz_host, int32_t n_chan, int32_t chan_begin,
+                                          int32_t chan_end, const int32_t* pa_bin, const int32_t* chan_subband_host,
+                                          const void* grid64, void* vis_out, int32_t n_pol, void* stream);
 
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* awg_last_error(void);

@@ -47,6 +47,8 @@ def _load():
             lib.oracle_grid.restype = None
             lib.oracle_degrid.argtypes = [i64, p, p, p, p, p, p, p, p, i32, p, i32, p, i32, p, p, i32]
             lib.oracle_degrid.restype = None
+            lib.oracle_grid_rows.argtypes = [i64, p, p, p, p, p, p, p, p, i32, p, p, p, i32, p, i32, i64, i64, p, i32]
+            lib.oracle_grid_rows.restype = None
             _lib = lib
     return _lib
 
@@ -93,6 +95,25 @@ def grid(idx: SampleIndex, cf_buf, cf_off, OS: int, N: int, vis, weight, nthread
                     _ptr(ph), P, _ptr(vis_ri), _ptr(wt), _ptr(off), OS, _ptr(cfd), N, _ptr(g), _ptr(sw),
                     nthreads or default_threads())
     return g[..., 0] + 1j * g[..., 1], sw
+
+
+def grid_rows(idx: SampleIndex, cf_buf, cf_off, OS: int, N: int, vis, weight, row_lo: int, row_hi: int,
+              nthreads=None):
+    """G restricted to grid rows [row_lo, row_hi): complex128 [row_hi - row_lo, N, P]."""
+    lib = _load()
+    n = idx.valid.shape[0]
+    vis = np.asarray(vis).reshape(n, -1)
+    P = vis.shape[1]
+    vis_ri = np.ascontiguousarray(np.stack([vis.real, vis.imag], -1).astype(np.float64))
+    wt = np.ascontiguousarray(np.asarray(weight, dtype=np.float64).reshape(n, P))
+    cfd = np.ascontiguousarray(np.stack([cf_buf.real, cf_buf.imag], -1).astype(np.float64))
+    off = np.ascontiguousarray(np.asarray(cf_off, dtype=np.int64))
+    band = np.zeros((row_hi - row_lo, N, P, 2), dtype=np.float64)
+    valid, cf, p0x, p0y, ox, oy, sup, ph = _prep(idx)
+    lib.oracle_grid_rows(n, _ptr(valid), _ptr(cf), _ptr(p0x), _ptr(p0y), _ptr(ox), _ptr(oy), _ptr(sup), _ptr(ph),
+                         P, _ptr(vis_ri), _ptr(wt), _ptr(off), OS, _ptr(cfd), N, row_lo, row_hi, _ptr(band),
+                         nthreads or default_threads())
+    return band[..., 0] + 1j * band[..., 1]
 
 
 def degrid(idx: SampleIndex, cf_buf, cf_off, OS: int, grid_c, nthreads=None):

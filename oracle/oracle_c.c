@@ -17,6 +17,12 @@
 #include <omp.h>
 #endif
 
+void oracle_grid_rows(int64_t n, const uint8_t* valid, const int32_t* cf, const int64_t* p0x,
+                      const int64_t* p0y, const int32_t* ox, const int32_t* oy, const int32_t* support,
+                      const double* phasor, int P, const double* vis, const double* wt, const int64_t* cf_off,
+                      int OS, const double* cf_data, int N, int64_t row_lo, int64_t row_hi,
+                      double* band /* [row_hi - row_lo][N][P][2], accumulated */, int nthreads);
+
 void oracle_grid(int64_t n, const uint8_t* valid, const int32_t* cf, const int64_t* p0x,
                  const int64_t* p0y, const int32_t* ox, const int32_t* oy, const int32_t* support,
                  const double* phasor /* [n][2] or NULL */, int P, const double* vis /* [n][P][2] */,
@@ -27,6 +33,16 @@ void oracle_grid(int64_t n, const uint8_t* valid, const int32_t* cf, const int64
     if (!valid[s]) continue;
     for (int p = 0; p < P; ++p) sumwt[p] += wt[s * P + p];
   }
+  oracle_grid_rows(n, valid, cf, p0x, p0y, ox, oy, support, phasor, P, vis, wt, cf_off, OS, cf_data, N, 0, N,
+                   grid, nthreads);
+}
+
+/* G restricted to grid rows [row_lo, row_hi): the same sums, for one band of the grid. */
+void oracle_grid_rows(int64_t n, const uint8_t* valid, const int32_t* cf, const int64_t* p0x,
+                      const int64_t* p0y, const int32_t* ox, const int32_t* oy, const int32_t* support,
+                      const double* phasor, int P, const double* vis, const double* wt, const int64_t* cf_off,
+                      int OS, const double* cf_data, int N, int64_t row_lo, int64_t row_hi, double* band,
+                      int nthreads) {
 #pragma omp parallel num_threads(nthreads)
   {
     int nt = 1, tid = 0;
@@ -34,7 +50,8 @@ void oracle_grid(int64_t n, const uint8_t* valid, const int32_t* cf, const int64
     nt = omp_get_num_threads();
     tid = omp_get_thread_num();
 #endif
-    int64_t y_lo = (int64_t)N * tid / nt, y_hi = (int64_t)N * (tid + 1) / nt;
+    const int64_t span = row_hi - row_lo;
+    int64_t y_lo = row_lo + span * tid / nt, y_hi = row_lo + span * (tid + 1) / nt;
     for (int64_t s = 0; s < n; ++s) {
       if (!valid[s]) continue;
       int S = support[s];
@@ -60,7 +77,7 @@ void oracle_grid(int64_t n, const uint8_t* valid, const int32_t* cf, const int64
         if (y < y_lo || y >= y_hi) continue;
         for (int tx = 0; tx < S; ++tx) {
           double cr = tab[2 * (ty * S + tx)], ci = -tab[2 * (ty * S + tx) + 1];   /* conj(CF) */
-          double* g = grid + ((y * N + p0x[s] + tx) * P) * 2;
+          double* g = band + (((y - row_lo) * N + p0x[s] + tx) * P) * 2;
           for (int p = 0; p < P; ++p) {
             g[2 * p] += cr * a_re[p] - ci * a_im[p];
             g[2 * p + 1] += cr * a_im[p] + ci * a_re[p];

@@ -18,7 +18,7 @@ AWG_GRID_KAHAN, AWG_GRID_FP64 = 1, 2
 EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_get_supports",
             "cf_set_copy_table", "plan_create", "plan_update", "plan_destroy", "plan_stats", "grid_visibilities",
             "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
-            "grid_visibilities_noalloc"]
+            "grid_visibilities_noalloc", "grid_visibilities_plain_fp64", "degrid_visibilities_plain_fp64"]
 
 
 class AwgError(RuntimeError):
@@ -46,6 +46,7 @@ class CfParams(ctypes.Structure):
         ("dish_diameter_m", ctypes.c_double),
         ("ellipticity", ctypes.c_double),
         ("cf_dtype", ctypes.c_int),
+        ("separable", ctypes.c_int),
     ]
 
 
@@ -69,7 +70,7 @@ def load():
             "cf_set_create": ([ctypes.POINTER(CfParams), vp, ctypes.POINTER(vp)], st),
             "cf_set_create_from_table": ([ctypes.POINTER(CfParams), vp, vp, vp, ctypes.POINTER(vp)], st),
             "cf_set_destroy": ([vp], st),
-            "cf_set_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], st),
+            "cf_set_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)], st),
             "cf_set_get_supports": ([vp, vp], st),
             "cf_set_copy_table": ([vp, i32, vp], st),
             "plan_create": ([vp, vp, i64, vp, i32, vp, vp, vp, vp, ctypes.POINTER(vp)], st),
@@ -82,6 +83,8 @@ def load():
             "awg_last_error": ([], ctypes.c_char_p),
             "awg_kernel_launches": ([], ctypes.c_int64),
             "grid_visibilities_noalloc": ([vp, vp, i64, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp], st),
+            "grid_visibilities_plain_fp64": ([vp, vp, i64, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp], st),
+            "degrid_visibilities_plain_fp64": ([vp, vp, i64, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

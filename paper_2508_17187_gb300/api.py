@@ -50,9 +50,12 @@ class CFSet:
         self.n_subbands = n_subbands
         n_cf = ctypes.c_int32()
         n_val = ctypes.c_int64()
-        check(_lib.load().cf_set_info(self._h, ctypes.byref(n_cf), ctypes.byref(n_val)), "cf_set_info")
+        sep = ctypes.c_int32()
+        check(_lib.load().cf_set_info(self._h, ctypes.byref(n_cf), ctypes.byref(n_val), ctypes.byref(sep)),
+              "cf_set_info")
         self.n_cf = int(n_cf.value)
         self.n_values = int(n_val.value)
+        self.separable = bool(sep.value)
 
     @property
     def handle(self):
@@ -87,7 +90,8 @@ class CFSet:
 
 def _params(grid_n, cell_rad, oversampling=20, ps_support=7, use_ps=True, use_w=False, n_wplanes=1,
             w_max_lambda=0.0, use_a=False, n_pa_bins=1, pa_bin_centers_rad=None, n_subbands=1,
-            subband_freq_hz=None, max_support=7, dish_diameter_m=25.0, ellipticity=0.05, cf_dtype=AWG_CF_FP32):
+            subband_freq_hz=None, max_support=7, dish_diameter_m=25.0, ellipticity=0.05, cf_dtype=AWG_CF_FP32,
+            separable=True):
     p = CfParams()
     p.grid_n = int(grid_n)
     p.cell_rad = float(cell_rad)
@@ -104,6 +108,7 @@ def _params(grid_n, cell_rad, oversampling=20, ps_support=7, use_ps=True, use_w=
     p.dish_diameter_m = float(dish_diameter_m)
     p.ellipticity = float(ellipticity)
     p.cf_dtype = int(cf_dtype)
+    p.separable = int(bool(separable))
     keep = []
     if pa_bin_centers_rad is not None:
         a = np.ascontiguousarray(pa_bin_centers_rad, dtype=np.float64)

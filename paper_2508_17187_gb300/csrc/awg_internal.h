@@ -70,6 +70,11 @@ struct CfSetImpl {
   int32_t* d_sup = nullptr;
   float* d_inv_taper = nullptr;   // 1 / T(x - N/2), x in [0, N)
   SlotTable slots{};
+  // Separable storage: CF = fy[oy][ty] * fx[ox][tx]; per CF, fx [OS+1][S] then fy [OS+1][S] c64.
+  int separable = 0;
+  std::vector<int64_t> sep_offsets;
+  void* d_sep = nullptr;
+  int64_t* d_sep_off = nullptr;
 };
 
 struct PlanImpl {
@@ -120,6 +125,10 @@ int screen_size(int S);
 void build_cf_table(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa,
                     int sb, int ks, std::vector<double>& out /* 2 (OS+1)^2 S^2 */);
 void taper_image(const awg_cf_params& p, std::vector<double>& out /* N */);
+// Rank-1 fit C = g f^T of a table seen as a ((OS+1) S) x ((OS+1) S) matrix; true when the
+// residual is at most tol of the peak.  fx = f, fy = g, interleaved complex.
+bool factor_rank1(const std::vector<double>& tab, int S, int OS, double tol, std::vector<double>& fx,
+                  std::vector<double>& fy);
 
 // Plan kernels (plan.cu).
 awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const int32_t* pa_bin,

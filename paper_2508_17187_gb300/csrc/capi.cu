@@ -106,6 +106,8 @@ static void free_cf(CfSetImpl* cf) {
   cudaFree(cf->d_off);
   cudaFree(cf->d_sup);
   cudaFree(cf->d_inv_taper);
+  cudaFree(cf->d_sep);
+  cudaFree(cf->d_sep_off);
   delete cf;
 }
 
@@ -164,6 +166,82 @@ static awg_status alloc_cf(CfSetImpl* cf, cudaStream_t st) {
   return AWG_OK;
 }
 
+// Separable storage: build every non-negative plane, fit it as fy fx, mirror the fit for the
+// negative planes, upload only the factors.  Returns AWG_ERR_UNSUPPORTED (nothing allocated on
+// the device) when some CF is not separable to 1e-7 of its peak.
+static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
+  const awg_cf_params& p = cf->p;
+  cf->n_signed = p.use_w ? 2 * p.n_wplanes - 1 : 1;
+  const int n_w = p.use_w ? p.n_wplanes : 1;
+  const int n_pos = p.n_pa_bins * p.n_subbands * n_w;
+  const int OS = p.oversampling;
+  std::vector<std::vector<double>> fx(cf->n_cf), fy(cf->n_cf);
+  int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < n_pos; ++j) {
+    if (failed) continue;
+    const int k = j % n_w, pasb = j / n_w;
+    const int pa = pasb / p.n_subbands, sb = pasb % p.n_subbands;
+    const int ks = p.use_w ? p.n_wplanes - 1 + k : 0;
+    std::vector<double> tab;
+    build_cf_table(p, cf->pa_centers.data(), cf->sb_freqs.data(), pa, sb, ks, tab);
+    const int S = support_of_plane(p, ks);
+    const int ci = pasb * cf->n_signed + ks;
+    if (!factor_rank1(tab, S, OS, 1e-7, fx[ci], fy[ci])) {
+#pragma omp atomic write
+      failed = 1;
+      continue;
+    }
+    if (p.use_w && k > 0) {
+      // table(-w) = conj(table(+w)) point-reflected: the factors reversed and conjugated
+      const int cn = pasb * cf->n_signed + (p.n_wplanes - 1 - k);
+      const size_t q = fx[ci].size() / 2;
+      fx[cn].resize(2 * q);
+      fy[cn].resize(2 * q);
+      for (size_t i = 0; i < q; ++i) {
+        fx[cn][2 * i] = fx[ci][2 * (q - 1 - i)];
+        fx[cn][2 * i + 1] = -fx[ci][2 * (q - 1 - i) + 1];
+        fy[cn][2 * i] = fy[ci][2 * (q - 1 - i)];
+        fy[cn][2 * i + 1] = -fy[ci][2 * (q - 1 - i) + 1];
+      }
+    }
+  }
+  if (failed) return AWG_ERR_UNSUPPORTED;
+  cf->separable = 1;
+  cf->sep_offsets.resize(cf->n_cf);
+  int64_t off = 0;
+  for (int i = 0; i < cf->n_cf; ++i) {
+    cf->sep_offsets[i] = off;
+    off += 2 * (int64_t)(OS + 1) * cf->supports[i];
+  }
+  cf->n_values = off;
+  std::vector<float> h((size_t)2 * off);
+  for (int i = 0; i < cf->n_cf; ++i) {
+    const int64_t q = (int64_t)(OS + 1) * cf->supports[i];
+    for (int64_t t = 0; t < 2 * q; ++t) {
+      h[2 * cf->sep_offsets[i] + t] = (float)fx[i][t];
+      h[2 * cf->sep_offsets[i] + 2 * q + t] = (float)fy[i][t];
+    }
+  }
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep, sizeof(float) * h.size()));
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep_off, sizeof(int64_t) * cf->n_cf));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep_off, cf->sep_offsets.data(), sizeof(int64_t) * cf->n_cf,
+                               cudaMemcpyHostToDevice, st));
+  // the support / offset bookkeeping the plan and the kernels share with the 2-D layout
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sup, cf->supports.data(), sizeof(int32_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
+  std::vector<double> taper;
+  taper_image(cf->p, taper);
+  std::vector<float> inv(cf->p.grid_n);
+  for (int i = 0; i < cf->p.grid_n; ++i) inv[i] = (float)(1.0 / taper[i]);
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_inv_taper, inv.data(), sizeof(float) * cf->p.grid_n, cudaMemcpyHostToDevice, st));
+  AWG_CUDA_TRY(cudaStreamSynchronize(st));
+  fill_slots(cf);
+  return AWG_OK;
+}
+
 }  // namespace awg
 
 using namespace awg;
@@ -197,6 +275,15 @@ awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* 
     for (int sb = 0; sb < params->n_subbands; ++sb)
       for (int ks = 0; ks < n_signed; ++ks)
         cf->supports[(pa * params->n_subbands + sb) * n_signed + ks] = support_of_plane(cf->p, ks);
+  if (params->separable && params->cf_dtype == AWG_CF_FP32) {
+    s = build_separable(cf, st);
+    if (s == AWG_OK) {
+      *out = (awg_cf_set)cf;
+      return AWG_OK;
+    }
+    if (s != AWG_ERR_UNSUPPORTED) { free_cf(cf); return s; }
+    cf->separable = 0;   // some CF is not an outer product: keep full tables
+  }
   s = alloc_cf(cf, st);
   if (s != AWG_OK) { free_cf(cf); return s; }
   // Build the non-negative planes (the others are their conjugate point reflections) in batches
@@ -310,11 +397,12 @@ awg_status cf_set_destroy(awg_cf_set h) {
   return AWG_OK;
 }
 
-awg_status cf_set_info(awg_cf_set h, int32_t* n_cf, int64_t* n_values) {
+awg_status cf_set_info(awg_cf_set h, int32_t* n_cf, int64_t* n_values, int32_t* separable) {
   if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
   CfSetImpl* cf = (CfSetImpl*)h;
   if (n_cf) *n_cf = cf->n_cf;
   if (n_values) *n_values = cf->n_values;
+  if (separable) *separable = cf->separable;
   return AWG_OK;
 }
 
@@ -330,6 +418,25 @@ awg_status cf_set_copy_table(awg_cf_set h, int32_t ci, float* out) {
   CfSetImpl* cf = (CfSetImpl*)h;
   if (ci < 0 || ci >= cf->n_cf) return set_error(AWG_ERR_INVALID_ARG, "cf index out of range");
   const int64_t nv = (int64_t)(cf->p.oversampling + 1) * (cf->p.oversampling + 1) * cf->supports[ci] * cf->supports[ci];
+  if (cf->separable) {
+    const int OS = cf->p.oversampling, S = cf->supports[ci];
+    const int64_t q = (int64_t)(OS + 1) * S;
+    std::vector<float> f((size_t)4 * q);
+    AWG_CUDA_TRY(cudaMemcpy(f.data(), (float*)cf->d_sep + 2 * cf->sep_offsets[ci], 16 * q, cudaMemcpyDeviceToHost));
+    const float* fx = f.data();
+    const float* fy = f.data() + 2 * q;
+    for (int oy = 0; oy <= OS; ++oy)
+      for (int ox = 0; ox <= OS; ++ox)
+        for (int ty = 0; ty < S; ++ty)
+          for (int tx = 0; tx < S; ++tx) {
+            const float gr = fy[2 * (oy * S + ty)], gi = fy[2 * (oy * S + ty) + 1];
+            const float fr = fx[2 * (ox * S + tx)], fi = fx[2 * (ox * S + tx) + 1];
+            const size_t o = ((((size_t)oy * (OS + 1) + ox) * S + ty) * S + tx) * 2;
+            out[o] = gr * fr - gi * fi;
+            out[o + 1] = gr * fi + gi * fr;
+          }
+    return AWG_OK;
+  }
   if (cf->p.cf_dtype == AWG_CF_BF16) {
     std::vector<uint16_t> h16((size_t)2 * nv);
     AWG_CUDA_TRY(cudaMemcpy(h16.data(), (uint16_t*)cf->d_data + 2 * cf->offsets[ci], 4 * nv, cudaMemcpyDeviceToHost));

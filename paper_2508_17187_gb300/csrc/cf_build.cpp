@@ -232,4 +232,63 @@ void build_cf_table(const awg_cf_params& p, const double* pa_centers, const doub
   }
 }
 
+bool factor_rank1(const std::vector<double>& tab, int S, int OS, double tol, std::vector<double>& fx,
+                  std::vector<double>& fy) {
+  // The table seen as a Q x Q matrix C[(oy, ty)][(ox, tx)], Q = (OS + 1) S.  A separable CF
+  // c(du, dv) = g(dv) f(du) makes C = g f^T; alternating least squares from the strongest column
+  // finds g and f, and the fit is accepted when max |C - g f^T| <= tol max |C|.
+  const int Q = (OS + 1) * S;
+  auto at = [&](int qy, int qx) {
+    const int oy = qy / S, ty = qy - oy * S, ox = qx / S, tx = qx - ox * S;
+    const size_t i = ((((size_t)oy * (OS + 1) + ox) * S + ty) * S + tx) * 2;
+    return cd(tab[i], tab[i + 1]);
+  };
+  double cmax = 0.0;
+  int jbest = 0;
+  for (int qy = 0; qy < Q; ++qy)
+    for (int qx = 0; qx < Q; ++qx) {
+      const double a = std::abs(at(qy, qx));
+      if (a > cmax) { cmax = a; jbest = qx; }
+    }
+  if (cmax == 0.0) return false;
+  std::vector<cd> g(Q), f(Q);
+  for (int qy = 0; qy < Q; ++qy) g[qy] = at(qy, jbest);
+  for (int it = 0; it < 4; ++it) {
+    double gg = 0.0;
+    for (const cd& v : g) gg += std::norm(v);
+    for (int qx = 0; qx < Q; ++qx) {
+      cd acc = 0.0;
+      for (int qy = 0; qy < Q; ++qy) acc += std::conj(g[qy]) * at(qy, qx);
+      f[qx] = acc / gg;
+    }
+    double ff = 0.0;
+    for (const cd& v : f) ff += std::norm(v);
+    for (int qy = 0; qy < Q; ++qy) {
+      cd acc = 0.0;
+      for (int qx = 0; qx < Q; ++qx) acc += at(qy, qx) * std::conj(f[qx]);
+      g[qy] = acc / ff;
+    }
+  }
+  // balance the two factors' magnitudes
+  double gm = 0.0, fm = 0.0;
+  for (const cd& v : g) gm = std::fmax(gm, std::abs(v));
+  for (const cd& v : f) fm = std::fmax(fm, std::abs(v));
+  const double sc = std::sqrt(fm / gm);
+  for (cd& v : g) v *= sc;
+  for (cd& v : f) v /= sc;
+  double res = 0.0;
+  for (int qy = 0; qy < Q; ++qy)
+    for (int qx = 0; qx < Q; ++qx) res = std::fmax(res, std::abs(at(qy, qx) - g[qy] * f[qx]));
+  if (res > tol * cmax) return false;
+  fx.resize(2 * (size_t)Q);
+  fy.resize(2 * (size_t)Q);
+  for (int q = 0; q < Q; ++q) {
+    fx[2 * q] = f[q].real();
+    fx[2 * q + 1] = f[q].imag();
+    fy[2 * q] = g[q].real();
+    fy[2 * q + 1] = g[q].imag();
+  }
+  return true;
+}
+
 }  // namespace awg

@@ -2,7 +2,7 @@
 // samples after degridding, and the taper normalisation kernel (grid_normalize).
 #include <cuda_runtime.h>
 
-#include "resample.cuh"
+#include "resample_sep.cuh"
 
 namespace awg {
 
@@ -10,6 +10,8 @@ AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_GRID, false)
 AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_GRID, true)
 AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_DEGRID, false)
 AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_DEGRID, true)
+AWG_FOR_SEP_CLASSES_AND_POLS(AWG_DECLARE_GRID_SEP)
+AWG_FOR_SEP_CLASSES_AND_POLS(AWG_DECLARE_DEGRID_SEP)
 
 namespace {
 
@@ -32,6 +34,22 @@ awg_status grid_class(int c, int P, const GridArgs& a, int sms, cudaStream_t st)
   AWG_FOR_CLASSES_AND_POLS(AWG_CASE, BF16)
 #undef AWG_CASE
   return set_error(AWG_ERR_UNSUPPORTED, "no gridding kernel for this class / pol count");
+}
+
+awg_status grid_class_sep(int c, int P, const GridArgs& a, int sms, cudaStream_t st) {
+#define AWG_CASE(C, PP) \
+  if (c == C && P == PP) return run_grid_sep<C, PP>(a, sms, st);
+  AWG_FOR_SEP_CLASSES_AND_POLS(AWG_CASE)
+#undef AWG_CASE
+  return set_error(AWG_ERR_UNSUPPORTED, "no separable gridding kernel for this class / pol count");
+}
+
+awg_status degrid_class_sep(int c, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+#define AWG_CASE(C, PP) \
+  if (c == C && P == PP) return run_degrid_sep<C, PP>(a, sms, st);
+  AWG_FOR_SEP_CLASSES_AND_POLS(AWG_CASE)
+#undef AWG_CASE
+  return set_error(AWG_ERR_UNSUPPORTED, "no separable degridding kernel for this class / pol count");
 }
 
 template <bool BF16>
@@ -100,12 +118,16 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   a.grid = (float*)grid;
   a.grid_lo = (float*)grid_lo;
   a.sumwt = sumwt;
+  a.sep = (const float*)cf->d_sep;
+  a.sep_off = cf->d_sep_off;
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kNumClasses, st));
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
   for (int c = kNumClasses - 1; c >= 0; --c) {   // largest supports first
     if (!class_present(cf, c)) continue;
-    awg_status s = bf16 ? grid_class<true>(c, P, a, sms, st) : grid_class<false>(c, P, a, sms, st);
+    awg_status s = cf->separable ? grid_class_sep(c, P, a, sms, st)
+                   : bf16        ? grid_class<true>(c, P, a, sms, st)
+                                 : grid_class<false>(c, P, a, sms, st);
     if (s != AWG_OK) return s;
   }
   return AWG_OK;
@@ -133,12 +155,16 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   a.freq = pl->d_freq;
   a.grid = (const float*)grid;
   a.vis_out = (float*)vis_out;
+  a.sep = (const float*)cf->d_sep;
+  a.sep_off = cf->d_sep_off;
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kNumClasses, st));
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
   for (int c = kNumClasses - 1; c >= 0; --c) {
     if (!class_present(cf, c)) continue;
-    awg_status s = bf16 ? degrid_class<true>(c, P, a, sms, st) : degrid_class<false>(c, P, a, sms, st);
+    awg_status s = cf->separable ? degrid_class_sep(c, P, a, sms, st)
+                   : bf16        ? degrid_class<true>(c, P, a, sms, st)
+                                 : degrid_class<false>(c, P, a, sms, st);
     if (s != AWG_OK) return s;
   }
   k_zero_dropped<<<sms * 4, 256, 0, st>>>(pl->d_drop, pl->d_counters, (float*)vis_out, P);

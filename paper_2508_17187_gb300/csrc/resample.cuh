@@ -43,6 +43,8 @@ struct GridArgs {
   float* grid;           // c64 [N][N][P] (or complex128 with AWG_GRID_FP64)
   float* grid_lo;        // c64 [N][N][P] with AWG_GRID_KAHAN
   double* sumwt;         // [P]
+  const float* sep;      // separable CF factors (c64), or NULL
+  const int64_t* sep_off;
 };
 
 struct DegridArgs {
@@ -58,6 +60,8 @@ struct DegridArgs {
   const double* freq;
   const float* grid;     // c64 [N][N][P]
   float* vis_out;        // c64 [n][P]
+  const float* sep;      // separable CF factors (c64), or NULL
+  const int64_t* sep_off;
 };
 
 template <bool BF16>

@@ -15,7 +15,7 @@ def oracle_params(wl, **over) -> ocf.CFParams:
     return ocf.CFParams(**p)
 
 
-def library_params(op: ocf.CFParams, cf_dtype: int = 0) -> dict:
+def library_params(op: ocf.CFParams, cf_dtype: int = 0, separable: bool = True) -> dict:
     return dict(grid_n=op.grid_n, cell_rad=op.cell_rad, oversampling=op.oversampling, ps_support=op.ps_support,
                 use_ps=op.use_ps, use_w=op.use_w, n_wplanes=op.n_wplanes, w_max_lambda=op.w_max_lambda,
                 use_a=op.use_a, n_pa_bins=op.n_pa_bins,
@@ -23,7 +23,7 @@ def library_params(op: ocf.CFParams, cf_dtype: int = 0) -> dict:
                 n_subbands=op.n_subbands,
                 subband_freq_hz=(np.asarray(op.subband_freq_hz, dtype=np.float64) if op.subband_freq_hz is not None else None),
                 max_support=op.max_support, dish_diameter_m=op.dish_diameter_m, ellipticity=op.ellipticity,
-                cf_dtype=cf_dtype)
+                cf_dtype=cf_dtype, separable=separable)
 
 
 def rel_rms(a, b) -> float:

@@ -41,10 +41,10 @@ def _dev(a, dtype=None):
 
 
 def _run_library(awg, op, uvw, freq, vis, wt, pa_bin=None, chan_sb=None, cf=None, phase_shift=None, flags=0,
-                 cf_dtype=0):
+                 cf_dtype=0, separable=True):
     """Plan + grid + degrid(grid) through the C ABI; returns host arrays."""
     if cf is None:
-        cf = awg.cf_set_create(**library_params(op, cf_dtype))
+        cf = awg.cf_set_create(**library_params(op, cf_dtype, separable))
     R, C = uvw.shape[0], freq.shape[0]
     P = vis.shape[-1]
     N = op.grid_n
@@ -80,8 +80,9 @@ def _oracle(op, uvw, freq, vis, wt, grid_for_degrid, pa_bin=None, chan_sb=None, 
 
 # ------------------------------------------------------------------------------------------ CF tables
 
+@pytest.mark.parametrize("separable", [True, False])
 @pytest.mark.parametrize("mode", ["ps", "wproj", "awproj"])
-def test_cf_tables_match_oracle(awg, mode):
+def test_cf_tables_match_oracle(awg, mode, separable):
     wl = synth.make_workload("standard", n_int=4, with_vis=False)
     over = dict(grid_n=256, cell_rad=2e-5, oversampling=6, max_support=24)
     if mode != "ps":
@@ -90,7 +91,9 @@ def test_cf_tables_match_oracle(awg, mode):
         over.update(use_a=True, n_pa_bins=2, pa_bin_centers=[0.3, -0.9], n_subbands=2,
                     subband_freq_hz=[2.2e9, 3.6e9])
     op = oracle_params(wl, **over)
-    cf = awg.cf_set_create(**library_params(op))
+    cf = awg.cf_set_create(**library_params(op, separable=separable))
+    # PS and W CFs are outer products to FP32 precision; A-terms are not and keep full tables
+    assert cf.separable == (separable and mode != "awproj")
     sup = cf.supports()
     assert np.array_equal(sup, ocf.supports(op))
     for ci in range(op.n_cf):
@@ -99,8 +102,10 @@ def test_cf_tables_match_oracle(awg, mode):
         ref = ocf.cf_table(op, pa, sb, ks)
         got = cf.copy_table(ci)
         assert got.shape == ref.shape
-        # FP64 build rounded once to FP32; two different FFT/DFT evaluations of one definition
-        assert np.abs(got - ref).max() <= 2e-7 * np.abs(ref).max() + 1e-9, (mode, ci)
+        # FP64 build rounded once to FP32 (or two FP32 factors and their FP32 product); two
+        # different FFT / DFT evaluations of one definition
+        tol = 3e-7 if cf.separable else 2e-7
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max() + 1e-9, (mode, ci)
 
 
 # ------------------------------------------------------------------------------------------ exact pins
@@ -131,12 +136,13 @@ def test_delta_cf_is_exact_binning(awg):
 
 # ------------------------------------------------------------------------------------------ parity
 
-def test_standard_grid_degrid_parity(awg):
+@pytest.mark.parametrize("separable", [True, False])
+def test_standard_grid_degrid_parity(awg, separable):
     wl = synth.make_workload("standard", n_int=40)
     op = oracle_params(wl)
     vis = wl.vis.reshape(-1, 1)
     wt = wl.weight.reshape(-1, 1)
-    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt)
+    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, separable=separable)
     orc = _oracle(op, wl.uvw_m, wl.freq_hz, vis, wt, res["grid_used"])
     assert res["stats"][0] == int(orc["idx"].valid.sum())
     assert rel_rms(res["grid"], orc["grid"]) < 1e-5
@@ -147,14 +153,16 @@ def test_standard_grid_degrid_parity(awg):
     assert rel_rms(res["vis"], orc["vis"]) < 1e-5
 
 
-def test_wproj_parity_several_tiles_ragged(awg):
+@pytest.mark.parametrize("separable", [True, False])
+def test_wproj_parity_several_tiles_ragged(awg, separable):
     """W-projection, 4 pols, OS 20, supports 8..64 over 8 signed planes: every CF class, many tiles,
-    ragged work items."""
+    ragged work items; separable (factor) and full-table CF storage."""
     wl = synth.make_workload("wproj", n_int=24, n_chan=8, grid_n=1024)
     op = oracle_params(wl, n_wplanes=8)
     vis = wl.vis.reshape(-1, 4)
     wt = wl.weight.reshape(-1, 4)
-    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt)
+    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, separable=separable)
+    assert res["cf"].separable == separable
     orc = _oracle(op, wl.uvw_m, wl.freq_hz, vis, wt, res["grid_used"])
     assert res["stats"][0] == int(orc["idx"].valid.sum())
     assert res["stats"][1] == int((~orc["idx"].valid).sum())
@@ -231,27 +239,29 @@ def test_every_support_class_random_tables(awg, P):
     assert abs(a - b) <= 1e-5 * abs(a)
 
 
-def test_phase_shift_parity(awg):
+@pytest.mark.parametrize("separable", [True, False])
+def test_phase_shift_parity(awg, separable):
     """The phase-gradient term of Eq. CIJ: G multiplies by the phasor, D by its conjugate."""
     wl = synth.make_workload("standard", n_int=30)
     op = oracle_params(wl)
     shift = (40 * wl.cell_rad, -25 * wl.cell_rad)
     vis = wl.vis.reshape(-1, 1)
     wt = wl.weight.reshape(-1, 1)
-    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, phase_shift=shift)
+    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, phase_shift=shift, separable=separable)
     orc = _oracle(op, wl.uvw_m, wl.freq_hz, vis, wt, res["grid_used"], phase_shift=shift)
     assert rel_rms(res["grid"], orc["grid"]) < 2e-5
     assert rel_rms(res["vis"], orc["vis"]) < 2e-5
 
 
+@pytest.mark.parametrize("separable", [True, False])
 @pytest.mark.parametrize("flags", ["kahan", "fp64"])
-def test_precision_variants(awg, flags):
+def test_precision_variants(awg, flags, separable):
     wl = synth.make_workload("wproj", n_int=16, n_chan=6, grid_n=512, n_wplanes=6, max_support=32)
     op = oracle_params(wl)
     vis = wl.vis.reshape(-1, 4)
     wt = wl.weight.reshape(-1, 4)
     f = awg.AWG_GRID_KAHAN if flags == "kahan" else awg.AWG_GRID_FP64
-    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, flags=f)
+    res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, flags=f, separable=separable)
     plain = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, cf=res["cf"])
     orc = _oracle(op, wl.uvw_m, wl.freq_hz, vis, wt, res["grid_used"])
     e_var = rel_rms(res["grid"], orc["grid"])
@@ -315,3 +325,38 @@ def test_argument_errors(awg):
         awg.cf_set_create(**library_params(oracle_params(wl, max_support=65)))
     with pytest.raises(awg.AwgError, match="INVALID_ARG"):
         awg.cf_set_create(**library_params(oracle_params(wl, use_w=True, n_wplanes=1)))
+
+
+def test_plain_fp64_baseline_parity(awg):
+    """The plain FP64 per-channel baseline matches the oracle (FP64 sums of the FP32 tables)."""
+    import ctypes
+    from paper_2508_17187_gb300 import _lib
+    lib = _lib.load()
+    wl = synth.make_workload("wproj", n_int=10, n_chan=4, grid_n=512, n_wplanes=6, max_support=32)
+    op = oracle_params(wl)
+    cf = awg.cf_set_create(**library_params(op, separable=False))
+    N, P, R, C = wl.grid_n, wl.n_pol, wl.n_rows, wl.n_chan
+    uvw = _dev(wl.uvw_m)
+    vis = _dev(wl.vis)
+    wt = _dev(wl.weight)
+    freq = np.ascontiguousarray(wl.freq_hz)
+    g = torch.zeros((N, N, P), dtype=torch.complex128, device="cuda")
+    sw = torch.zeros(P, dtype=torch.float64, device="cuda")
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    fp = freq.ctypes.data_as(ctypes.c_void_p)
+    assert lib.grid_visibilities_plain_fp64(cf.handle, vp(uvw), R, fp, C, 0, C, None, None, vp(vis), vp(wt), P,
+                                            vp(g), vp(sw), st) == 0
+    out = torch.zeros((R, C, P), dtype=torch.complex64, device="cuda")
+    assert lib.degrid_visibilities_plain_fp64(cf.handle, vp(uvw), R, fp, C, 0, C, None, None, vp(g), vp(out), P,
+                                              st) == 0
+    torch.cuda.synchronize()
+    tables = {ci: cf.copy_table(ci).astype(np.complex128) for ci in range(op.n_cf)}
+    orc = _oracle(op, wl.uvw_m, wl.freq_hz, wl.vis.reshape(-1, P), wl.weight.reshape(-1, P), g.cpu().numpy(),
+                  tables=tables)
+    assert rel_rms(g.cpu().numpy(), orc["grid"]) < 1e-12
+    assert np.allclose(sw.cpu().numpy(), orc["sumwt"], rtol=1e-12)
+    assert rel_rms(out.cpu().numpy().reshape(-1, P), orc["vis"]) < 1e-6
+    sep = awg.cf_set_create(**library_params(op))
+    assert lib.grid_visibilities_plain_fp64(sep.handle, vp(uvw), R, fp, C, 0, C, None, None, vp(vis), vp(wt), P,
+                                            vp(g), vp(sw), st) == 2
