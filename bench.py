@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-every", type=int, default=40, help="oracle sample: every k-th integration")
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="CF storage / accumulation variants against the FP64 oracle (one JSON line each)")
     return ap.parse_args()
 
 
@@ -172,11 +174,18 @@ def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    wl = rank_workload(1, 0, args.n_int or synth.CONFIGS[CONFIG]["n_int"], "cpu")
+    # only the sampled integrations get visibilities (CPU DFT of the sky), the rest is never read
+    full = rank_workload(1, 0, args.n_int or synth.CONFIGS[CONFIG]["n_int"], "cpu", with_vis=False)
+    ints = np.arange(0, full.n_int, args.cpu_sample_every)
+    rows = np.concatenate([np.arange(t * full.n_bl, (t + 1) * full.n_bl) for t in ints])
+    wl = dataclasses.replace(full, uvw_m=full.uvw_m[rows].copy(), pa_rad=full.pa_rad[rows].copy(),
+                             pa_bin=full.pa_bin[rows].copy(), n_int=len(ints))
+    synth.fill_visibilities(wl, device="cpu")
     times = []
     info = None
     for i in range(args.warmup + args.steps):
-        info = run_cpu_baseline(wl, args.cpu_sample_every)
+        info = run_cpu_baseline(wl, 1)
+        info["sample"] = info["sample"].replace("every 1th integration", f"every {args.cpu_sample_every}th integration")
         if i >= args.warmup:
             times.append(info["seconds"])
     per_step = statistics.mean(times)
@@ -194,10 +203,123 @@ def reference_arm(args):
     return 0
 
 
+def precision_sweep(args):
+    """Per-variant dirty-image and degridding error against the FP64 oracle, and throughput.
+
+    Workload: the W-projection configuration with `--n-int` integrations (default 100, 9M
+    visibilities) so that the oracle's FP64 gridding of every sample takes seconds.  Image error:
+    relative RMS of the dirty image over the inner half of the field (where the PS taper is above
+    0.25); degridding error: relative RMS of D applied to one common model grid."""
+    import ctypes
+
+    import torch
+
+    import paper_2508_17187_gb300 as awg
+    from paper_2508_17187_gb300 import _lib
+    from oracle import cf as ocf
+    from oracle import image as oimage
+    from oracle import index as oindex
+    from oracle import ops as oops
+    lib = _lib.load()
+    n_int = args.n_int or 100
+    wl = rank_workload(1, 0, n_int, "cuda")
+    N, P, R, C = wl.grid_n, wl.n_pol, wl.n_rows, wl.n_chan
+    op = ocf.CFParams(grid_n=N, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support,
+                      use_w=True, n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda, max_support=wl.max_support)
+    idx = oindex.sample_index(op, wl.uvw_m, wl.freq_hz)
+    buf, off, _ = ocf.flatten_cf_set(op, ocf.cf_set(op, which=set(np.unique(idx.cf[idx.valid]).tolist())))
+    vis_h = wl.vis.cpu().numpy().reshape(-1, P)
+    wt_h = wl.weight.cpu().numpy().reshape(-1, P)
+    g_o, sw_o = oops.grid(idx, buf, off, op.oversampling, N, vis_h, wt_h)
+    img_o = oimage.dirty_image(g_o, sw_o, wl.ps_support)[N // 4:3 * N // 4, N // 4:3 * N // 4]
+    rng = np.random.default_rng(7)
+    model = np.zeros((N, N, P))
+    pts = rng.integers(N // 4, 3 * N // 4, (50, 2))
+    model[pts[:, 0], pts[:, 1], :] = rng.uniform(0.1, 1.0, (50, 1))
+    mgrid = oimage.model_to_grid(model, wl.ps_support)
+    d_o = oops.degrid(idx, buf, off, op.oversampling, mgrid)
+    mgrid_d = torch.as_tensor(mgrid.astype(np.complex64)).cuda()
+    uvw = torch.as_tensor(wl.uvw_m).cuda()
+    freq = torch.as_tensor(wl.freq_hz).cuda()
+    base = dict(grid_n=N, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support, use_w=True,
+                n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda, max_support=wl.max_support)
+    variants = [("cf fp32 separable, grid fp32", dict(separable=True), 0),
+                ("cf fp32 full tables, grid fp32", dict(separable=False), 0),
+                ("cf bf16 full tables, grid fp32", dict(separable=False, cf_dtype=awg.AWG_CF_BF16), 0),
+                ("cf fp32 separable, grid fp32 + Kahan flush", dict(separable=True), awg.AWG_GRID_KAHAN),
+                ("cf fp32 separable, grid fp64 flush", dict(separable=True), awg.AWG_GRID_FP64)]
+    n_vis = R * C * P
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for name, kw, flags in variants:
+        cf = awg.cf_set_create(**base, **kw)
+        plan = awg.plan_create(cf, uvw, freq)
+        dt = torch.complex128 if flags & awg.AWG_GRID_FP64 else torch.complex64
+        g = torch.zeros((N, N, P), dtype=dt, device="cuda")
+        glo = torch.zeros((N, N, P), dtype=torch.complex64, device="cuda") if flags & awg.AWG_GRID_KAHAN else None
+        sw = torch.zeros(P, dtype=torch.float64, device="cuda")
+
+        def do_grid():
+            g.zero_()
+            sw.zero_()
+            if glo is not None:
+                glo.zero_()
+            awg.grid_visibilities(cf, plan, wl.vis, wl.weight, g, sw, grid_lo=glo, flags=flags)
+        ms = timed(do_grid)
+        gh = g.to(torch.complex128) + (glo.to(torch.complex128) if glo is not None else 0)
+        img = oimage.dirty_image(gh.cpu().numpy(), sw.cpu().numpy(), wl.ps_support)[N // 4:3 * N // 4, N // 4:3 * N // 4]
+        err_img = float(np.linalg.norm(img - img_o) / np.linalg.norm(img_o))
+        out = torch.empty_like(wl.vis)
+        ms_d = timed(lambda: awg.degrid_visibilities(cf, plan, mgrid_d, out))
+        err_d = float(np.linalg.norm(out.cpu().numpy().reshape(-1, P) - d_o) / np.linalg.norm(d_o))
+        print(json.dumps({"variant": name, "image_rel_rms": err_img, "degrid_rel_rms": err_d,
+                          "grid_visibilities_per_s": n_vis / (ms / 1e3), "degrid_visibilities_per_s": n_vis / (ms_d / 1e3),
+                          "workload": f"W-projection, {n_int} integrations x 351 baselines x {C} channels x {P} pols"}),
+              flush=True)
+    # the plain FP64 per-channel launch on the same data
+    cf = awg.cf_set_create(**base, separable=False)
+    g64 = torch.zeros((N, N, P), dtype=torch.complex128, device="cuda")
+    sw = torch.zeros(P, dtype=torch.float64, device="cuda")
+    fr = np.ascontiguousarray(wl.freq_hz)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def plain():
+        g64.zero_()
+        sw.zero_()
+        rc = lib.grid_visibilities_plain_fp64(cf.handle, vp(uvw), R, fr.ctypes.data_as(ctypes.c_void_p), C, 0, C,
+                                              None, None, vp(wl.vis), vp(wl.weight), P, vp(g64), vp(sw), st)
+        assert rc == 0, lib.awg_last_error()
+    ms = timed(plain, reps=1)
+    img = oimage.dirty_image(g64.cpu().numpy(), sw.cpu().numpy(), wl.ps_support)[N // 4:3 * N // 4, N // 4:3 * N // 4]
+    out = torch.empty_like(wl.vis)
+    g64.copy_(mgrid_d.to(torch.complex128))
+    ms_d = timed(lambda: lib.degrid_visibilities_plain_fp64(cf.handle, vp(uvw), R, fr.ctypes.data_as(ctypes.c_void_p),
+                                                            C, 0, C, None, None, vp(g64), vp(out), P, st), reps=1)
+    err_d = float(np.linalg.norm(out.cpu().numpy().reshape(-1, P) - d_o) / np.linalg.norm(d_o))
+    print(json.dumps({"variant": "plain FP64 per-channel launches (baseline)",
+                      "image_rel_rms": float(np.linalg.norm(img - img_o) / np.linalg.norm(img_o)),
+                      "degrid_rel_rms": err_d, "grid_visibilities_per_s": n_vis / (ms / 1e3),
+                      "degrid_visibilities_per_s": n_vis / (ms_d / 1e3)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.precision_sweep:
+        return precision_sweep(args)
     import torch
     import torch.distributed as dist
 

@@ -8,6 +8,7 @@
 // k_scatter : counting-sort scatter of the kept samples into bucket order.
 // k_items   : work items of at most kItemChunk samples per bucket; buckets are ordered by
 //             support, so the items of each kernel class form one contiguous range.
+// k_sort_items : samples of each item ordered by first-tap position (row-major).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -270,6 +271,49 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ key, const Samp
   }
 }
 
+// Orders the samples of every work item by first-tap position, row-major (y, then x), with a
+// bitonic sort of up to kItemChunk records in shared memory.  Consecutive samples then share
+// their first-tap row for long runs and move right along it, so the gridding and degridding
+// kernels recompute their row state only at row changes and a thread's pixels change rarely.
+__global__ void __launch_bounds__(kItemChunk) k_sort_items(const int32_t* __restrict__ n_items_ptr,
+                                                          const WorkItem* __restrict__ items, SampleRec* rec) {
+  __shared__ SampleRec s_rec[kItemChunk];
+  __shared__ unsigned s_key[kItemChunk];
+  __shared__ unsigned short s_idx[kItemChunk];
+  const int n_items = *n_items_ptr;
+  const int t = threadIdx.x;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const WorkItem wi = items[it];
+    if (t < wi.count) {
+      s_rec[t] = rec[wi.start + t];
+      s_key[t] = ((unsigned)s_rec[t].p0y << 16) | s_rec[t].p0x;
+    } else {
+      s_key[t] = 0xffffffffu;
+    }
+    s_idx[t] = (unsigned short)t;
+    __syncthreads();
+    for (int k = 2; k <= kItemChunk; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int ixj = t ^ j;
+        if (ixj > t) {
+          const bool up = (t & k) == 0;
+          const unsigned a = s_key[t], b = s_key[ixj];
+          if ((a > b) == up) {
+            s_key[t] = b;
+            s_key[ixj] = a;
+            const unsigned short ti = s_idx[t];
+            s_idx[t] = s_idx[ixj];
+            s_idx[ixj] = ti;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (t < wi.count) rec[wi.start + t] = s_rec[s_idx[t]];
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 // class_of_support is also used in device code above.
@@ -334,6 +378,9 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_bcount, pl->d_boff, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, st));
     const int blocks = (int)std::min<int64_t>((pl->n + 255) / 256, (int64_t)sms * 8);
     k_scatter<<<blocks, 256, 0, st>>>(pl->n, pl->d_key, pl->d_rec_tmp, pl->d_bcount, pl->d_rec);
+    AWG_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    k_sort_items<<<sms * 8, kItemChunk, 0, st>>>(pl->d_ioff + nb, pl->d_items, pl->d_rec);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   }

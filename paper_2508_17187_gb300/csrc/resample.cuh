@@ -113,20 +113,30 @@ __device__ __forceinline__ void flush_pixel(const GridArgs& a, size_t g, const f
     return;
   }
   float* dst = a.grid + 2 * g;
+  if (!(a.flags & AWG_GRID_KAHAN)) {
+    // plain flush: the old value is never read, so these compile to reductions (no return trip)
+    if constexpr (P == 1) {
+      atomicAdd(reinterpret_cast<float2*>(dst), v[0]);
+    } else {
+#pragma unroll
+      for (int h = 0; h < P / 2; ++h)
+        atomicAdd(reinterpret_cast<float4*>(dst + 4 * h),
+                  make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y));
+    }
+    return;
+  }
+  // compensated flush: TwoSum of the value the atomic saw and the added value
   if constexpr (P == 1) {
     const float2 old = atomicAdd(reinterpret_cast<float2*>(dst), v[0]);
-    if (a.flags & AWG_GRID_KAHAN) {
-      float s0 = old.x + v[0].x, s1 = old.y + v[0].y;
-      float b0 = s0 - old.x, b1 = s1 - old.y;
-      float2 e = make_float2((old.x - (s0 - b0)) + (v[0].x - b0), (old.y - (s1 - b1)) + (v[0].y - b1));
-      if (e.x != 0.f || e.y != 0.f) atomicAdd(reinterpret_cast<float2*>(a.grid_lo + 2 * g), e);
-    }
+    const float s0 = old.x + v[0].x, s1 = old.y + v[0].y;
+    const float b0 = s0 - old.x, b1 = s1 - old.y;
+    const float2 e = make_float2((old.x - (s0 - b0)) + (v[0].x - b0), (old.y - (s1 - b1)) + (v[0].y - b1));
+    if (e.x != 0.f || e.y != 0.f) atomicAdd(reinterpret_cast<float2*>(a.grid_lo + 2 * g), e);
   } else {
 #pragma unroll
-  for (int h = 0; h < P / 2; ++h) {
-    const float4 val = make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
-    const float4 old = atomicAdd(reinterpret_cast<float4*>(dst + 4 * h), val);
-    if (a.flags & AWG_GRID_KAHAN) {
+    for (int h = 0; h < P / 2; ++h) {
+      const float4 val = make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+      const float4 old = atomicAdd(reinterpret_cast<float4*>(dst + 4 * h), val);
       const float o[4] = {old.x, old.y, old.z, old.w};
       const float b[4] = {val.x, val.y, val.z, val.w};
       float e[4];
@@ -139,7 +149,6 @@ __device__ __forceinline__ void flush_pixel(const GridArgs& a, size_t g, const f
       if (e[0] != 0.f || e[1] != 0.f || e[2] != 0.f || e[3] != 0.f)
         atomicAdd(reinterpret_cast<float4*>(a.grid_lo + 2 * g + 4 * h), make_float4(e[0], e[1], e[2], e[3]));
     }
-  }
   }
 }
 

@@ -6,7 +6,8 @@
 // resample.cuh; the tap ownership is arranged so the factorisation also saves arithmetic:
 //
 // Thread t of NT owns column residue rx = t mod S and rows ry = t div S + k G, G = NT div S
-// (threads t >= G S idle).  Gridding: per sample the thread forms alpha_p = conj(fx[tx]) w V_p
+// (threads t >= G S idle).  The window is pol-planar (tile[p][pixel]) so that the threads of a
+// warp, which own consecutive columns, touch consecutive words.  Gridding: per sample the thread forms alpha_p = conj(fx[tx]) w V_p
 // once for its column and then adds conj(fy[ty]) alpha_p for each of its rows: 4 FFMA per tap
 // and pol, as with a full table, but the only per-tap load is fy[ty] from shared memory.
 // Registers accumulate until a residue's pixel changes (column change: all rows; row change:
@@ -20,8 +21,6 @@
 
 namespace awg {
 
-constexpr int kSepStage = 16;   // samples staged per chunk (their factor rows live in shared memory)
-
 // Rows per thread needed by any support of a class: max over S in (smin, smax] of ceil(S / (NT / S)).
 __host__ __device__ constexpr int sep_rows(int smin, int smax, int nt) {
   int r = 1;
@@ -33,26 +32,146 @@ __host__ __device__ constexpr int sep_rows(int smin, int smax, int nt) {
   return r;
 }
 
+// Staged samples per chunk: the factor rows of a chunk live in shared memory, twice (the chunk
+// being computed and the one being fetched).
+__host__ __device__ constexpr int sep_stage(int smax) { return smax >= 56 ? 8 : 16; }
+
+// Shared-memory layout: the U x U window, then two slots of staged samples.
 template <int SMAX, int TILE, int P>
 struct SepLayout {
+  static constexpr int ST = sep_stage(SMAX);
   static constexpr int UMAX = TILE + SMAX - 1;
-  static constexpr size_t tile_bytes = (size_t)UMAX * UMAX * P * sizeof(float2);
-  static constexpr size_t f_bytes = (size_t)kSepStage * 2 * SMAX * sizeof(float2);
-  static constexpr size_t a_bytes = (size_t)kSepStage * P * sizeof(float2);
-  static constexpr size_t bytes = tile_bytes + f_bytes + a_bytes + kSepStage * (2 * sizeof(long long) + 4 * sizeof(int));
+  // rounded up so that each slot starts 128-byte aligned (16-byte cp.async destinations)
+  static constexpr size_t tile_bytes = ((size_t)UMAX * UMAX * P * sizeof(float2) + 127) & ~(size_t)127;
+  // per slot
+  static constexpr size_t f_off = 0;                                             // float2 [ST][2][SMAX]
+  static constexpr size_t v_off = f_off + (size_t)ST * 2 * SMAX * sizeof(float2);  // float2 [ST][P]
+  static constexpr size_t a_off = v_off + (size_t)ST * P * sizeof(float2);        // float2 [ST][P]
+  static constexpr size_t w_off = a_off + (size_t)ST * P * sizeof(float2);        // float [ST][P] (padded)
+  static constexpr size_t r_off = w_off + (((size_t)ST * P * sizeof(float) + 15) & ~(size_t)15);  // SampleRec [ST]
+  static constexpr size_t x_off = r_off + (size_t)ST * sizeof(SampleRec);          // long long [ST] fx offsets
+  static constexpr size_t y_off = x_off + (size_t)ST * sizeof(long long);          // long long [ST] fy offsets
+  static constexpr size_t ph_off = y_off + (size_t)ST * sizeof(long long);         // float2 [ST]
+  static constexpr size_t k_off = ph_off + (size_t)ST * sizeof(float2);            // int [ST] packed offsets
+  static constexpr size_t s_off = k_off + (size_t)ST * sizeof(int);                // int [ST] sample index
+  static constexpr size_t slot_bytes = (s_off + (size_t)ST * sizeof(int) + 127) & ~(size_t)127;
+  static constexpr size_t bytes = tile_bytes + 2 * slot_bytes;
+};
+
+template <int SMAX, int TILE, int P>
+struct SepSlot {
+  using L = SepLayout<SMAX, TILE, P>;
+  unsigned char* base;
+  __device__ SepSlot(unsigned char* smem, int slot) : base(smem + L::tile_bytes + slot * L::slot_bytes) {}
+  __device__ float2* f() const { return reinterpret_cast<float2*>(base + L::f_off); }
+  __device__ float2* v() const { return reinterpret_cast<float2*>(base + L::v_off); }
+  __device__ float2* a() const { return reinterpret_cast<float2*>(base + L::a_off); }
+  __device__ float* w() const { return reinterpret_cast<float*>(base + L::w_off); }
+  __device__ SampleRec* rec() const { return reinterpret_cast<SampleRec*>(base + L::r_off); }
+  __device__ long long* fxo() const { return reinterpret_cast<long long*>(base + L::x_off); }
+  __device__ long long* fyo() const { return reinterpret_cast<long long*>(base + L::y_off); }
+  __device__ float2* ph() const { return reinterpret_cast<float2*>(base + L::ph_off); }
+  __device__ int* pack() const { return reinterpret_cast<int*>(base + L::k_off); }
+  __device__ int* src() const { return reinterpret_cast<int*>(base + L::s_off); }
+};
+
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src));
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Records of chunk c into a slot (threads < nst, one 16-byte copy each).
+template <int SMAX, int TILE, int P>
+__device__ __forceinline__ void stage_recs(const SampleRec* rec, int start, int nst, const SepSlot<SMAX, TILE, P>& sl) {
+  if ((int)threadIdx.x < nst) cp_async(sl.rec() + threadIdx.x, rec + start + threadIdx.x, 16);
+}
+
+// From staged records: packed window offsets, factor-row offsets, sample index, phasor.
+template <int SMAX, int TILE, int P, class Args>
+__device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, int Y0, const SepSlot<SMAX, TILE, P>& sl) {
+  const int j = threadIdx.x;
+  if (j < nst) {
+    const SampleRec rc = sl.rec()[j];
+    const long long base = a.sep_off[rc.cf];
+    sl.fxo()[j] = base + (long long)rc.ox * S;
+    sl.fyo()[j] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
+    sl.pack()[j] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
+    sl.src()[j] = rc.src;
+    sl.ph()[j] = a.has_phase ? sample_phasor(a.uvw, a.freq, a.C, rc.src, a.dl, a.dm, a.dn) : make_float2(1.f, 0.f);
+  }
+}
+
+// Asynchronous copies of a chunk's factor rows (all threads) and, when vis != NULL, its
+// visibilities and weights (threads < nst).
+template <int SMAX, int TILE, int P, int NT>
+__device__ __forceinline__ void stage_payload(const float* sep, const float* vis, const float* weight, int nst, int S,
+                                              const SepSlot<SMAX, TILE, P>& sl) {
+  const float2* sep2 = reinterpret_cast<const float2*>(sep);
+  const long long* fxo = sl.fxo();
+  const long long* fyo = sl.fyo();
+  float2* f = sl.f();
+  for (int i = threadIdx.x; i < nst * 2 * S; i += NT) {
+    const int j = i / (2 * S), r = i - j * 2 * S;
+    const bool isx = r < S;
+    const long long srcidx = isx ? fxo[j] + r : fyo[j] + (r - S);
+    cp_async(f + (j * 2 + (isx ? 0 : 1)) * SMAX + (isx ? r : r - S), sep2 + srcidx, 8);
+  }
+  if (vis != nullptr && (int)threadIdx.x < nst) {
+    const int j = threadIdx.x;
+    const size_t s = (size_t)sl.src()[j];
+    const float* vp = vis + s * 2 * P;
+    const float* wp = weight + s * P;
+    if (P == 4) {
+      cp_async(sl.v() + j * P, vp, 16);
+      cp_async(sl.v() + j * P + 2, vp + 4, 16);
+      cp_async(sl.w() + j * P, wp, 16);
+    } else if (P == 2) {
+      cp_async(sl.v() + j * P, vp, 16);
+      cp_async(sl.w() + j * P, wp, 8);
+    } else {
+      cp_async(sl.v() + j * P, vp, 8);
+      cp_async(sl.w() + j * P, wp, 4);
+    }
+  }
+}
+
+// Per-thread row state of the separable kernels.  The rows a thread owns are ry0 + k G (k < R,
+// valid while below S); for a sample whose first tap is (p0x, p0y) the row residue ry touches
+// window row dy + ((ry - p0y) mod S).  Samples of an item are sorted row-major, so that state is
+// recomputed only when p0y changes (a test that is uniform across the CTA).
+template <int R>
+struct RowState {
+  int ty[R];   // tap row of each owned row for the current p0y
+  int Y[R];    // window row of each owned row for the current p0y
+  __device__ __forceinline__ void update(int ry0, int G, int S, int dy, int my, unsigned vmask) {
+    int ty0 = ry0 - my;
+    ty0 += (ty0 < 0) ? S : 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (vmask & (1u << k)) {
+        int t = ty0 + k * G;
+        t -= (t >= S) ? S : 0;
+        ty[k] = t;
+        Y[k] = dy + t;
+      }
+    }
+  }
 };
 
 template <int SMIN, int SMAX, int NT, int TILE, int P>
 __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
-  using L = SepLayout<SMAX, TILE, P>;
+  constexpr int ST = sep_stage(SMAX);
+  using Slot = SepSlot<SMAX, TILE, P>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
-  float2* s_f = reinterpret_cast<float2*>(smem + L::tile_bytes);              // [stage][2][SMAX]
-  float2* s_a = reinterpret_cast<float2*>(smem + L::tile_bytes + L::f_bytes);  // [stage][P]
-  long long* s_fxo = reinterpret_cast<long long*>(smem + L::tile_bytes + L::f_bytes + L::a_bytes);
-  long long* s_fyo = s_fxo + kSepStage;
-  int* s_pack = reinterpret_cast<int*>(s_fyo + kSepStage);
   __shared__ int s_item;
   __shared__ double s_wsum[NT / 32][P];
 
@@ -74,103 +193,106 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
     const int G = NT / S;
     const bool active = tid < G * S;
     const int rx = tid % S, ry0 = tid / S;
-    for (int i = tid; i < U * U * P; i += NT) tile[i] = make_float2(0.f, 0.f);
+    unsigned vmask = 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) vmask |= (ry0 + k * G < S) ? (1u << k) : 0u;
+    const int nch = (wi.count + ST - 1) / ST;
+    auto nst_of = [&](int c) { return min(ST, wi.count - c * ST); };
+    const int UU = U * U;   // the window is pol-planar: tile[p * UU + pixel]
+    for (int i = tid; i < UU * P; i += NT) tile[i] = make_float2(0.f, 0.f);
+    // prologue: records of chunks 0 and 1, derived data of chunks 0 and 1, payload of chunk 0
+    {
+      const Slot s0(smem, 0), s1(smem, 1);
+      stage_recs(a.rec, wi.start, nst_of(0), s0);
+      if (nch > 1) stage_recs(a.rec, wi.start + ST, nst_of(1), s1);
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncthreads();
+      derive(a, nst_of(0), S, X0, Y0, s0);
+      if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
+      __syncthreads();
+      stage_payload<SMAX, TILE, P, NT>(a.sep, a.vis, a.weight, nst_of(0), S, s0);
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncthreads();
+      if (tid < nst_of(0)) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const float wv = s0.w()[tid * P + p];
+          const float2 v = s0.v()[tid * P + p];
+          const float2 ph = s0.ph()[tid];
+          wsum[p] += (double)wv;
+          const float xr = wv * v.x, xi = wv * v.y;
+          s0.a()[tid * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
+        }
+      }
+      __syncthreads();
+    }
+
+    RowState<R> rs;
+    int prev_row = -1;
     int curX = -1;
     int curY[R];
     float2 acc[R][P];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       curY[k] = -1;
+      rs.ty[k] = 0;
+      rs.Y[k] = -1;
 #pragma unroll
       for (int p = 0; p < P; ++p) acc[k][p] = make_float2(0.f, 0.f);
     }
-    for (int c0 = 0; c0 < wi.count; c0 += kSepStage) {
-      const int nst = min(kSepStage, wi.count - c0);
-      __syncthreads();
-      if (tid < nst) {
-        const SampleRec rc = a.rec[wi.start + c0 + tid];
-        const float* vp = a.vis + (size_t)rc.src * 2 * P;
-        const float* wp = a.weight + (size_t)rc.src * P;
-        float2 v[P];
-        float wt[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          v[p] = __ldg(reinterpret_cast<const float2*>(vp) + p);
-          wt[p] = __ldg(wp + p);
-        }
-        float2 ph = make_float2(1.f, 0.f);
-        if (a.has_phase) ph = sample_phasor(a.uvw, a.freq, a.C, rc.src, a.dl, a.dm, a.dn);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          wsum[p] += (double)wt[p];
-          const float xr = wt[p] * v[p].x, xi = wt[p] * v[p].y;
-          s_a[tid * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
-        }
-        const long long base = a.sep_off[rc.cf];
-        s_fxo[tid] = base + (long long)rc.ox * S;
-        s_fyo[tid] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
-        s_pack[tid] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
-      }
-      __syncthreads();
-      for (int i = tid; i < nst * 2 * S; i += NT) {
-        const int j = i / (2 * S), r = i - j * 2 * S;
-        const long long src = r < S ? s_fxo[j] + r : s_fyo[j] + (r - S);
-        s_f[(j * 2 + (r < S ? 0 : 1)) * SMAX + (r < S ? r : r - S)] =
-            __ldg(reinterpret_cast<const float2*>(a.sep) + src);
-      }
-      __syncthreads();
+    for (int c = 0; c < nch; ++c) {
+      const Slot A(smem, c & 1), B(smem, (c & 1) ^ 1);
+      if (c + 1 < nch) stage_payload<SMAX, TILE, P, NT>(a.sep, a.vis, a.weight, nst_of(c + 1), S, B);
+      if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
+      cp_async_commit();
+      const int nst = nst_of(c);
       if (active) {
         for (int j = 0; j < nst; ++j) {
-          const int pk = s_pack[j];
-          const int dx = pk & 0xff, dy = (pk >> 8) & 0xff, mx = (pk >> 16) & 0xff, my = (pk >> 24) & 0xff;
+          const int pk = A.pack()[j];
+          const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
+          const int row = pk & 0xff00ff00;   // (dy, my): identical for the whole CTA
+          bool row_changed = false;
+          if (row != prev_row) {
+            prev_row = row;
+            rs.update(ry0, G, S, (pk >> 8) & 0xff, (pk >> 24) & 0xff, vmask);
+            row_changed = true;
+          }
           int tx = rx - mx;
           tx += (tx < 0) ? S : 0;
           const int X = dx + tx;
-          const float2 fxv = s_f[(j * 2) * SMAX + tx];
-          float2 al[P];
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const float2 av = s_a[j * P + p];
-            al[p] = make_float2(fxv.x * av.x + fxv.y * av.y, fxv.x * av.y - fxv.y * av.x);   // conj(fx) a
-          }
-          if (X != curX) {
+          if (X != curX || row_changed) {
+            const bool xchg = X != curX;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-              if (curY[k] >= 0) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                  float2* t = tile + (curY[k] * U + curX) * P + p;
-                  t->x += acc[k][p].x;
-                  t->y += acc[k][p].y;
-                  acc[k][p] = make_float2(0.f, 0.f);
-                }
-                curY[k] = -1;
-              }
-            }
-            curX = X;
-          }
-          int ty0 = ry0 - my;
-          ty0 += (ty0 < 0) ? S : 0;
-          const float2* fyrow = s_f + (j * 2 + 1) * SMAX;
-#pragma unroll
-          for (int k = 0; k < R; ++k) {
-            if (ry0 + k * G < S) {
-              int ty = ty0 + k * G;
-              ty -= (ty >= S) ? S : 0;
-              const int Y = dy + ty;
-              if (Y != curY[k]) {
+              if ((vmask & (1u << k)) && (xchg || rs.Y[k] != curY[k])) {
                 if (curY[k] >= 0) {
 #pragma unroll
                   for (int p = 0; p < P; ++p) {
-                    float2* t = tile + (curY[k] * U + curX) * P + p;
+                    float2* t = tile + p * UU + curY[k] * U + curX;
                     t->x += acc[k][p].x;
                     t->y += acc[k][p].y;
                     acc[k][p] = make_float2(0.f, 0.f);
                   }
                 }
-                curY[k] = Y;
+                curY[k] = rs.Y[k];
               }
-              const float2 f = fyrow[ty];
+            }
+            curX = X;
+          }
+          const float2 fxv = A.f()[(j * 2) * SMAX + tx];
+          float2 al[P];
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            const float2 av = A.a()[j * P + p];
+            al[p] = make_float2(fxv.x * av.x + fxv.y * av.y, fxv.x * av.y - fxv.y * av.x);   // conj(fx) a
+          }
+          const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
+#pragma unroll
+          for (int k = 0; k < R; ++k) {
+            if (vmask & (1u << k)) {
+              const float2 f = fyrow[rs.ty[k]];
 #pragma unroll
               for (int p = 0; p < P; ++p) {   // acc += conj(fy) alpha
                 acc[k][p].x = fmaf(f.x, al[p].x, fmaf(f.y, al[p].y, acc[k][p].x));
@@ -180,20 +302,36 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
           }
         }
       }
+      cp_async_wait_all();
+      __syncthreads();
+      // slot A is free: derive chunk c+2 into it; chunk c+1's payload has landed in B: form w V
+      if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
+      if (c + 1 < nch && tid < nst_of(c + 1)) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const float wv = B.w()[tid * P + p];
+          const float2 v = B.v()[tid * P + p];
+          const float2 ph = B.ph()[tid];
+          wsum[p] += (double)wv;
+          const float xr = wv * v.x, xi = wv * v.y;
+          B.a()[tid * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
+        }
+      }
+      __syncthreads();
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       if (curY[k] >= 0) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-          float2* t = tile + (curY[k] * U + curX) * P + p;
+          float2* t = tile + p * UU + curY[k] * U + curX;
           t->x += acc[k][p].x;
           t->y += acc[k][p].y;
         }
       }
     }
     __syncthreads();
-    for (int i = tid; i < U * U; i += NT) {
+    for (int i = tid; i < UU; i += NT) {
       const int ly = i / U, lx = i - ly * U;
       const int gy = Y0 + ly, gx = X0 + lx;
       if (gy >= a.N || gx >= a.N) continue;
@@ -201,7 +339,7 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
       bool nz = false;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        v[p] = tile[i * P + p];
+        v[p] = tile[p * UU + i];
         nz |= (v[p].x != 0.f) || (v[p].y != 0.f);
       }
       if (nz) flush_pixel<P>(a, ((size_t)gy * a.N + gx) * P, v);
@@ -222,20 +360,24 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
   }
 }
 
+// Degridding keeps the window pixels of its rows in registers (reloaded when a pixel changes)
+// when they fit; otherwise it reads them from the pol-planar window for every sample.
+template <int R, int P>
+struct DegridCache {
+  static constexpr bool enabled = R * P * 2 <= 48;
+};
+
 template <int SMIN, int SMAX, int NT, int TILE, int P>
 __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
   constexpr int NW = NT / 32;
   constexpr int B = 32 / (2 * P);
-  using L = SepLayout<SMAX, TILE, P>;
+  constexpr int ST = sep_stage(SMAX);
+  constexpr bool CACHE = DegridCache<R, P>::enabled;
+  constexpr int RC = CACHE ? R : 1;
+  using Slot = SepSlot<SMAX, TILE, P>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
-  float2* s_f = reinterpret_cast<float2*>(smem + L::tile_bytes);
-  float2* s_ph = reinterpret_cast<float2*>(smem + L::tile_bytes + L::f_bytes);    // [stage] (a_bytes >= this)
-  long long* s_fxo = reinterpret_cast<long long*>(smem + L::tile_bytes + L::f_bytes + L::a_bytes);
-  long long* s_fyo = s_fxo + kSepStage;
-  int* s_pack = reinterpret_cast<int*>(s_fyo + kSepStage);
-  int* s_src = s_pack + kSepStage;
   __shared__ float s_red[2][NW][32];
   __shared__ int s_item;
 
@@ -255,36 +397,53 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
     const int G = NT / S;
     const bool active = tid < G * S;
     const int rx = tid % S, ry0 = tid / S;
-    for (int i = tid; i < U * U; i += NT) {
-      const int ly = i / U, lx = i - ly * U;
-      const int gy = Y0 + ly, gx = X0 + lx;
-      const bool in = gy < a.N && gx < a.N;
-      const float2* src = reinterpret_cast<const float2*>(a.grid) + ((size_t)gy * a.N + gx) * P;
+    unsigned vmask = 0;
 #pragma unroll
-      for (int p = 0; p < P; ++p) tile[i * P + p] = in ? __ldg(src + p) : make_float2(0.f, 0.f);
+    for (int k = 0; k < R; ++k) vmask |= (ry0 + k * G < S) ? (1u << k) : 0u;
+    const int nch = (wi.count + ST - 1) / ST;
+    auto nst_of = [&](int c) { return min(ST, wi.count - c * ST); };
+    const int UU = U * U;   // the window is pol-planar: tile[p * UU + pixel]
+    {
+      const Slot s0(smem, 0), s1(smem, 1);
+      stage_recs(a.rec, wi.start, nst_of(0), s0);
+      if (nch > 1) stage_recs(a.rec, wi.start + ST, nst_of(1), s1);
+      cp_async_commit();
+      for (int i = tid; i < UU; i += NT) {
+        const int ly = i / U, lx = i - ly * U;
+        const int gy = Y0 + ly, gx = X0 + lx;
+        const bool in = gy < a.N && gx < a.N;
+        const float2* src = reinterpret_cast<const float2*>(a.grid) + ((size_t)gy * a.N + gx) * P;
+#pragma unroll
+        for (int p = 0; p < P; ++p) tile[p * UU + i] = in ? __ldg(src + p) : make_float2(0.f, 0.f);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      derive(a, nst_of(0), S, X0, Y0, s0);
+      if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
+      __syncthreads();
+      stage_payload<SMAX, TILE, P, NT>(a.sep, nullptr, nullptr, nst_of(0), S, s0);
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncthreads();
     }
-    for (int c0 = 0; c0 < wi.count; c0 += kSepStage) {
-      const int nst = min(kSepStage, wi.count - c0);
-      __syncthreads();
-      if (tid < nst) {
-        const SampleRec rc = a.rec[wi.start + c0 + tid];
-        const long long base = a.sep_off[rc.cf];
-        s_fxo[tid] = base + (long long)rc.ox * S;
-        s_fyo[tid] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
-        s_pack[tid] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
-        s_src[tid] = rc.src;
-        float2 ph = make_float2(1.f, 0.f);
-        if (a.has_phase) ph = sample_phasor(a.uvw, a.freq, a.C, rc.src, a.dl, a.dm, a.dn);
-        s_ph[tid] = ph;
-      }
-      __syncthreads();
-      for (int i = tid; i < nst * 2 * S; i += NT) {
-        const int j = i / (2 * S), r = i - j * 2 * S;
-        const long long src = r < S ? s_fxo[j] + r : s_fyo[j] + (r - S);
-        s_f[(j * 2 + (r < S ? 0 : 1)) * SMAX + (r < S ? r : r - S)] =
-            __ldg(reinterpret_cast<const float2*>(a.sep) + src);
-      }
-      __syncthreads();
+    RowState<R> rs;
+    int prev_row = -1;
+    int curX = -1;
+    int curY[RC];
+    float2 gc[RC][P];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      rs.ty[k] = 0;
+      rs.Y[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < RC; ++k) curY[k] = -1;
+    for (int c = 0; c < nch; ++c) {
+      const Slot A(smem, c & 1), Bs(smem, (c & 1) ^ 1);
+      if (c + 1 < nch) stage_payload<SMAX, TILE, P, NT>(a.sep, nullptr, nullptr, nst_of(c + 1), S, Bs);
+      if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
+      cp_async_commit();
+      const int nst = nst_of(c);
       for (int j0 = 0; j0 < nst; j0 += B) {
         float vals[32];
 #pragma unroll
@@ -293,33 +452,51 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
         for (int b = 0; b < B; ++b) {
           const int j = j0 + b;
           if (active && j < nst) {
-            const int pk = s_pack[j];
-            const int dx = pk & 0xff, dy = (pk >> 8) & 0xff, mx = (pk >> 16) & 0xff, my = (pk >> 24) & 0xff;
+            const int pk = A.pack()[j];
+            const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
+            const int row = pk & 0xff00ff00;
+            bool row_changed = false;
+            if (row != prev_row) {
+              prev_row = row;
+              rs.update(ry0, G, S, (pk >> 8) & 0xff, (pk >> 24) & 0xff, vmask);
+              row_changed = true;
+            }
             int tx = rx - mx;
             tx += (tx < 0) ? S : 0;
             const int X = dx + tx;
-            int ty0 = ry0 - my;
-            ty0 += (ty0 < 0) ? S : 0;
-            const float2* fyrow = s_f + (j * 2 + 1) * SMAX;
+            if constexpr (CACHE) {
+              if (X != curX || row_changed) {
+                const bool xchg = X != curX;
+#pragma unroll
+                for (int k = 0; k < RC; ++k) {
+                  if ((vmask & (1u << k)) && (xchg || rs.Y[k] != curY[k])) {
+                    curY[k] = rs.Y[k];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) gc[k][p] = tile[p * UU + curY[k] * U + X];
+                  }
+                }
+                curX = X;
+              }
+            }
+            const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
             float2 part[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) part[p] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-              if (ry0 + k * G < S) {
-                int ty = ty0 + k * G;
-                ty -= (ty >= S) ? S : 0;
-                const float2 f = fyrow[ty];
-                const float2* g = tile + ((dy + ty) * U + X) * P;
+              if (vmask & (1u << k)) {
+                const float2 f = fyrow[rs.ty[k]];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                  const float2 gv = g[p];
+                  float2 gv;
+                  if constexpr (CACHE) gv = gc[k < RC ? k : 0][p];
+                  else gv = tile[p * UU + rs.Y[k] * U + X];
                   part[p].x = fmaf(f.x, gv.x, fmaf(-f.y, gv.y, part[p].x));
                   part[p].y = fmaf(f.x, gv.y, fmaf(f.y, gv.x, part[p].y));
                 }
               }
             }
-            const float2 fxv = s_f[(j * 2) * SMAX + tx];
+            const float2 fxv = A.f()[(j * 2) * SMAX + tx];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
               vals[b * 2 * P + 2 * p] = fxv.x * part[p].x - fxv.y * part[p].y;
@@ -347,30 +524,39 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
           const int j = j0 + b;
           const float partner = __shfl_xor_sync(0xffffffffu, v, 1);
           if (j < nst) {
-            const float2 ph = s_ph[j];
+            const float2 ph = A.ph()[j];
             const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
-            a.vis_out[(size_t)s_src[j] * 2 * P + comp] = out;
+            a.vis_out[(size_t)A.src()[j] * 2 * P + comp] = out;
           }
         }
         buf ^= 1;
       }
+      cp_async_wait_all();
+      __syncthreads();
+      if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
+      __syncthreads();
     }
   }
 }
+
+// Threads per CTA of the separable kernels by class: enough warps per SM to hide latency while
+// each thread keeps several rows of its column in registers.
+constexpr int kSepThreads[kNumClasses] = {128, 256, 256, 512, 512, 512};
 
 template <int CLS, int P>
 awg_status run_grid_sep(const GridArgs& a, int sms, cudaStream_t st) {
   constexpr ClassCfg cc = kClasses[CLS];
   constexpr int smin = CLS == 0 ? 0 : kClasses[CLS > 0 ? CLS - 1 : 0].smax;
+  constexpr int nt = kSepThreads[CLS];
   using L = SepLayout<cc.smax, cc.tile, P>;
-  auto kern = k_grid_sep<smin, cc.smax, cc.nt, cc.tile, P>;
+  auto kern = k_grid_sep<smin, cc.smax, nt, cc.tile, P>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
     AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, cc.nt, L::bytes));
     if (bps < 1) return set_error(AWG_ERR_CUDA, "separable gridding kernel does not fit on an SM");
   }
-  kern<<<sms * bps, cc.nt, L::bytes, st>>>(a, CLS);
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, CLS);
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return AWG_OK;
@@ -380,15 +566,16 @@ template <int CLS, int P>
 awg_status run_degrid_sep(const DegridArgs& a, int sms, cudaStream_t st) {
   constexpr ClassCfg cc = kClasses[CLS];
   constexpr int smin = CLS == 0 ? 0 : kClasses[CLS > 0 ? CLS - 1 : 0].smax;
+  constexpr int nt = kSepThreads[CLS];
   using L = SepLayout<cc.smax, cc.tile, P>;
-  auto kern = k_degrid_sep<smin, cc.smax, cc.nt, cc.tile, P>;
+  auto kern = k_degrid_sep<smin, cc.smax, nt, cc.tile, P>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
     AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, cc.nt, L::bytes));
     if (bps < 1) return set_error(AWG_ERR_CUDA, "separable degridding kernel does not fit on an SM");
   }
-  kern<<<sms * bps, cc.nt, L::bytes, st>>>(a, CLS);
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, CLS);
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return AWG_OK;
