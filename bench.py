@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--n-int", type=int, default=None, help="integrations per rank (default: the full 2000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-every", type=int, default=40, help="oracle sample: every k-th integration")
+    ap.add_argument("--cpu-sample-every", type=int, default=None,
+                    help="oracle sample: every k-th integration (default 40 for cpu_baseline, 200 per reference step)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="CF storage / accumulation variants against the FP64 oracle (one JSON line each)")
     return ap.parse_args()
@@ -138,6 +139,31 @@ def measured_peaks():
         return {}
 
 
+def csrc_hash() -> str:
+    """SHA-256 over the library's CUDA / C++ sources (names and contents, sorted)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2508_17187_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(op: str):
+    """DRAM bytes per full-size launch of `op` from the committed ncu summary, or None when the
+    kernels have changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_wproj.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("csrc_sha256") != csrc_hash():
+        return None
+    return rec.get("per_launch_bytes", {}).get(op)
+
+
 def fp32_alu_peak_tflops(sms: int, mhz: float) -> float:
     """Non-tensor FP32 FMA peak: SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -176,7 +202,8 @@ def reference_arm(args):
         return 0
     # only the sampled integrations get visibilities (CPU DFT of the sky), the rest is never read
     full = rank_workload(1, 0, args.n_int or synth.CONFIGS[CONFIG]["n_int"], "cpu", with_vis=False)
-    ints = np.arange(0, full.n_int, args.cpu_sample_every)
+    every = args.cpu_sample_every or 200
+    ints = np.arange(0, full.n_int, every)
     rows = np.concatenate([np.arange(t * full.n_bl, (t + 1) * full.n_bl) for t in ints])
     wl = dataclasses.replace(full, uvw_m=full.uvw_m[rows].copy(), pa_rad=full.pa_rad[rows].copy(),
                              pa_bin=full.pa_bin[rows].copy(), n_int=len(ints))
@@ -185,7 +212,7 @@ def reference_arm(args):
     info = None
     for i in range(args.warmup + args.steps):
         info = run_cpu_baseline(wl, 1)
-        info["sample"] = info["sample"].replace("every 1th integration", f"every {args.cpu_sample_every}th integration")
+        info["sample"] = info["sample"].replace("every 1th integration", f"every {every}th integration")
         if i >= args.warmup:
             times.append(info["seconds"])
     per_step = statistics.mean(times)
@@ -493,7 +520,8 @@ def main():
         "cf_gmac_per_s": 2 * P * sum_taps * world / (ms / 1e3) / 1e9,
         "ops_ms": {k: statistics.mean(v) for k, v in op_ms.items()},
         "roofline": {"bound": "alu", "kernel": f"{dom}_visibilities (all support classes)", "achieved": achieved,
-                     "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": None,
+                     "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
+                     "traffic": measured_traffic(dom),
                      "peak_basis": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)"},
         "clocks": {k: cs[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "gpu_launches": int(launches),
@@ -501,7 +529,7 @@ def main():
     }
     if not args.no_cpu_baseline:
         host_wl = dataclasses.replace(wl, vis=vis.cpu().numpy(), weight=wt.cpu().numpy())
-        cb = run_cpu_baseline(host_wl, args.cpu_sample_every)
+        cb = run_cpu_baseline(host_wl, args.cpu_sample_every or 40)
         cb.pop("seconds")
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)

@@ -110,7 +110,9 @@ awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* 
  * Same, with caller-supplied tables instead of the built ones (e.g. a support-1 delta kernel).
  * supports: host [n_cf] taps per CF (1..64); table: host c64, all CFs concatenated in CF-index
  * order, each [OS+1][OS+1][S][S].  Only grid_n, oversampling, use_w, n_wplanes, w_max_lambda,
- * n_pa_bins, n_subbands and cf_dtype of params are read.
+ * n_pa_bins, n_subbands, cf_dtype and separable of params are read.  With separable and FP32
+ * storage, only factors are kept when every table is an outer product fy[oy][ty] fx[ox][tx] to
+ * 1e-6 of its peak (the accuracy of FP32 input); otherwise the full tables are.
  */
 awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* supports,
                                     const float* table, void* stream, awg_cf_set* out);

@@ -14,7 +14,7 @@ namespace awg {
 constexpr double kCLight = 299792458.0;
 constexpr int kMaxSupport = 64;
 constexpr int kNumClasses = 6;
-constexpr int kItemChunk = 256;   // samples per work item at most (bounds the queue tail)
+constexpr int kItemChunk = 1024;  // samples per work item at most (bounds the queue tail)
 
 // Kernel classes: supports in (smax of the previous class, smax] run in one template instance
 // with nt threads per CTA and tile x tile sample-start positions per work item.
@@ -22,10 +22,10 @@ struct ClassCfg {
   int smax, nt, tile;
 };
 constexpr ClassCfg kClasses[kNumClasses] = {
-    {8, 64, 32}, {16, 128, 32}, {24, 192, 32}, {32, 256, 32}, {48, 256, 16}, {64, 256, 16}};
+    {8, 64, 32}, {16, 128, 32}, {24, 192, 32}, {32, 256, 32}, {48, 256, 16}, {64, 256, 8}};
 
 // Class of a support (the smax column of kClasses, spelled out so device code can call it).
-__host__ __device__ inline int class_of_support(int S) {
+__host__ __device__ constexpr int class_of_support(int S) {
   return S <= 8 ? 0 : S <= 16 ? 1 : S <= 24 ? 2 : S <= 32 ? 3 : S <= 48 ? 4 : S <= 64 ? 5 : -1;
 }
 
@@ -99,7 +99,8 @@ struct PlanImpl {
   int32_t* d_scan_tmp = nullptr;
   WorkItem* d_items = nullptr;    // [max_items]
   int32_t* d_class_range = nullptr;  // [kNumClasses + 1]
-  int32_t* d_queue = nullptr;        // [kNumClasses] work-queue heads
+  int32_t* d_slot_range = nullptr;   // [kMaxSupport + 1]: work items of each distinct support
+  int32_t* d_queue = nullptr;        // [kMaxSupport] work-queue heads (one per launch)
   unsigned long long* d_counters = nullptr;  // [0] kept, [1] dropped, [2] sum of S^2
   double* d_uvw = nullptr;        // plan-owned copies of uvw / freq (only with a phase shift,
   double* d_freq = nullptr;       // whose phasor the compute kernels form per sample)

@@ -166,6 +166,46 @@ static awg_status alloc_cf(CfSetImpl* cf, cudaStream_t st) {
   return AWG_OK;
 }
 
+// Upload the factors fx[ci], fy[ci] (FP64 pairs, [(OS+1) S] each) of every CF as the separable
+// storage, with the support / offset bookkeeping the plan shares with the 2-D layout.
+static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<double>>& fx,
+                                   const std::vector<std::vector<double>>& fy, cudaStream_t st) {
+  const int OS = cf->p.oversampling;
+  cf->separable = 1;
+  cf->sep_offsets.resize(cf->n_cf);
+  int64_t off = 0;
+  for (int i = 0; i < cf->n_cf; ++i) {
+    cf->sep_offsets[i] = off;
+    off += 2 * (int64_t)(OS + 1) * cf->supports[i];
+  }
+  cf->n_values = off;
+  std::vector<float> h((size_t)2 * off);
+  for (int i = 0; i < cf->n_cf; ++i) {
+    const int64_t q = (int64_t)(OS + 1) * cf->supports[i];
+    for (int64_t t = 0; t < 2 * q; ++t) {
+      h[2 * cf->sep_offsets[i] + t] = (float)fx[i][t];
+      h[2 * cf->sep_offsets[i] + 2 * q + t] = (float)fy[i][t];
+    }
+  }
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep, sizeof(float) * h.size()));
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep_off, sizeof(int64_t) * cf->n_cf));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep_off, cf->sep_offsets.data(), sizeof(int64_t) * cf->n_cf,
+                               cudaMemcpyHostToDevice, st));
+  // the support / offset bookkeeping the plan and the kernels share with the 2-D layout
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sup, cf->supports.data(), sizeof(int32_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
+  std::vector<double> taper;
+  taper_image(cf->p, taper);
+  std::vector<float> inv(cf->p.grid_n);
+  for (int i = 0; i < cf->p.grid_n; ++i) inv[i] = (float)(1.0 / taper[i]);
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_inv_taper, inv.data(), sizeof(float) * cf->p.grid_n, cudaMemcpyHostToDevice, st));
+  AWG_CUDA_TRY(cudaStreamSynchronize(st));
+  fill_slots(cf);
+  return AWG_OK;
+}
+
 // Separable storage: build every non-negative plane, fit it as fy fx, mirror the fit for the
 // negative planes, upload only the factors.  Returns AWG_ERR_UNSUPPORTED (nothing allocated on
 // the device) when some CF is not separable to 1e-7 of its peak.
@@ -207,39 +247,7 @@ static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
     }
   }
   if (failed) return AWG_ERR_UNSUPPORTED;
-  cf->separable = 1;
-  cf->sep_offsets.resize(cf->n_cf);
-  int64_t off = 0;
-  for (int i = 0; i < cf->n_cf; ++i) {
-    cf->sep_offsets[i] = off;
-    off += 2 * (int64_t)(OS + 1) * cf->supports[i];
-  }
-  cf->n_values = off;
-  std::vector<float> h((size_t)2 * off);
-  for (int i = 0; i < cf->n_cf; ++i) {
-    const int64_t q = (int64_t)(OS + 1) * cf->supports[i];
-    for (int64_t t = 0; t < 2 * q; ++t) {
-      h[2 * cf->sep_offsets[i] + t] = (float)fx[i][t];
-      h[2 * cf->sep_offsets[i] + 2 * q + t] = (float)fy[i][t];
-    }
-  }
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep, sizeof(float) * h.size()));
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep_off, sizeof(int64_t) * cf->n_cf));
-  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
-  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep_off, cf->sep_offsets.data(), sizeof(int64_t) * cf->n_cf,
-                               cudaMemcpyHostToDevice, st));
-  // the support / offset bookkeeping the plan and the kernels share with the 2-D layout
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
-  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sup, cf->supports.data(), sizeof(int32_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
-  std::vector<double> taper;
-  taper_image(cf->p, taper);
-  std::vector<float> inv(cf->p.grid_n);
-  for (int i = 0; i < cf->p.grid_n; ++i) inv[i] = (float)(1.0 / taper[i]);
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
-  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_inv_taper, inv.data(), sizeof(float) * cf->p.grid_n, cudaMemcpyHostToDevice, st));
-  AWG_CUDA_TRY(cudaStreamSynchronize(st));
-  fill_slots(cf);
-  return AWG_OK;
+  return upload_separable(cf, fx, fy, st);
 }
 
 }  // namespace awg
@@ -371,6 +379,35 @@ awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* 
     if (v > kMaxSupport) { delete cf; return set_error(AWG_ERR_UNSUPPORTED, "support > 64 is not supported"); }
     if (v > params->grid_n) { delete cf; return set_error(AWG_ERR_INVALID_ARG, "support exceeds grid_n"); }
   }
+  if (params->separable && params->cf_dtype == AWG_CF_FP32) {
+    // keep only factors when every caller table is an outer product to FP32 accuracy
+    cf->n_signed = params->use_w ? 2 * params->n_wplanes - 1 : 1;
+    int64_t off = 0;
+    std::vector<int64_t> offs(cf->n_cf);
+    for (int ci = 0; ci < cf->n_cf; ++ci) {
+      offs[ci] = off;
+      off += (int64_t)(params->oversampling + 1) * (params->oversampling + 1) * cf->supports[ci] * cf->supports[ci];
+    }
+    std::vector<std::vector<double>> fx(cf->n_cf), fy(cf->n_cf);
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int ci = 0; ci < cf->n_cf; ++ci) {
+      if (failed) continue;
+      const int S = cf->supports[ci];
+      const int64_t nv = (int64_t)(params->oversampling + 1) * (params->oversampling + 1) * S * S;
+      std::vector<double> tab(table + 2 * offs[ci], table + 2 * (offs[ci] + nv));
+      if (!factor_rank1(tab, S, params->oversampling, 1e-6, fx[ci], fy[ci])) {
+#pragma omp atomic write
+        failed = 1;
+      }
+    }
+    if (!failed) {
+      s = upload_separable(cf, fx, fy, st);
+      if (s != AWG_OK) { free_cf(cf); return s; }
+      *out = (awg_cf_set)cf;
+      return AWG_OK;
+    }
+  }
   s = alloc_cf(cf, st);
   if (s != AWG_OK) { free_cf(cf); return s; }
   std::vector<int> idx;
@@ -460,6 +497,7 @@ static awg_status plan_free(PlanImpl* pl) {
   cudaFree(pl->d_scan_tmp);
   cudaFree(pl->d_items);
   cudaFree(pl->d_class_range);
+  cudaFree(pl->d_slot_range);
   cudaFree(pl->d_queue);
   cudaFree(pl->d_counters);
   cudaFree(pl->d_uvw);
@@ -514,7 +552,8 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
   A((void**)&pl->d_scan_tmp, ((nb + 1023) / 1024 + 1024) * sizeof(int32_t));
   A((void**)&pl->d_items, (size_t)pl->max_items * sizeof(WorkItem));
   A((void**)&pl->d_class_range, (kNumClasses + 1) * sizeof(int32_t));
-  A((void**)&pl->d_queue, kNumClasses * sizeof(int32_t));
+  A((void**)&pl->d_slot_range, (kMaxSupport + 1) * sizeof(int32_t));
+  A((void**)&pl->d_queue, kMaxSupport * sizeof(int32_t));
   A((void**)&pl->d_counters, 4 * sizeof(unsigned long long));
   if (pl->has_phase) {
     A((void**)&pl->d_uvw, (size_t)std::max<int64_t>(pl->R, 1) * 3 * sizeof(double));

@@ -12,6 +12,8 @@ AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_DEGRID, false)
 AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_DEGRID, true)
 AWG_FOR_SEP_CLASSES_AND_POLS(AWG_DECLARE_GRID_SEP)
 AWG_FOR_SEP_CLASSES_AND_POLS(AWG_DECLARE_DEGRID_SEP)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT)
 
 namespace {
 
@@ -36,20 +38,32 @@ awg_status grid_class(int c, int P, const GridArgs& a, int sms, cudaStream_t st)
   return set_error(AWG_ERR_UNSUPPORTED, "no gridding kernel for this class / pol count");
 }
 
-awg_status grid_class_sep(int c, int P, const GridArgs& a, int sms, cudaStream_t st) {
+// Separable kernels run once per distinct support (slot): the exact-support kernel when there is
+// one for S, else the class kernel restricted to the slot's items.
+awg_status grid_slot_sep(int S, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
+#define AWG_CASE(SS, PP) \
+  if (S == SS && P == PP) return run_grid_exact<SS, PP>(a, slot, sms, st);
+  AWG_FOR_EXACT_AND_POLS(AWG_CASE)
+#undef AWG_CASE
+  const int c = class_of_support(S);
 #define AWG_CASE(C, PP) \
-  if (c == C && P == PP) return run_grid_sep<C, PP>(a, sms, st);
+  if (c == C && P == PP) return run_grid_sep<C, PP>(a, slot, sms, st);
   AWG_FOR_SEP_CLASSES_AND_POLS(AWG_CASE)
 #undef AWG_CASE
-  return set_error(AWG_ERR_UNSUPPORTED, "no separable gridding kernel for this class / pol count");
+  return set_error(AWG_ERR_UNSUPPORTED, "no separable gridding kernel for this support / pol count");
 }
 
-awg_status degrid_class_sep(int c, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+awg_status degrid_slot_sep(int S, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+#define AWG_CASE(SS, PP) \
+  if (S == SS && P == PP) return run_degrid_exact<SS, PP>(a, slot, sms, st);
+  AWG_FOR_EXACT_AND_POLS(AWG_CASE)
+#undef AWG_CASE
+  const int c = class_of_support(S);
 #define AWG_CASE(C, PP) \
-  if (c == C && P == PP) return run_degrid_sep<C, PP>(a, sms, st);
+  if (c == C && P == PP) return run_degrid_sep<C, PP>(a, slot, sms, st);
   AWG_FOR_SEP_CLASSES_AND_POLS(AWG_CASE)
 #undef AWG_CASE
-  return set_error(AWG_ERR_UNSUPPORTED, "no separable degridding kernel for this class / pol count");
+  return set_error(AWG_ERR_UNSUPPORTED, "no separable degridding kernel for this support / pol count");
 }
 
 template <bool BF16>
@@ -120,14 +134,20 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   a.sumwt = sumwt;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
-  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kNumClasses, st));
+  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
+  if (cf->separable) {
+    a.class_range = pl->d_slot_range;
+    for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
+      awg_status s = grid_slot_sep(cf->slots.S[i], i, P, a, sms, st);
+      if (s != AWG_OK) return s;
+    }
+    return AWG_OK;
+  }
   for (int c = kNumClasses - 1; c >= 0; --c) {   // largest supports first
     if (!class_present(cf, c)) continue;
-    awg_status s = cf->separable ? grid_class_sep(c, P, a, sms, st)
-                   : bf16        ? grid_class<true>(c, P, a, sms, st)
-                                 : grid_class<false>(c, P, a, sms, st);
+    awg_status s = bf16 ? grid_class<true>(c, P, a, sms, st) : grid_class<false>(c, P, a, sms, st);
     if (s != AWG_OK) return s;
   }
   return AWG_OK;
@@ -157,15 +177,21 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   a.vis_out = (float*)vis_out;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
-  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kNumClasses, st));
+  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
-  for (int c = kNumClasses - 1; c >= 0; --c) {
-    if (!class_present(cf, c)) continue;
-    awg_status s = cf->separable ? degrid_class_sep(c, P, a, sms, st)
-                   : bf16        ? degrid_class<true>(c, P, a, sms, st)
-                                 : degrid_class<false>(c, P, a, sms, st);
-    if (s != AWG_OK) return s;
+  if (cf->separable) {
+    a.class_range = pl->d_slot_range;
+    for (int i = cf->slots.n - 1; i >= 0; --i) {
+      awg_status s = degrid_slot_sep(cf->slots.S[i], i, P, a, sms, st);
+      if (s != AWG_OK) return s;
+    }
+  } else {
+    for (int c = kNumClasses - 1; c >= 0; --c) {
+      if (!class_present(cf, c)) continue;
+      awg_status s = bf16 ? degrid_class<true>(c, P, a, sms, st) : degrid_class<false>(c, P, a, sms, st);
+      if (s != AWG_OK) return s;
+    }
   }
   k_zero_dropped<<<sms * 4, 256, 0, st>>>(pl->d_drop, pl->d_counters, (float*)vis_out, P);
   AWG_CUDA_TRY(cudaGetLastError());

@@ -31,7 +31,7 @@ constexpr size_t kBucketBytes = align256(sizeof(int32_t) * (kNoAllocMaxBuckets +
 constexpr size_t kScanBytes = align256(sizeof(int32_t) * ((kNoAllocMaxBuckets + 1) / 1024 + 1024));
 constexpr int64_t kNoAllocMaxItems = kNoAllocMaxBuckets + kNoAllocMaxSamples / kItemChunk + 1;
 constexpr size_t kItemBytes = align256(sizeof(WorkItem) * kNoAllocMaxItems);
-constexpr size_t kSmallBytes = 3 * 256;   // class ranges, queue heads, counters
+constexpr size_t kSmallBytes = 256 + 512 + 512 + 256;   // class ranges, slot ranges, queue heads, counters
 constexpr size_t kScratchBytes = 2 * kRecBytes + 2 * kKeyBytes + 4 * kBucketBytes + kScanBytes + kItemBytes + kSmallBytes;
 
 // The scratch itself: about 4.7 MB, shared by every call on a device.
@@ -112,7 +112,8 @@ extern "C" awg_status grid_visibilities_noalloc(awg_cf_set hc, const double* uvw
   pl.d_scan_tmp = (int32_t*)take(kScanBytes);
   pl.d_items = (WorkItem*)take(kItemBytes);
   pl.d_class_range = (int32_t*)take(256);
-  pl.d_queue = (int32_t*)take(256);
+  pl.d_slot_range = (int32_t*)take(512);
+  pl.d_queue = (int32_t*)take(512);
   pl.d_counters = (unsigned long long*)take(256);
   // plan_build clears the bucket counts and counters it accumulates into and overwrites every
   // other slice before reading it, so what the previous call left in the array does not matter.

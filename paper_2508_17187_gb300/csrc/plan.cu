@@ -255,9 +255,11 @@ struct ClassFirstBucket {
   int b[kNumClasses + 1];
 };
 
-__global__ void k_class_range(const int32_t* __restrict__ ioff, ClassFirstBucket fb, int32_t* __restrict__ range) {
+__global__ void k_class_range(const int32_t* __restrict__ ioff, ClassFirstBucket fb, SlotTable st,
+                              int32_t* __restrict__ range, int32_t* __restrict__ slot_range) {
   const int c = threadIdx.x;
   if (c <= kNumClasses) range[c] = ioff[fb.b[c]];
+  if (c <= st.n) slot_range[c] = ioff[st.base[c]];
 }
 
 __global__ void k_scatter(int64_t n, const int32_t* __restrict__ key, const SampleRec* __restrict__ rec_tmp,
@@ -371,7 +373,7 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
     for (int i = 0; i < cf->slots.n; ++i)
       if (class_of_support(cf->slots.S[i]) >= c) { fb.b[c] = cf->slots.base[i]; break; }
   }
-  k_class_range<<<1, 32, 0, st>>>(pl->d_ioff, fb, pl->d_class_range);
+  k_class_range<<<1, kMaxSupport + 1, 0, st>>>(pl->d_ioff, fb, cf->slots, pl->d_class_range, pl->d_slot_range);
   AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   if (pl->n > 0 && nb > 0) {

@@ -21,12 +21,20 @@
 
 namespace awg {
 
-// Rows per thread needed by any support of a class: max over S in (smin, smax] of ceil(S / (NT / S)).
+// Row groups for support S on NT threads: G = NT / S (at most S); thread t < G S owns column
+// t mod S and rows t div S + k G below S (the last rows of a column may be fewer).
+__host__ __device__ constexpr int row_groups(int S, int nt) {
+  int g = nt / S;
+  if (g > S) g = S;
+  return g < 1 ? 1 : g;
+}
+
+// Rows per thread needed by any support of a class: max over S in (smin, smax] of ceil(S / G).
 __host__ __device__ constexpr int sep_rows(int smin, int smax, int nt) {
   int r = 1;
   for (int S = smin + 1; S <= smax; ++S) {
-    const int G = nt / S;
-    const int rows = (S + G - 1) / G;
+    const int g = row_groups(S, nt);
+    const int rows = (S + g - 1) / g;
     r = rows > r ? rows : r;
   }
   return r;
@@ -55,7 +63,11 @@ struct SepLayout {
   static constexpr size_t k_off = ph_off + (size_t)ST * sizeof(float2);            // int [ST] packed offsets
   static constexpr size_t s_off = k_off + (size_t)ST * sizeof(int);                // int [ST] sample index
   static constexpr size_t slot_bytes = (s_off + (size_t)ST * sizeof(int) + 127) & ~(size_t)127;
-  static constexpr size_t bytes = tile_bytes + 2 * slot_bytes;
+  // per-chunk table by column residue: gridding alpha[j][rx][p] = conj(fx[j][tx]) w V_p,
+  // degridding beta[j][rx] = fx[j][tx], tx = (rx - p0x) mod S
+  static constexpr size_t al_off = tile_bytes + 2 * slot_bytes;
+  static constexpr size_t al_bytes = (size_t)ST * SMAX * P * sizeof(float2);
+  static constexpr size_t bytes = al_off + al_bytes;
 };
 
 template <int SMAX, int TILE, int P>
@@ -165,6 +177,46 @@ struct RowState {
   }
 };
 
+// alpha[j][rx][p] = conj(fx[j][(rx - mx_j) mod S]) * w_jp V_jp (* phasor): formed once per
+// chunk for every (sample, column residue) instead of by each of the G threads of a column.  The
+// threads below nst also add the chunk's weights to the sum of weights.
+template <int SMAX, int TILE, int P, int NT>
+__device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P>& sl, float2* alpha, int nst, int S,
+                                           double (&wsum)[P]) {
+  if ((int)threadIdx.x < nst) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) wsum[p] += (double)sl.w()[threadIdx.x * P + p];
+  }
+  for (int i = threadIdx.x; i < nst * S; i += NT) {
+    const int j = i / S, rx = i - j * S;
+    const int mx = (sl.pack()[j] >> 16) & 0xff;
+    int tx = rx - mx;
+    tx += (tx < 0) ? S : 0;
+    const float2 fxv = sl.f()[(j * 2) * SMAX + tx];
+    const float2 ph = sl.ph()[j];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const float wv = sl.w()[j * P + p];
+      const float2 v = sl.v()[j * P + p];
+      const float xr = wv * v.x, xi = wv * v.y;
+      const float ar = xr * ph.x - xi * ph.y, ai = xr * ph.y + xi * ph.x;
+      alpha[(j * SMAX + rx) * P + p] = make_float2(fxv.x * ar + fxv.y * ai, fxv.x * ai - fxv.y * ar);
+    }
+  }
+}
+
+// beta[j][rx] = fx[j][(rx - mx_j) mod S] for the degridding kernel.
+template <int SMAX, int TILE, int P, int NT>
+__device__ __forceinline__ void form_beta(const SepSlot<SMAX, TILE, P>& sl, float2* beta, int nst, int S) {
+  for (int i = threadIdx.x; i < nst * S; i += NT) {
+    const int j = i / S, rx = i - j * S;
+    const int mx = (sl.pack()[j] >> 16) & 0xff;
+    int tx = rx - mx;
+    tx += (tx < 0) ? S : 0;
+    beta[j * SMAX + rx] = sl.f()[(j * 2) * SMAX + tx];
+  }
+}
+
 template <int SMIN, int SMAX, int NT, int TILE, int P>
 __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
@@ -172,8 +224,10 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
   using Slot = SepSlot<SMAX, TILE, P>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
+  float2* alpha = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P>::al_off);
   __shared__ int s_item;
   __shared__ double s_wsum[NT / 32][P];
+  static_assert(NT % 32 == 0, "the warp reductions need whole warps");
 
   const int tid = threadIdx.x;
   const int begin = a.class_range[cls], end = a.class_range[cls + 1];
@@ -188,9 +242,10 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
     const int it = s_item;
     if (it >= end) break;
     const WorkItem wi = a.items[it];
-    const int S = wi.S, U = TILE + S - 1;
+    const int S = (SMIN + 1 == SMAX) ? SMAX : (int)wi.S;   // a constant for exact-support kernels
+    const int U = TILE + S - 1;
     const int X0 = wi.tile_x * TILE, Y0 = wi.tile_y * TILE;
-    const int G = NT / S;
+    const int G = row_groups(S, NT);
     const bool active = tid < G * S;
     const int rx = tid % S, ry0 = tid / S;
     unsigned vmask = 0;
@@ -215,17 +270,7 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      if (tid < nst_of(0)) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const float wv = s0.w()[tid * P + p];
-          const float2 v = s0.v()[tid * P + p];
-          const float2 ph = s0.ph()[tid];
-          wsum[p] += (double)wv;
-          const float xr = wv * v.x, xi = wv * v.y;
-          s0.a()[tid * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
-        }
-      }
+      form_alpha<SMAX, TILE, P, NT>(s0, alpha, nst_of(0), S, wsum);
       __syncthreads();
     }
 
@@ -251,6 +296,9 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
       if (active) {
         for (int j = 0; j < nst; ++j) {
           const int pk = A.pack()[j];
+          float2 al[P];
+#pragma unroll
+          for (int p = 0; p < P; ++p) al[p] = alpha[(j * SMAX + rx) * P + p];
           const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
           const int row = pk & 0xff00ff00;   // (dy, my): identical for the whole CTA
           bool row_changed = false;
@@ -281,13 +329,6 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
             }
             curX = X;
           }
-          const float2 fxv = A.f()[(j * 2) * SMAX + tx];
-          float2 al[P];
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const float2 av = A.a()[j * P + p];
-            al[p] = make_float2(fxv.x * av.x + fxv.y * av.y, fxv.x * av.y - fxv.y * av.x);   // conj(fx) a
-          }
           const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
 #pragma unroll
           for (int k = 0; k < R; ++k) {
@@ -306,17 +347,7 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
       __syncthreads();
       // slot A is free: derive chunk c+2 into it; chunk c+1's payload has landed in B: form w V
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
-      if (c + 1 < nch && tid < nst_of(c + 1)) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const float wv = B.w()[tid * P + p];
-          const float2 v = B.v()[tid * P + p];
-          const float2 ph = B.ph()[tid];
-          wsum[p] += (double)wv;
-          const float xr = wv * v.x, xi = wv * v.y;
-          B.a()[tid * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
-        }
-      }
+      if (c + 1 < nch) form_alpha<SMAX, TILE, P, NT>(B, alpha, nst_of(c + 1), S, wsum);
       __syncthreads();
     }
 #pragma unroll
@@ -371,6 +402,7 @@ template <int SMIN, int SMAX, int NT, int TILE, int P>
 __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
   constexpr int NW = NT / 32;
+  static_assert(NT % 32 == 0, "the warp reductions need whole warps");
   constexpr int B = 32 / (2 * P);
   constexpr int ST = sep_stage(SMAX);
   constexpr bool CACHE = DegridCache<R, P>::enabled;
@@ -378,6 +410,7 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
   using Slot = SepSlot<SMAX, TILE, P>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
+  float2* beta = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P>::al_off);
   __shared__ float s_red[2][NW][32];
   __shared__ int s_item;
 
@@ -392,9 +425,10 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
     const int it = s_item;
     if (it >= end) break;
     const WorkItem wi = a.items[it];
-    const int S = wi.S, U = TILE + S - 1;
+    const int S = (SMIN + 1 == SMAX) ? SMAX : (int)wi.S;   // a constant for exact-support kernels
+    const int U = TILE + S - 1;
     const int X0 = wi.tile_x * TILE, Y0 = wi.tile_y * TILE;
-    const int G = NT / S;
+    const int G = row_groups(S, NT);
     const bool active = tid < G * S;
     const int rx = tid % S, ry0 = tid / S;
     unsigned vmask = 0;
@@ -425,6 +459,8 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
+      form_beta<SMAX, TILE, P, NT>(s0, beta, nst_of(0), S);
+      __syncthreads();
     }
     RowState<R> rs;
     int prev_row = -1;
@@ -453,6 +489,7 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
           const int j = j0 + b;
           if (active && j < nst) {
             const int pk = A.pack()[j];
+            const float2 fxv = beta[j * SMAX + rx];
             const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
             const int row = pk & 0xff00ff00;
             bool row_changed = false;
@@ -496,7 +533,6 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
                 }
               }
             }
-            const float2 fxv = A.f()[(j * 2) * SMAX + tx];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
               vals[b * 2 * P + 2 * p] = fxv.x * part[p].x - fxv.y * part[p].y;
@@ -534,6 +570,7 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
       cp_async_wait_all();
       __syncthreads();
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
+      if (c + 1 < nch) form_beta<SMAX, TILE, P, NT>(Bs, beta, nst_of(c + 1), S);
       __syncthreads();
     }
   }
@@ -544,7 +581,7 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
 constexpr int kSepThreads[kNumClasses] = {128, 256, 256, 512, 512, 512};
 
 template <int CLS, int P>
-awg_status run_grid_sep(const GridArgs& a, int sms, cudaStream_t st) {
+awg_status run_grid_sep(const GridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr ClassCfg cc = kClasses[CLS];
   constexpr int smin = CLS == 0 ? 0 : kClasses[CLS > 0 ? CLS - 1 : 0].smax;
   constexpr int nt = kSepThreads[CLS];
@@ -556,14 +593,14 @@ awg_status run_grid_sep(const GridArgs& a, int sms, cudaStream_t st) {
     AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, cc.nt, L::bytes));
     if (bps < 1) return set_error(AWG_ERR_CUDA, "separable gridding kernel does not fit on an SM");
   }
-  kern<<<sms * bps, nt, L::bytes, st>>>(a, CLS);
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, slot);
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return AWG_OK;
 }
 
 template <int CLS, int P>
-awg_status run_degrid_sep(const DegridArgs& a, int sms, cudaStream_t st) {
+awg_status run_degrid_sep(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr ClassCfg cc = kClasses[CLS];
   constexpr int smin = CLS == 0 ? 0 : kClasses[CLS > 0 ? CLS - 1 : 0].smax;
   constexpr int nt = kSepThreads[CLS];
@@ -575,21 +612,83 @@ awg_status run_degrid_sep(const DegridArgs& a, int sms, cudaStream_t st) {
     AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, cc.nt, L::bytes));
     if (bps < 1) return set_error(AWG_ERR_CUDA, "separable degridding kernel does not fit on an SM");
   }
-  kern<<<sms * bps, nt, L::bytes, st>>>(a, CLS);
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, slot);
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return AWG_OK;
 }
 
+// Exact-support kernels for the supports of the W-projection schedule: S is a compile-time
+// constant and G (rows groups) divides S, so every thread owns S / G rows; S * G is a whole
+// number of warps.
+template <int S>
+struct ExactCfg;
+template <> struct ExactCfg<8> { static constexpr int G = 8; };
+template <> struct ExactCfg<16> { static constexpr int G = 16; };
+template <> struct ExactCfg<24> { static constexpr int G = 12; };
+template <> struct ExactCfg<32> { static constexpr int G = 16; };
+template <> struct ExactCfg<40> { static constexpr int G = 20; };
+template <> struct ExactCfg<48> { static constexpr int G = 16; };
+template <> struct ExactCfg<56> { static constexpr int G = 8; };
+template <> struct ExactCfg<64> { static constexpr int G = 8; };
+
+template <int S, int P>
+awg_status run_grid_exact(const GridArgs& a, int slot, int sms, cudaStream_t st) {
+  constexpr int tile = kClasses[class_of_support(S)].tile;
+  constexpr int nt = S * ExactCfg<S>::G;
+  using L = SepLayout<S, tile, P>;
+  auto kern = k_grid_sep<S - 1, S, nt, tile, P>;
+  static int bps = 0;
+  if (bps == 0) {
+    AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+    AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, nt, L::bytes));
+    if (bps < 1) return set_error(AWG_ERR_CUDA, "exact-support gridding kernel does not fit on an SM");
+  }
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, slot);
+  AWG_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return AWG_OK;
+}
+
+template <int S, int P>
+awg_status run_degrid_exact(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
+  constexpr int tile = kClasses[class_of_support(S)].tile;
+  constexpr int nt = S * ExactCfg<S>::G;
+  using L = SepLayout<S, tile, P>;
+  auto kern = k_degrid_sep<S - 1, S, nt, tile, P>;
+  static int bps = 0;
+  if (bps == 0) {
+    AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+    AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, nt, L::bytes));
+    if (bps < 1) return set_error(AWG_ERR_CUDA, "exact-support degridding kernel does not fit on an SM");
+  }
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, slot);
+  AWG_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return AWG_OK;
+}
+
+#define AWG_FOR_EXACT_AND_POLS(M) \
+  M(8, 1) M(8, 2) M(8, 4) M(16, 1) M(16, 2) M(16, 4) M(24, 1) M(24, 2) M(24, 4) M(32, 1) M(32, 2) M(32, 4) \
+  M(40, 1) M(40, 2) M(40, 4) M(48, 1) M(48, 2) M(48, 4) M(56, 1) M(56, 2) M(56, 4) M(64, 1) M(64, 2) M(64, 4)
+#define AWG_DECLARE_GRID_EXACT(S, P) \
+  extern template awg_status run_grid_exact<S, P>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_DECLARE_DEGRID_EXACT(S, P) \
+  extern template awg_status run_degrid_exact<S, P>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_EXACT(S, P) template awg_status run_grid_exact<S, P>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_DEGRID_EXACT(S, P) \
+  template awg_status run_degrid_exact<S, P>(const DegridArgs&, int, int, cudaStream_t);
+
 #define AWG_FOR_SEP_CLASSES_AND_POLS(M) \
   M(0, 1) M(0, 2) M(0, 4) M(1, 1) M(1, 2) M(1, 4) M(2, 1) M(2, 2) M(2, 4) M(3, 1) M(3, 2) M(3, 4) M(4, 1) M(4, 2) M(4, 4) \
   M(5, 1) M(5, 2) M(5, 4)
 
-#define AWG_DECLARE_GRID_SEP(C, P) extern template awg_status run_grid_sep<C, P>(const GridArgs&, int, cudaStream_t);
+#define AWG_DECLARE_GRID_SEP(C, P) \
+  extern template awg_status run_grid_sep<C, P>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_DECLARE_DEGRID_SEP(C, P) \
-  extern template awg_status run_degrid_sep<C, P>(const DegridArgs&, int, cudaStream_t);
-#define AWG_INSTANTIATE_GRID_SEP(C, P) template awg_status run_grid_sep<C, P>(const GridArgs&, int, cudaStream_t);
+  extern template awg_status run_degrid_sep<C, P>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_SEP(C, P) template awg_status run_grid_sep<C, P>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_INSTANTIATE_DEGRID_SEP(C, P) \
-  template awg_status run_degrid_sep<C, P>(const DegridArgs&, int, cudaStream_t);
+  template awg_status run_degrid_sep<C, P>(const DegridArgs&, int, int, cudaStream_t);
 
 }  // namespace awg

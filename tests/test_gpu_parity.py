@@ -110,8 +110,10 @@ def test_cf_tables_match_oracle(awg, mode, separable):
 
 # ------------------------------------------------------------------------------------------ exact pins
 
-def test_delta_cf_is_exact_binning(awg):
-    """Support-1 delta CF with integer-valued data: G is direct binning, D direct lookup, bit exact."""
+@pytest.mark.parametrize("separable", [True, False])
+def test_delta_cf_is_exact_binning(awg, separable):
+    """Support-1 delta CF with integer-valued data: G is direct binning, D direct lookup, bit exact
+    (as factors 1 x 1 and as a full table)."""
     wl = synth.make_workload("standard", n_int=30, with_vis=False)
     N = wl.grid_n
     op = oracle_params(wl, oversampling=1, max_support=1, ps_support=1, use_ps=False)
@@ -119,7 +121,8 @@ def test_delta_cf_is_exact_binning(awg):
     n = wl.n_samples
     vis = (rng.integers(-8, 9, n) + 1j * rng.integers(-8, 9, n)).astype(np.complex64).reshape(-1, 1)
     wt = rng.integers(0, 4, n).astype(np.float32).reshape(-1, 1)
-    cf = awg.cf_set_create_from_table([1], np.ones(4, dtype=np.complex64), **library_params(op))
+    cf = awg.cf_set_create_from_table([1], np.ones(4, dtype=np.complex64), **library_params(op, separable=separable))
+    assert cf.separable == separable
     res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, vis, wt, cf=cf)
     sc = wl.freq_hz / synth.C_LIGHT
     u = (wl.uvw_m[:, 0:1] * sc).reshape(-1)
@@ -190,42 +193,50 @@ def test_awproj_parity(awg):
     assert rel_rms(res["vis"], orc["vis"]) < 1e-5
 
 
-@pytest.mark.parametrize("P", [1, 2, 4])
-def test_every_support_class_random_tables(awg, P):
-    """Random (non-symmetric) tables with supports 1..64 spread over all kernel classes; CF chosen
-    per row through the PA-bin index.  Also checks <G V, X> = <V, D X> on the GPU."""
+def _random_tables_case(awg, P, rank1):
     sups = [1, 3, 7, 8, 9, 15, 16, 17, 24, 25, 31, 32, 33, 40, 48, 49, 56, 63, 64]
     wl = synth.make_workload("standard", n_int=16, n_chan=3, f_lo=2.8e9, f_hi=3.2e9, with_vis=False)
     N = 384
     OS = 3
     op = ocf.CFParams(grid_n=N, cell_rad=wl.cell_rad * 512 / N * 0.45, oversampling=OS, ps_support=1, use_ps=False,
                       n_pa_bins=len(sups), max_support=64)
-    rng = np.random.default_rng(100 + P)
-    tables = {}
+    rng = np.random.default_rng(100 + P + (10 if rank1 else 0))
+
+    def cplx(*shape):
+        return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
     flat = []
-    for ci, S in enumerate(sups):
-        t = (rng.standard_normal((OS + 1, OS + 1, S, S)) + 1j * rng.standard_normal((OS + 1, OS + 1, S, S)))
-        t = t.astype(np.complex64).astype(np.complex128)
-        tables[ci] = t
-        flat.append(t.reshape(-1))
+    for S in sups:
+        if rank1:
+            # an outer product fy[oy][ty] fx[ox][tx]: stored as factors by the library
+            t = cplx(OS + 1, S)[:, None, :, None] * cplx(OS + 1, S)[None, :, None, :]
+        else:
+            t = cplx(OS + 1, OS + 1, S, S)
+        flat.append(t.astype(np.complex64).astype(np.complex128).reshape(-1))
     R, C = wl.n_rows, wl.n_chan
     pa_bin = rng.integers(0, len(sups), R).astype(np.int32)
     idx = oindex.sample_index(op, wl.uvw_m, wl.freq_hz, pa_bin=pa_bin, supports=sups)
     assert idx.valid.mean() > 0.5
+    assert set(np.unique(idx.support[idx.valid]).tolist()) == set(sups)
     offs = np.zeros(len(sups), dtype=np.int64)
     offs[1:] = np.cumsum([(OS + 1) ** 2 * s * s for s in sups])[:-1]
     buf = np.concatenate(flat)
     n = R * C
     V = (rng.standard_normal((n, P)) + 1j * rng.standard_normal((n, P))).astype(np.complex64)
     W = rng.uniform(0.5, 2.0, (n, P)).astype(np.float32)
-    cfset = awg.cf_set_create_from_table(sups, np.concatenate(flat).astype(np.complex64), grid_n=N,
-                                         cell_rad=op.cell_rad, oversampling=OS, n_pa_bins=len(sups))
+    cfset = awg.cf_set_create_from_table(sups, buf.astype(np.complex64), grid_n=N, cell_rad=op.cell_rad,
+                                         oversampling=OS, n_pa_bins=len(sups), separable=True)
+    assert cfset.separable == rank1
     res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, V, W, pa_bin=pa_bin, cf=cfset)
     g_o, sw_o = oops.grid(idx, buf, offs, OS, N, V.astype(np.complex128), W.astype(np.float64))
     assert rel_rms(res["grid"], g_o) < 1e-5
     assert np.allclose(res["sumwt"], sw_o, rtol=1e-12)
     d_o = oops.degrid(idx, buf, offs, OS, res["grid_used"].astype(np.complex128))
     assert rel_rms(res["vis"], d_o) < 1e-5
+    # per-support check: every kernel (exact-support or class) is right on its own samples
+    for S in sups:
+        m = idx.valid & (idx.support == S)
+        assert rel_rms(res["vis"][m], d_o[m]) < 1e-5, S
     # adjoint on the GPU with unit weights: <G V, X> = <V, D X>
     X = (rng.standard_normal((N, N, P)) + 1j * rng.standard_normal((N, N, P))).astype(np.complex64)
     plan = res["plan"]
@@ -237,6 +248,20 @@ def test_every_support_class_random_tables(awg, P):
     a = np.vdot(g.cpu().numpy().astype(np.complex128), X.astype(np.complex128))
     b = np.vdot(V.reshape(R, C, P).astype(np.complex128), dx.cpu().numpy().astype(np.complex128))
     assert abs(a - b) <= 1e-5 * abs(a)
+
+
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_every_support_class_random_tables(awg, P):
+    """Random (non-symmetric, full-rank) tables with supports 1..64 spread over all kernel classes;
+    CF chosen per row through the PA-bin index.  Also checks <G V, X> = <V, D X> on the GPU."""
+    _random_tables_case(awg, P, rank1=False)
+
+
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_every_support_separable_random_factors(awg, P):
+    """Random outer-product tables with the same supports: the separable path, every exact-support
+    kernel (8, 16, ..., 64) and every class kernel for the supports in between."""
+    _random_tables_case(awg, P, rank1=True)
 
 
 @pytest.mark.parametrize("separable", [True, False])
