@@ -29,6 +29,32 @@ __host__ __device__ constexpr int class_of_support(int S) {
   return S <= 8 ? 0 : S <= 16 ? 1 : S <= 24 ? 2 : S <= 32 ? 3 : S <= 48 ? 4 : S <= 64 ? 5 : -1;
 }
 
+// Separable kernels specialised for one support S (the W-projection schedule's multiples of 8):
+// row groups G of the gridding and degridding kernels (each thread owns S / G rows of one column
+// residue; S * G threads per CTA, a whole number of warps), the tile of first-tap positions per
+// work item, which the plan uses for these supports when the CF set is separable, and the
+// samples staged per chunk.  Small tiles and shallow stages let two CTAs share an SM.  The
+// supports listed here and AWG_FOR_EXACT_AND_POLS must agree.
+struct ExactCfg {
+  int S, g_grid, g_degrid, tile, stage;
+};
+constexpr ExactCfg kExact[] = {
+    {8, 8, 8, 32, 16},
+    {16, 8, 8, 16, 8},
+    {24, 8, 8, 16, 8},
+    {32, 8, 8, 16, 8},
+    {40, 8, 8, 8, 8},
+    {48, 16, 8, 16, 16},
+    {56, 8, 8, 16, 8},
+    {64, 8, 8, 8, 8},
+};
+constexpr ExactCfg exact_cfg(int S) {
+  for (const ExactCfg& e : kExact)
+    if (e.S == S) return e;
+  return ExactCfg{S, 0, 0, 0, 0};
+}
+constexpr bool has_exact(int S) { return exact_cfg(S).tile > 0; }
+
 // One kept sample in plan order (16 bytes, one vector load).
 struct __align__(16) SampleRec {
   int32_t src;      // row * C + chan

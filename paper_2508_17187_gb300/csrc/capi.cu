@@ -90,7 +90,7 @@ static void fill_slots(CfSetImpl* cf) {
     if (!present[s]) continue;
     const int i = st.n++;
     st.S[i] = s;
-    st.tile[i] = kClasses[class_of_support(s)].tile;
+    st.tile[i] = cf->separable && has_exact(s) ? exact_cfg(s).tile : kClasses[class_of_support(s)].tile;
     const int span = N - s + 1;    // possible first-tap positions per axis
     st.nt[i] = span > 0 ? (span + st.tile[i] - 1) / st.tile[i] : 0;
     st.base[i] = base;

@@ -41,10 +41,13 @@ awg_status grid_class(int c, int P, const GridArgs& a, int sms, cudaStream_t st)
 // Separable kernels run once per distinct support (slot): the exact-support kernel when there is
 // one for S, else the class kernel restricted to the slot's items.
 awg_status grid_slot_sep(int S, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
+  if (has_exact(S)) {   // the plan binned this support by its exact-kernel tile
 #define AWG_CASE(SS, PP) \
   if (S == SS && P == PP) return run_grid_exact<SS, PP>(a, slot, sms, st);
-  AWG_FOR_EXACT_AND_POLS(AWG_CASE)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE)
 #undef AWG_CASE
+    return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
+  }
   const int c = class_of_support(S);
 #define AWG_CASE(C, PP) \
   if (c == C && P == PP) return run_grid_sep<C, PP>(a, slot, sms, st);
@@ -54,10 +57,13 @@ awg_status grid_slot_sep(int S, int slot, int P, const GridArgs& a, int sms, cud
 }
 
 awg_status degrid_slot_sep(int S, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+  if (has_exact(S)) {   // the plan binned this support by its exact-kernel tile
 #define AWG_CASE(SS, PP) \
   if (S == SS && P == PP) return run_degrid_exact<SS, PP>(a, slot, sms, st);
-  AWG_FOR_EXACT_AND_POLS(AWG_CASE)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE)
 #undef AWG_CASE
+    return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
+  }
   const int c = class_of_support(S);
 #define AWG_CASE(C, PP) \
   if (c == C && P == PP) return run_degrid_sep<C, PP>(a, slot, sms, st);

@@ -40,14 +40,13 @@ __host__ __device__ constexpr int sep_rows(int smin, int smax, int nt) {
   return r;
 }
 
-// Staged samples per chunk: the factor rows of a chunk live in shared memory, twice (the chunk
-// being computed and the one being fetched).
+// Staged samples per chunk of the class kernels: the factor rows of a chunk live in shared
+// memory, twice (the chunk being computed and the one being fetched).
 __host__ __device__ constexpr int sep_stage(int smax) { return smax >= 56 ? 8 : 16; }
 
 // Shared-memory layout: the U x U window, then two slots of staged samples.
-template <int SMAX, int TILE, int P>
+template <int SMAX, int TILE, int P, int ST>
 struct SepLayout {
-  static constexpr int ST = sep_stage(SMAX);
   static constexpr int UMAX = TILE + SMAX - 1;
   // rounded up so that each slot starts 128-byte aligned (16-byte cp.async destinations)
   static constexpr size_t tile_bytes = ((size_t)UMAX * UMAX * P * sizeof(float2) + 127) & ~(size_t)127;
@@ -70,9 +69,18 @@ struct SepLayout {
   static constexpr size_t bytes = al_off + al_bytes;
 };
 
-template <int SMAX, int TILE, int P>
+// CTAs per SM that the shared-memory window allows (228 KB per SM, 1 KB reserved per CTA),
+// capped so that each thread keeps at least 96 registers: the min-blocks hint of the kernels.
+__host__ __device__ constexpr int sep_min_blocks(size_t smem_bytes, int nt) {
+  const int by_smem = (int)(233472 / (smem_bytes + 1024));
+  const int by_regs = 65536 / (nt * 96);
+  const int b = by_smem < by_regs ? by_smem : by_regs;
+  return b < 1 ? 1 : b;
+}
+
+template <int SMAX, int TILE, int P, int ST>
 struct SepSlot {
-  using L = SepLayout<SMAX, TILE, P>;
+  using L = SepLayout<SMAX, TILE, P, ST>;
   unsigned char* base;
   __device__ SepSlot(unsigned char* smem, int slot) : base(smem + L::tile_bytes + slot * L::slot_bytes) {}
   __device__ float2* f() const { return reinterpret_cast<float2*>(base + L::f_off); }
@@ -100,14 +108,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Records of chunk c into a slot (threads < nst, one 16-byte copy each).
-template <int SMAX, int TILE, int P>
-__device__ __forceinline__ void stage_recs(const SampleRec* rec, int start, int nst, const SepSlot<SMAX, TILE, P>& sl) {
+template <int SMAX, int TILE, int P, int ST>
+__device__ __forceinline__ void stage_recs(const SampleRec* rec, int start, int nst, const SepSlot<SMAX, TILE, P, ST>& sl) {
   if ((int)threadIdx.x < nst) cp_async(sl.rec() + threadIdx.x, rec + start + threadIdx.x, 16);
 }
 
 // From staged records: packed window offsets, factor-row offsets, sample index, phasor.
-template <int SMAX, int TILE, int P, class Args>
-__device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, int Y0, const SepSlot<SMAX, TILE, P>& sl) {
+template <int SMAX, int TILE, int P, int ST, class Args>
+__device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, int Y0, const SepSlot<SMAX, TILE, P, ST>& sl) {
   const int j = threadIdx.x;
   if (j < nst) {
     const SampleRec rc = sl.rec()[j];
@@ -122,9 +130,9 @@ __device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, in
 
 // Asynchronous copies of a chunk's factor rows (all threads) and, when vis != NULL, its
 // visibilities and weights (threads < nst).
-template <int SMAX, int TILE, int P, int NT>
+template <int SMAX, int TILE, int P, int ST, int NT>
 __device__ __forceinline__ void stage_payload(const float* sep, const float* vis, const float* weight, int nst, int S,
-                                              const SepSlot<SMAX, TILE, P>& sl) {
+                                              const SepSlot<SMAX, TILE, P, ST>& sl) {
   const float2* sep2 = reinterpret_cast<const float2*>(sep);
   const long long* fxo = sl.fxo();
   const long long* fyo = sl.fyo();
@@ -180,8 +188,8 @@ struct RowState {
 // alpha[j][rx][p] = conj(fx[j][(rx - mx_j) mod S]) * w_jp V_jp (* phasor): formed once per
 // chunk for every (sample, column residue) instead of by each of the G threads of a column.  The
 // threads below nst also add the chunk's weights to the sum of weights.
-template <int SMAX, int TILE, int P, int NT>
-__device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P>& sl, float2* alpha, int nst, int S,
+template <int SMAX, int TILE, int P, int ST, int NT>
+__device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P, ST>& sl, float2* alpha, int nst, int S,
                                            double (&wsum)[P]) {
   if ((int)threadIdx.x < nst) {
 #pragma unroll
@@ -206,8 +214,8 @@ __device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P>& sl, flo
 }
 
 // beta[j][rx] = fx[j][(rx - mx_j) mod S] for the degridding kernel.
-template <int SMAX, int TILE, int P, int NT>
-__device__ __forceinline__ void form_beta(const SepSlot<SMAX, TILE, P>& sl, float2* beta, int nst, int S) {
+template <int SMAX, int TILE, int P, int ST, int NT>
+__device__ __forceinline__ void form_beta(const SepSlot<SMAX, TILE, P, ST>& sl, float2* beta, int nst, int S) {
   for (int i = threadIdx.x; i < nst * S; i += NT) {
     const int j = i / S, rx = i - j * S;
     const int mx = (sl.pack()[j] >> 16) & 0xff;
@@ -217,14 +225,14 @@ __device__ __forceinline__ void form_beta(const SepSlot<SMAX, TILE, P>& sl, floa
   }
 }
 
-template <int SMIN, int SMAX, int NT, int TILE, int P>
-__global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls) {
+template <int SMIN, int SMAX, int NT, int TILE, int P, int ST>
+__global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST>::bytes, NT))
+    k_grid_sep(const GridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
-  constexpr int ST = sep_stage(SMAX);
-  using Slot = SepSlot<SMAX, TILE, P>;
+  using Slot = SepSlot<SMAX, TILE, P, ST>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
-  float2* alpha = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P>::al_off);
+  float2* alpha = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST>::al_off);
   __shared__ int s_item;
   __shared__ double s_wsum[NT / 32][P];
   static_assert(NT % 32 == 0, "the warp reductions need whole warps");
@@ -266,11 +274,11 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
       derive(a, nst_of(0), S, X0, Y0, s0);
       if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
       __syncthreads();
-      stage_payload<SMAX, TILE, P, NT>(a.sep, a.vis, a.weight, nst_of(0), S, s0);
+      stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(0), S, s0);
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      form_alpha<SMAX, TILE, P, NT>(s0, alpha, nst_of(0), S, wsum);
+      form_alpha<SMAX, TILE, P, ST, NT>(s0, alpha, nst_of(0), S, wsum);
       __syncthreads();
     }
 
@@ -289,7 +297,7 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
     }
     for (int c = 0; c < nch; ++c) {
       const Slot A(smem, c & 1), B(smem, (c & 1) ^ 1);
-      if (c + 1 < nch) stage_payload<SMAX, TILE, P, NT>(a.sep, a.vis, a.weight, nst_of(c + 1), S, B);
+      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(c + 1), S, B);
       if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
       cp_async_commit();
       const int nst = nst_of(c);
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(NT) k_grid_sep(const GridArgs a, const int cls
       __syncthreads();
       // slot A is free: derive chunk c+2 into it; chunk c+1's payload has landed in B: form w V
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
-      if (c + 1 < nch) form_alpha<SMAX, TILE, P, NT>(B, alpha, nst_of(c + 1), S, wsum);
+      if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT>(B, alpha, nst_of(c + 1), S, wsum);
       __syncthreads();
     }
 #pragma unroll
@@ -398,19 +406,19 @@ struct DegridCache {
   static constexpr bool enabled = R * P * 2 <= 48;
 };
 
-template <int SMIN, int SMAX, int NT, int TILE, int P>
-__global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int cls) {
+template <int SMIN, int SMAX, int NT, int TILE, int P, int ST>
+__global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST>::bytes, NT))
+    k_degrid_sep(const DegridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
   constexpr int NW = NT / 32;
   static_assert(NT % 32 == 0, "the warp reductions need whole warps");
   constexpr int B = 32 / (2 * P);
-  constexpr int ST = sep_stage(SMAX);
   constexpr bool CACHE = DegridCache<R, P>::enabled;
   constexpr int RC = CACHE ? R : 1;
-  using Slot = SepSlot<SMAX, TILE, P>;
+  using Slot = SepSlot<SMAX, TILE, P, ST>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
-  float2* beta = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P>::al_off);
+  float2* beta = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST>::al_off);
   __shared__ float s_red[2][NW][32];
   __shared__ int s_item;
 
@@ -455,11 +463,11 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
       derive(a, nst_of(0), S, X0, Y0, s0);
       if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
       __syncthreads();
-      stage_payload<SMAX, TILE, P, NT>(a.sep, nullptr, nullptr, nst_of(0), S, s0);
+      stage_payload<SMAX, TILE, P, ST, NT>(a.sep, nullptr, nullptr, nst_of(0), S, s0);
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      form_beta<SMAX, TILE, P, NT>(s0, beta, nst_of(0), S);
+      form_beta<SMAX, TILE, P, ST, NT>(s0, beta, nst_of(0), S);
       __syncthreads();
     }
     RowState<R> rs;
@@ -476,7 +484,7 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
     for (int k = 0; k < RC; ++k) curY[k] = -1;
     for (int c = 0; c < nch; ++c) {
       const Slot A(smem, c & 1), Bs(smem, (c & 1) ^ 1);
-      if (c + 1 < nch) stage_payload<SMAX, TILE, P, NT>(a.sep, nullptr, nullptr, nst_of(c + 1), S, Bs);
+      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT>(a.sep, nullptr, nullptr, nst_of(c + 1), S, Bs);
       if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
       cp_async_commit();
       const int nst = nst_of(c);
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(NT) k_degrid_sep(const DegridArgs a, const int
       cp_async_wait_all();
       __syncthreads();
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
-      if (c + 1 < nch) form_beta<SMAX, TILE, P, NT>(Bs, beta, nst_of(c + 1), S);
+      if (c + 1 < nch) form_beta<SMAX, TILE, P, ST, NT>(Bs, beta, nst_of(c + 1), S);
       __syncthreads();
     }
   }
@@ -585,8 +593,9 @@ awg_status run_grid_sep(const GridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr ClassCfg cc = kClasses[CLS];
   constexpr int smin = CLS == 0 ? 0 : kClasses[CLS > 0 ? CLS - 1 : 0].smax;
   constexpr int nt = kSepThreads[CLS];
-  using L = SepLayout<cc.smax, cc.tile, P>;
-  auto kern = k_grid_sep<smin, cc.smax, nt, cc.tile, P>;
+  constexpr int st_depth = sep_stage(cc.smax);
+  using L = SepLayout<cc.smax, cc.tile, P, st_depth>;
+  auto kern = k_grid_sep<smin, cc.smax, nt, cc.tile, P, st_depth>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
@@ -604,8 +613,9 @@ awg_status run_degrid_sep(const DegridArgs& a, int slot, int sms, cudaStream_t s
   constexpr ClassCfg cc = kClasses[CLS];
   constexpr int smin = CLS == 0 ? 0 : kClasses[CLS > 0 ? CLS - 1 : 0].smax;
   constexpr int nt = kSepThreads[CLS];
-  using L = SepLayout<cc.smax, cc.tile, P>;
-  auto kern = k_degrid_sep<smin, cc.smax, nt, cc.tile, P>;
+  constexpr int st_depth = sep_stage(cc.smax);
+  using L = SepLayout<cc.smax, cc.tile, P, st_depth>;
+  auto kern = k_degrid_sep<smin, cc.smax, nt, cc.tile, P, st_depth>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
@@ -618,26 +628,17 @@ awg_status run_degrid_sep(const DegridArgs& a, int slot, int sms, cudaStream_t s
   return AWG_OK;
 }
 
-// Exact-support kernels for the supports of the W-projection schedule: S is a compile-time
-// constant and G (rows groups) divides S, so every thread owns S / G rows; S * G is a whole
-// number of warps.
-template <int S>
-struct ExactCfg;
-template <> struct ExactCfg<8> { static constexpr int G = 8; };
-template <> struct ExactCfg<16> { static constexpr int G = 16; };
-template <> struct ExactCfg<24> { static constexpr int G = 12; };
-template <> struct ExactCfg<32> { static constexpr int G = 16; };
-template <> struct ExactCfg<40> { static constexpr int G = 20; };
-template <> struct ExactCfg<48> { static constexpr int G = 16; };
-template <> struct ExactCfg<56> { static constexpr int G = 8; };
-template <> struct ExactCfg<64> { static constexpr int G = 8; };
-
+// Exact-support kernels (the kExact table): S is a compile-time constant and the row groups
+// divide S, so every thread owns the same number of rows.
 template <int S, int P>
 awg_status run_grid_exact(const GridArgs& a, int slot, int sms, cudaStream_t st) {
-  constexpr int tile = kClasses[class_of_support(S)].tile;
-  constexpr int nt = S * ExactCfg<S>::G;
-  using L = SepLayout<S, tile, P>;
-  auto kern = k_grid_sep<S - 1, S, nt, tile, P>;
+  constexpr ExactCfg e = exact_cfg(S);
+  constexpr int nt = S * e.g_grid;
+  static_assert(e.tile > 0 && S % e.g_grid == 0 && nt <= 1024 && e.stage >= 1 && e.stage <= nt,
+                "bad exact-support configuration");
+  using L = SepLayout<S, e.tile, P, e.stage>;
+  static_assert(L::bytes <= 227 * 1024, "exact-support gridding window does not fit in shared memory");
+  auto kern = k_grid_sep<S - 1, S, nt, e.tile, P, e.stage>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
@@ -652,10 +653,13 @@ awg_status run_grid_exact(const GridArgs& a, int slot, int sms, cudaStream_t st)
 
 template <int S, int P>
 awg_status run_degrid_exact(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
-  constexpr int tile = kClasses[class_of_support(S)].tile;
-  constexpr int nt = S * ExactCfg<S>::G;
-  using L = SepLayout<S, tile, P>;
-  auto kern = k_degrid_sep<S - 1, S, nt, tile, P>;
+  constexpr ExactCfg e = exact_cfg(S);
+  constexpr int nt = S * e.g_degrid;
+  static_assert(e.tile > 0 && S % e.g_degrid == 0 && nt <= 1024 && e.stage >= 1 && e.stage <= nt,
+                "bad exact-support configuration");
+  using L = SepLayout<S, e.tile, P, e.stage>;
+  static_assert(L::bytes <= 227 * 1024, "exact-support degridding window does not fit in shared memory");
+  auto kern = k_degrid_sep<S - 1, S, nt, e.tile, P, e.stage>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
