@@ -242,6 +242,17 @@ awg_status degrid_visibilities_plain_fp64(awg_cf_set cf, const double* uvw_m, in
                                           int32_t chan_end, const int32_t* pa_bin, const int32_t* chan_subband_host,
                                           const void* grid64, void* vis_out, int32_t n_pol, void* stream);
 
+/*
+ * FP32 FMA probe (a measurement utility; the paper has no counterpart): launches n_blocks CTAs
+ * of 256 threads on `stream`, each thread running `iters` iterations of 8 independent FP32
+ * fused multiply-adds, and writes one float per thread to out (device, n_blocks * 256 floats,
+ * caller-owned) so the work cannot be elided.  *flop (host) receives the FLOP count of the
+ * launch (2 per FMA).  The caller times the launch on `stream`; FLOP / time is the rate of the
+ * non-tensor FP32 pipe that bounds gridding and degridding.  Asynchronous.
+ * Errors: INVALID_ARG, CUDA.
+ */
+awg_status awg_fp32_fma_probe(float* out, int32_t n_blocks, int64_t iters, void* stream, double* flop);
+
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* awg_last_error(void);
 

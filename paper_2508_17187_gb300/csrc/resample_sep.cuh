@@ -162,6 +162,22 @@ __device__ __forceinline__ void stage_payload(const float* sep, const float* vis
   }
 }
 
+// P consecutive complex values from shared memory (16-byte loads where the layout allows).
+template <int P>
+__device__ __forceinline__ void load_pols(const float2* src, float2 (&out)[P]) {
+  if constexpr (P % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(src)[q];
+      out[2 * q] = make_float2(v.x, v.y);
+      out[2 * q + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) out[p] = src[p];
+  }
+}
+
 // Per-thread row state of the separable kernels.  The rows a thread owns are ry0 + k G (k < R,
 // valid while below S); for a sample whose first tap is (p0x, p0y) the row residue ry touches
 // window row dy + ((ry - p0y) mod S).  Samples of an item are sorted row-major, so that state is
@@ -259,6 +275,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     unsigned vmask = 0;
 #pragma unroll
     for (int k = 0; k < R; ++k) vmask |= (ry0 + k * G < S) ? (1u << k) : 0u;
+    if (SMIN + 1 == SMAX) vmask = (1u << R) - 1;   // G divides S: every thread owns R rows
     const int nch = (wi.count + ST - 1) / ST;
     auto nst_of = [&](int c) { return min(ST, wi.count - c * ST); };
     const int UU = U * U;   // the window is pol-planar: tile[p * UU + pixel]
@@ -283,7 +300,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     }
 
     RowState<R> rs;
-    int prev_row = -1;
+    int prev_row = -1, prev_pk = -1;
     int curX = -1;
     int curY[R];
     float2 acc[R][P];
@@ -305,37 +322,39 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
         for (int j = 0; j < nst; ++j) {
           const int pk = A.pack()[j];
           float2 al[P];
-#pragma unroll
-          for (int p = 0; p < P; ++p) al[p] = alpha[(j * SMAX + rx) * P + p];
-          const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
-          const int row = pk & 0xff00ff00;   // (dy, my): identical for the whole CTA
-          bool row_changed = false;
-          if (row != prev_row) {
-            prev_row = row;
-            rs.update(ry0, G, S, (pk >> 8) & 0xff, (pk >> 24) & 0xff, vmask);
-            row_changed = true;
-          }
-          int tx = rx - mx;
-          tx += (tx < 0) ? S : 0;
-          const int X = dx + tx;
-          if (X != curX || row_changed) {
-            const bool xchg = X != curX;
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-              if ((vmask & (1u << k)) && (xchg || rs.Y[k] != curY[k])) {
-                if (curY[k] >= 0) {
-#pragma unroll
-                  for (int p = 0; p < P; ++p) {
-                    float2* t = tile + p * UU + curY[k] * U + curX;
-                    t->x += acc[k][p].x;
-                    t->y += acc[k][p].y;
-                    acc[k][p] = make_float2(0.f, 0.f);
-                  }
-                }
-                curY[k] = rs.Y[k];
-              }
+          load_pols<P>(alpha + (j * SMAX + rx) * P, al);
+          if (pk != prev_pk) {   // the first tap moved (the same test in every thread of the CTA)
+            prev_pk = pk;
+            const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
+            const int row = pk & 0xff00ff00;   // (dy, my)
+            bool row_changed = false;
+            if (row != prev_row) {
+              prev_row = row;
+              rs.update(ry0, G, S, (pk >> 8) & 0xff, (pk >> 24) & 0xff, vmask);
+              row_changed = true;
             }
-            curX = X;
+            int tx = rx - mx;
+            tx += (tx < 0) ? S : 0;
+            const int X = dx + tx;
+            if (X != curX || row_changed) {
+              const bool xchg = X != curX;
+#pragma unroll
+              for (int k = 0; k < R; ++k) {
+                if ((vmask & (1u << k)) && (xchg || rs.Y[k] != curY[k])) {
+                  if (curY[k] >= 0) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                      float2* t = tile + p * UU + curY[k] * U + curX;
+                      t->x += acc[k][p].x;
+                      t->y += acc[k][p].y;
+                      acc[k][p] = make_float2(0.f, 0.f);
+                    }
+                  }
+                  curY[k] = rs.Y[k];
+                }
+              }
+              curX = X;
+            }
           }
           const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
 #pragma unroll
@@ -442,6 +461,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     unsigned vmask = 0;
 #pragma unroll
     for (int k = 0; k < R; ++k) vmask |= (ry0 + k * G < S) ? (1u << k) : 0u;
+    if (SMIN + 1 == SMAX) vmask = (1u << R) - 1;   // G divides S: every thread owns R rows
     const int nch = (wi.count + ST - 1) / ST;
     auto nst_of = [&](int c) { return min(ST, wi.count - c * ST); };
     const int UU = U * U;   // the window is pol-planar: tile[p * UU + pixel]
@@ -471,8 +491,8 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       __syncthreads();
     }
     RowState<R> rs;
-    int prev_row = -1;
-    int curX = -1;
+    int prev_row = -1, prev_pk = -1;
+    int curX = -1, X = 0;
     int curY[RC];
     float2 gc[RC][P];
 #pragma unroll
@@ -498,29 +518,32 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
           if (active && j < nst) {
             const int pk = A.pack()[j];
             const float2 fxv = beta[j * SMAX + rx];
-            const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
-            const int row = pk & 0xff00ff00;
-            bool row_changed = false;
-            if (row != prev_row) {
-              prev_row = row;
-              rs.update(ry0, G, S, (pk >> 8) & 0xff, (pk >> 24) & 0xff, vmask);
-              row_changed = true;
-            }
-            int tx = rx - mx;
-            tx += (tx < 0) ? S : 0;
-            const int X = dx + tx;
-            if constexpr (CACHE) {
-              if (X != curX || row_changed) {
-                const bool xchg = X != curX;
+            if (pk != prev_pk) {   // the first tap moved (the same test in every thread of the CTA)
+              prev_pk = pk;
+              const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
+              const int row = pk & 0xff00ff00;
+              bool row_changed = false;
+              if (row != prev_row) {
+                prev_row = row;
+                rs.update(ry0, G, S, (pk >> 8) & 0xff, (pk >> 24) & 0xff, vmask);
+                row_changed = true;
+              }
+              int tx = rx - mx;
+              tx += (tx < 0) ? S : 0;
+              X = dx + tx;
+              if constexpr (CACHE) {
+                if (X != curX || row_changed) {
+                  const bool xchg = X != curX;
 #pragma unroll
-                for (int k = 0; k < RC; ++k) {
-                  if ((vmask & (1u << k)) && (xchg || rs.Y[k] != curY[k])) {
-                    curY[k] = rs.Y[k];
+                  for (int k = 0; k < RC; ++k) {
+                    if ((vmask & (1u << k)) && (xchg || rs.Y[k] != curY[k])) {
+                      curY[k] = rs.Y[k];
 #pragma unroll
-                    for (int p = 0; p < P; ++p) gc[k][p] = tile[p * UU + curY[k] * U + X];
+                      for (int p = 0; p < P; ++p) gc[k][p] = tile[p * UU + curY[k] * U + X];
+                    }
                   }
+                  curX = X;
                 }
-                curX = X;
               }
             }
             const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
