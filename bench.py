@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-every", type=int, default=None,
                     help="oracle sample: every k-th integration (default 40 for cpu_baseline, 200 per reference step)")
+    ap.add_argument("--config", choices=["wproj", "awproj"], default="wproj",
+                    help="wproj: the W-projection workload (default); awproj: the batched AW-projection workload "
+                         "(20 PA bins x 32 w-planes x 16 sub-bands, CFs as sums of outer products)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="CF storage / accumulation variants against the FP64 oracle (one JSON line each)")
     return ap.parse_args()
@@ -155,7 +158,7 @@ def measured_traffic(op: str):
     """DRAM bytes per full-size launch of `op` from the committed ncu summary, or None when the
     kernels have changed since the counters were taken."""
     try:
-        with open(os.path.join(ROOT, "profiles", "dram_traffic_wproj.json")) as f:
+        with open(os.path.join(ROOT, "profiles", f"dram_traffic_{CONFIG}.json")) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
@@ -383,8 +386,29 @@ def precision_sweep(args):
     return 0
 
 
+WORKLOADS = {
+    "wproj": "W-projection: 351 baselines x 2000 integrations x 64 channels (2-4 GHz) x 4 pols per rank, 64 w-planes, "
+             "CF supports 8-64, oversampling 20, 4096x4096x4 c64 grid",
+    "awproj": "batched AW-projection: 351 baselines x 2000 integrations x 64 channels (2-4 GHz) x 4 pols per rank, "
+              "20 PA bins x 32 w-planes x 16 sub-bands = 10,240 A-term CFs (20,160 signed), supports 8-64, "
+              "oversampling 20, 4096x4096x4 c64 grid",
+}
+
+
+def cf_kwargs(wl) -> dict:
+    """cf_set_create arguments of a workload."""
+    kw = dict(grid_n=wl.grid_n, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support,
+              use_w=wl.use_w, n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda, max_support=wl.max_support)
+    if wl.use_a:
+        kw.update(use_a=True, n_pa_bins=wl.n_pa_bins, pa_bin_centers_rad=np.asarray(wl.pa_bin_centers),
+                  n_subbands=wl.n_subbands, subband_freq_hz=np.asarray(wl.subband_freq_hz))
+    return kw
+
+
 def main():
+    global CONFIG
     args = parse()
+    CONFIG = args.config
     if args.impl == "reference":
         return reference_arm(args)
     if args.precision_sweep:
@@ -406,13 +430,15 @@ def main():
     R, C = wl.n_rows, wl.n_chan
     lib = _lib.load()
 
-    cf = awg.cf_set_create(grid_n=N, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support,
-                           use_w=True, n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda,
-                           max_support=wl.max_support)
+    t_cf = time.perf_counter()
+    cf = awg.cf_set_create(**cf_kwargs(wl))
+    t_cf = time.perf_counter() - t_cf
     uvw = torch.as_tensor(wl.uvw_m, device=dev)
     freq = torch.as_tensor(wl.freq_hz, device=dev)
+    pa_bin = torch.as_tensor(wl.pa_bin, device=dev) if wl.use_a else None
+    chan_sb = torch.as_tensor(wl.chan_subband, device=dev) if wl.use_a else None
     vis, wt = wl.vis, wl.weight
-    plan = awg.plan_create(cf, uvw, freq)
+    plan = awg.plan_create(cf, uvw, freq, pa_bin, chan_sb)
     kept, dropped, sum_taps = plan.stats()
     grid = torch.zeros((N, N, P), dtype=torch.complex64, device=dev)
     sumwt = torch.zeros(P, dtype=torch.float64, device=dev)
@@ -436,7 +462,7 @@ def main():
     def step(record=False):
         if record:
             ev[0].record(stream)
-        plan.update(uvw, freq)
+        plan.update(uvw, freq, pa_bin, chan_sb)
         if record:
             ev[1].record(stream)
         grid.zero_()
@@ -498,6 +524,8 @@ def main():
         h_wt = wt.cpu().pin_memory()
         h_uvw = uvw.cpu().pin_memory()
         h_freq = freq.cpu().pin_memory()
+        h_pa = pa_bin.cpu().pin_memory() if pa_bin is not None else None
+        h_sb = chan_sb.cpu().pin_memory() if chan_sb is not None else None
         h_out = torch.empty(vis_out.shape, dtype=vis_out.dtype).pin_memory()
         h_grid = torch.empty(grid.shape, dtype=grid.dtype).pin_memory()
         h_sw = torch.empty(sumwt.shape, dtype=sumwt.dtype).pin_memory()
@@ -507,6 +535,9 @@ def main():
             wt.copy_(h_wt, non_blocking=True)
             uvw.copy_(h_uvw, non_blocking=True)
             freq.copy_(h_freq, non_blocking=True)
+            if h_pa is not None:
+                pa_bin.copy_(h_pa, non_blocking=True)
+                chan_sb.copy_(h_sb, non_blocking=True)
             step()
             h_out.copy_(vis_out, non_blocking=True)
             h_grid.copy_(grid, non_blocking=True)
@@ -528,6 +559,8 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e_ms = float(tt.item())
         h2d = vis.numel() * 8 + wt.numel() * 4 + uvw.numel() * 8 + freq.numel() * 8
+        if pa_bin is not None:
+            h2d += pa_bin.numel() * 4 + chan_sb.numel() * 4
         d2h = vis_out.numel() * 8 + grid.numel() * 8 + sumwt.numel() * 8
         e2e = {"value": vis_per_step / (e_ms / 1e3), "unit": "visibilities/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
@@ -562,8 +595,8 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic VLA A-array-like uvw, 200 point sources + 1 mJy noise, natural weights",
-        "config": {"workload": "W-projection: 351 baselines x 2000 integrations x 64 channels (2-4 GHz) x 4 pols "
-                               "per rank, 64 w-planes, CF supports 8-64, oversampling 20, 4096x4096x4 c64 grid",
+        "config": {"workload": WORKLOADS[CONFIG], "cf_terms": max(cf.rank, 1), "cf_storage":
+                   "separable factors" if cf.separable else "full tables", "cf_build_s": t_cf,
                    "visibilities_per_step": vis_per_step, "kept_samples": kept, "dropped_samples": dropped,
                    "mean_taps": sum_taps / max(kept, 1), "l2": "inputs larger than L2 (2.7 GB per step)",
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
@@ -582,7 +615,10 @@ def main():
         "gpu_launches": int(launches),
         "e2e": e2e,
     }
-    if not args.no_cpu_baseline:
+    if cf.separable and cf.rank > 1:
+        # the kernels run one rank-1 record per (sample, term): rank x the method's arithmetic
+        line["executed_tflops"] = {k: max(cf.rank, 1) * ops[k]["tflops"] for k in ops}
+    if not args.no_cpu_baseline and CONFIG == "wproj":
         host_wl = dataclasses.replace(wl, vis=vis.cpu().numpy(), weight=wt.cpu().numpy())
         cb = run_cpu_baseline(host_wl, args.cpu_sample_every or 40)
         cb.pop("seconds")

@@ -90,19 +90,24 @@ typedef struct {
   double dish_diameter_m;           /* A-term aperture (e.g. 25) */
   double ellipticity;               /* A-term distortion (e.g. 0.05) */
   int cf_dtype;                     /* AWG_CF_FP32 or AWG_CF_BF16 */
-  int separable;                    /* 1: store each CF as an outer product fy[oy][ty] fx[ox][tx] when
-                                       every CF of the set fits one to 1e-7 of its peak (PS and
-                                       W-projection CFs do; A-terms do not); 0: always full tables */
+  int separable;                    /* 1: store each CF as a sum of r <= 6 outer products
+                                       fy_k[oy][ty] fx_k[ox][tx] when every CF of the set fits one
+                                       to 1e-6 of its peak (PS and W-projection CFs with r = 1,
+                                       A-term CFs with r of about 4); 0: always full tables */
 } awg_cf_params;
 
 /*
  * Build the CF set on the host in FP64 (PreCompute, Sec. 4.1 and Sec. 6 CFCache) and upload it,
  * rounded to cf_dtype, to the current device.  Negative-w planes are the conjugate point
  * reflections of the positive ones (screen(-w) = conj(screen(w))).  With params->separable and FP32
- * storage, each table seen as a ((OS+1) S)^2 matrix is fitted as g f^T (alternating least squares);
- * if every fit is within 1e-7 of the table's peak only the factors are kept (2 (OS+1) S values per
- * CF instead of ((OS+1) S)^2), otherwise the full tables are.  Blocking: returns once the
- * tables are resident.  Errors: INVALID_ARG (bad params), UNSUPPORTED (max_support > 64), OOM.
+ * storage, each table seen as a ((OS+1) S)^2 matrix is fitted as sum_k g_k f_k^T, one term at a
+ * time from the residual (alternating least squares), until the residual is within 1e-6 of the
+ * table's peak; if every CF fits with at most 6 terms only the factors are kept (2 (OS+1) S values
+ * per term instead of ((OS+1) S)^2 per CF; the set's rank r is the largest term count, smaller fits
+ * are padded with zero terms), otherwise the full tables are.  A plan on a rank-r set holds r
+ * records per sample, so gridding and degridding cost r times the rank-1 work.  Blocking: returns
+ * once the tables are resident.  Errors: INVALID_ARG (bad params), UNSUPPORTED (max_support > 64),
+ * OOM.
  */
 awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* out);
 
@@ -111,22 +116,23 @@ awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* 
  * supports: host [n_cf] taps per CF (1..64); table: host c64, all CFs concatenated in CF-index
  * order, each [OS+1][OS+1][S][S].  Only grid_n, oversampling, use_w, n_wplanes, w_max_lambda,
  * n_pa_bins, n_subbands, cf_dtype and separable of params are read.  With separable and FP32
- * storage, only factors are kept when every table is an outer product fy[oy][ty] fx[ox][tx] to
- * 1e-6 of its peak (the accuracy of FP32 input); otherwise the full tables are.
+ * storage, only factors are kept when every table is a sum of at most 6 outer products to 1e-6 of
+ * its peak (the fit of cf_set_create); otherwise the full tables are.
  */
 awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* supports,
                                     const float* table, void* stream, awg_cf_set* out);
 
 awg_status cf_set_destroy(awg_cf_set cf);
 
-/* Number of CFs, complex values held (2-D tables or factors) and whether the set is separable. */
+/* Number of CFs, complex values held (2-D tables or factors) and the separable rank: the number of
+ * outer-product terms per CF, or 0 for full tables. */
 awg_status cf_set_info(awg_cf_set cf, int32_t* n_cf, int64_t* n_values, int32_t* separable);
 
 /* Host copy of the support of every CF: supports_out host [n_cf]. */
 awg_status cf_set_get_supports(awg_cf_set cf, int32_t* supports_out);
 
 /* Host copy of one CF table as c64 [OS+1][OS+1][S][S] (BF16 tables are widened; a separable CF
- * is expanded as the FP32 product fy fx). Blocking. */
+ * is expanded as the sum of its FP32 products fy_k fx_k). Blocking. */
 awg_status cf_set_copy_table(awg_cf_set cf, int32_t cf_index, float* table_out);
 
 /*

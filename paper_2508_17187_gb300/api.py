@@ -55,7 +55,8 @@ class CFSet:
               "cf_set_info")
         self.n_cf = int(n_cf.value)
         self.n_values = int(n_val.value)
-        self.separable = bool(sep.value)
+        self.rank = int(sep.value)            # outer-product terms per CF; 0 for full tables
+        self.separable = self.rank > 0
 
     @property
     def handle(self):

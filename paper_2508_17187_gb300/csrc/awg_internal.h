@@ -98,7 +98,8 @@ struct CfSetImpl {
   SlotTable slots{};
   // Separable storage: CF = fy[oy][ty] * fx[ox][tx]; per CF, fx [OS+1][S] then fy [OS+1][S] c64.
   int separable = 0;
-  std::vector<int64_t> sep_offsets;
+  int rank = 1;                      // outer-product terms per CF when separable
+  std::vector<int64_t> sep_offsets;  // [n_cf * rank]: element offset of term k of CF c at c * rank + k
   void* d_sep = nullptr;
   int64_t* d_sep_off = nullptr;
 };
@@ -108,6 +109,9 @@ struct PlanImpl {
   int64_t R = 0;
   int C = 0;
   int64_t n = 0;
+  int rank = 1;        // records per sample: the CF set's terms per CF
+  int64_t n_rec = 0;   // n * rank
+  float2* d_part = nullptr;   // rank > 1: per-term degridded values [n][rank][4 pols]
   int has_phase = 0;
   double dl = 0, dm = 0, dn = 0;
   int device = 0;
@@ -152,10 +156,18 @@ int screen_size(int S);
 void build_cf_table(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa,
                     int sb, int ks, std::vector<double>& out /* 2 (OS+1)^2 S^2 */);
 void taper_image(const awg_cf_params& p, std::vector<double>& out /* N */);
-// Rank-1 fit C = g f^T of a table seen as a ((OS+1) S) x ((OS+1) S) matrix; true when the
-// residual is at most tol of the peak.  fx = f, fy = g, interleaved complex.
-bool factor_rank1(const std::vector<double>& tab, int S, int OS, double tol, std::vector<double>& fx,
-                  std::vector<double>& fy);
+// Low-rank fit C = sum_k g_k f_k^T (k < r) of a table seen as a ((OS+1) S) x ((OS+1) S) matrix:
+// the smallest r <= r_max whose residual is at most tol of the peak, or 0 when there is none.
+// fx = [f_0, f_1, ...], fy = [g_0, g_1, ...], each term (OS+1) S interleaved complex values.
+int factor_low_rank(const std::vector<double>& tab, int S, int OS, double tol, int r_max, std::vector<double>& fx,
+                    std::vector<double>& fy);
+// The same fit for a built CF, done on its M x M image-plane screen (the CF is the screen's
+// separable 2-D transform, so screen terms map to CF terms); the residual is checked on the CF's
+// offset slices (0, OS/2, OS)^2.  Returns the term count, or 0 when r_max terms do not reach tol.
+int build_cf_factors(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa, int sb,
+                     int ks, double tol, int r_max, std::vector<double>& fx, std::vector<double>& fy);
+constexpr int kMaxRank = 6;        // outer-product terms per CF at most (separable storage)
+constexpr double kSepTol = 1e-6;   // largest accepted residual of the fit, relative to the peak
 
 // Plan kernels (plan.cu).
 awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const int32_t* pa_bin,

@@ -166,31 +166,45 @@ static awg_status alloc_cf(CfSetImpl* cf, cudaStream_t st) {
   return AWG_OK;
 }
 
-// Upload the factors fx[ci], fy[ci] (FP64 pairs, [(OS+1) S] each) of every CF as the separable
-// storage, with the support / offset bookkeeping the plan shares with the 2-D layout.
+// Upload the factors of every CF as the separable storage, with the support / offset bookkeeping
+// the plan shares with the 2-D layout.  fx[ci], fy[ci] hold the CF's terms back to back (FP64
+// pairs, [(OS+1) S] per term); the set's rank is the largest term count, and a CF with fewer
+// terms gets zero terms (all of them point at one zero block at the start of the storage).
 static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<double>>& fx,
                                    const std::vector<std::vector<double>>& fy, cudaStream_t st) {
   const int OS = cf->p.oversampling;
+  int rank = 1;
+  for (int i = 0; i < cf->n_cf; ++i)
+    rank = std::max(rank, (int)(fx[i].size() / (2 * (size_t)(OS + 1) * cf->supports[i])));
   cf->separable = 1;
-  cf->sep_offsets.resize(cf->n_cf);
-  int64_t off = 0;
-  for (int i = 0; i < cf->n_cf; ++i) {
-    cf->sep_offsets[i] = off;
-    off += 2 * (int64_t)(OS + 1) * cf->supports[i];
-  }
-  cf->n_values = off;
-  std::vector<float> h((size_t)2 * off);
+  cf->rank = rank;
+  cf->sep_offsets.assign((size_t)cf->n_cf * rank, 0);
+  int64_t off = 2 * (int64_t)(OS + 1) * kMaxSupport;   // the zero block (fx and fy of the largest support)
   for (int i = 0; i < cf->n_cf; ++i) {
     const int64_t q = (int64_t)(OS + 1) * cf->supports[i];
-    for (int64_t t = 0; t < 2 * q; ++t) {
-      h[2 * cf->sep_offsets[i] + t] = (float)fx[i][t];
-      h[2 * cf->sep_offsets[i] + 2 * q + t] = (float)fy[i][t];
+    const int r_i = (int)(fx[i].size() / (2 * q));
+    for (int k = 0; k < r_i; ++k) {
+      cf->sep_offsets[(size_t)i * rank + k] = off;
+      off += 2 * q;
+    }
+  }
+  cf->n_values = off;
+  std::vector<float> h((size_t)2 * off, 0.f);
+  for (int i = 0; i < cf->n_cf; ++i) {
+    const int64_t q = (int64_t)(OS + 1) * cf->supports[i];
+    const int r_i = (int)(fx[i].size() / (2 * q));
+    for (int k = 0; k < r_i; ++k) {
+      const int64_t o = 2 * cf->sep_offsets[(size_t)i * rank + k];
+      for (int64_t t = 0; t < 2 * q; ++t) {
+        h[o + t] = (float)fx[i][2 * q * k + t];
+        h[o + 2 * q + t] = (float)fy[i][2 * q * k + t];
+      }
     }
   }
   AWG_CUDA_TRY(cudaMalloc(&cf->d_sep, sizeof(float) * h.size()));
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep_off, sizeof(int64_t) * cf->n_cf));
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep_off, sizeof(int64_t) * cf->sep_offsets.size()));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
-  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep_off, cf->sep_offsets.data(), sizeof(int64_t) * cf->n_cf,
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep_off, cf->sep_offsets.data(), sizeof(int64_t) * cf->sep_offsets.size(),
                                cudaMemcpyHostToDevice, st));
   // the support / offset bookkeeping the plan and the kernels share with the 2-D layout
   AWG_CUDA_TRY(cudaMalloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
@@ -206,9 +220,10 @@ static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<
   return AWG_OK;
 }
 
-// Separable storage: build every non-negative plane, fit it as fy fx, mirror the fit for the
+// Separable storage: fit every non-negative plane as a sum of at most kMaxRank outer products
+// fy fx (from its image-plane screen, without forming the 2-D table), mirror the fit for the
 // negative planes, upload only the factors.  Returns AWG_ERR_UNSUPPORTED (nothing allocated on
-// the device) when some CF is not separable to 1e-7 of its peak.
+// the device) when some CF needs more terms than that to come within kSepTol of its peak.
 static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
   const awg_cf_params& p = cf->p;
   cf->n_signed = p.use_w ? 2 * p.n_wplanes - 1 : 1;
@@ -223,27 +238,29 @@ static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
     const int k = j % n_w, pasb = j / n_w;
     const int pa = pasb / p.n_subbands, sb = pasb % p.n_subbands;
     const int ks = p.use_w ? p.n_wplanes - 1 + k : 0;
-    std::vector<double> tab;
-    build_cf_table(p, cf->pa_centers.data(), cf->sb_freqs.data(), pa, sb, ks, tab);
     const int S = support_of_plane(p, ks);
     const int ci = pasb * cf->n_signed + ks;
-    if (!factor_rank1(tab, S, OS, 1e-7, fx[ci], fy[ci])) {
+    if (build_cf_factors(p, cf->pa_centers.data(), cf->sb_freqs.data(), pa, sb, ks, kSepTol, kMaxRank, fx[ci],
+                         fy[ci]) == 0) {
 #pragma omp atomic write
       failed = 1;
       continue;
     }
     if (p.use_w && k > 0) {
-      // table(-w) = conj(table(+w)) point-reflected: the factors reversed and conjugated
+      // table(-w) = conj(table(+w)) point-reflected: each term's factors reversed and conjugated
       const int cn = pasb * cf->n_signed + (p.n_wplanes - 1 - k);
-      const size_t q = fx[ci].size() / 2;
-      fx[cn].resize(2 * q);
-      fy[cn].resize(2 * q);
-      for (size_t i = 0; i < q; ++i) {
-        fx[cn][2 * i] = fx[ci][2 * (q - 1 - i)];
-        fx[cn][2 * i + 1] = -fx[ci][2 * (q - 1 - i) + 1];
-        fy[cn][2 * i] = fy[ci][2 * (q - 1 - i)];
-        fy[cn][2 * i + 1] = -fy[ci][2 * (q - 1 - i) + 1];
-      }
+      const size_t q = (size_t)(OS + 1) * S;
+      const size_t terms = fx[ci].size() / (2 * q);
+      fx[cn].resize(fx[ci].size());
+      fy[cn].resize(fy[ci].size());
+      for (size_t t = 0; t < terms; ++t)
+        for (size_t i = 0; i < q; ++i) {
+          const size_t d = 2 * (t * q + i), sidx = 2 * (t * q + q - 1 - i);
+          fx[cn][d] = fx[ci][sidx];
+          fx[cn][d + 1] = -fx[ci][sidx + 1];
+          fy[cn][d] = fy[ci][sidx];
+          fy[cn][d + 1] = -fy[ci][sidx + 1];
+        }
     }
   }
   if (failed) return AWG_ERR_UNSUPPORTED;
@@ -396,7 +413,7 @@ awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* 
       const int S = cf->supports[ci];
       const int64_t nv = (int64_t)(params->oversampling + 1) * (params->oversampling + 1) * S * S;
       std::vector<double> tab(table + 2 * offs[ci], table + 2 * (offs[ci] + nv));
-      if (!factor_rank1(tab, S, params->oversampling, 1e-6, fx[ci], fy[ci])) {
+      if (factor_low_rank(tab, S, params->oversampling, kSepTol, kMaxRank, fx[ci], fy[ci]) == 0) {
 #pragma omp atomic write
         failed = 1;
       }
@@ -439,7 +456,7 @@ awg_status cf_set_info(awg_cf_set h, int32_t* n_cf, int64_t* n_values, int32_t* 
   CfSetImpl* cf = (CfSetImpl*)h;
   if (n_cf) *n_cf = cf->n_cf;
   if (n_values) *n_values = cf->n_values;
-  if (separable) *separable = cf->separable;
+  if (separable) *separable = cf->separable ? cf->rank : 0;
   return AWG_OK;
 }
 
@@ -456,22 +473,27 @@ awg_status cf_set_copy_table(awg_cf_set h, int32_t ci, float* out) {
   if (ci < 0 || ci >= cf->n_cf) return set_error(AWG_ERR_INVALID_ARG, "cf index out of range");
   const int64_t nv = (int64_t)(cf->p.oversampling + 1) * (cf->p.oversampling + 1) * cf->supports[ci] * cf->supports[ci];
   if (cf->separable) {
+    // the sum of the CF's terms, each product in FP32 as the kernels form it
     const int OS = cf->p.oversampling, S = cf->supports[ci];
     const int64_t q = (int64_t)(OS + 1) * S;
+    std::fill(out, out + 2 * nv, 0.f);
     std::vector<float> f((size_t)4 * q);
-    AWG_CUDA_TRY(cudaMemcpy(f.data(), (float*)cf->d_sep + 2 * cf->sep_offsets[ci], 16 * q, cudaMemcpyDeviceToHost));
-    const float* fx = f.data();
-    const float* fy = f.data() + 2 * q;
-    for (int oy = 0; oy <= OS; ++oy)
-      for (int ox = 0; ox <= OS; ++ox)
-        for (int ty = 0; ty < S; ++ty)
-          for (int tx = 0; tx < S; ++tx) {
-            const float gr = fy[2 * (oy * S + ty)], gi = fy[2 * (oy * S + ty) + 1];
-            const float fr = fx[2 * (ox * S + tx)], fi = fx[2 * (ox * S + tx) + 1];
-            const size_t o = ((((size_t)oy * (OS + 1) + ox) * S + ty) * S + tx) * 2;
-            out[o] = gr * fr - gi * fi;
-            out[o + 1] = gr * fi + gi * fr;
-          }
+    for (int k = 0; k < cf->rank; ++k) {
+      AWG_CUDA_TRY(cudaMemcpy(f.data(), (float*)cf->d_sep + 2 * cf->sep_offsets[(size_t)ci * cf->rank + k], 16 * q,
+                              cudaMemcpyDeviceToHost));
+      const float* fx = f.data();
+      const float* fy = f.data() + 2 * q;
+      for (int oy = 0; oy <= OS; ++oy)
+        for (int ox = 0; ox <= OS; ++ox)
+          for (int ty = 0; ty < S; ++ty)
+            for (int tx = 0; tx < S; ++tx) {
+              const float gr = fy[2 * (oy * S + ty)], gi = fy[2 * (oy * S + ty) + 1];
+              const float fr = fx[2 * (ox * S + tx)], fi = fx[2 * (ox * S + tx) + 1];
+              const size_t o = ((((size_t)oy * (OS + 1) + ox) * S + ty) * S + tx) * 2;
+              out[o] += gr * fr - gi * fi;
+              out[o + 1] += gr * fi + gi * fr;
+            }
+    }
     return AWG_OK;
   }
   if (cf->p.cf_dtype == AWG_CF_BF16) {
@@ -488,6 +510,7 @@ static awg_status plan_free(PlanImpl* pl) {
   if (!pl) return AWG_OK;
   cudaFree(pl->d_rec);
   cudaFree(pl->d_rec_tmp);
+  cudaFree(pl->d_part);
   cudaFree(pl->d_key);
   cudaFree(pl->d_drop);
   cudaFree(pl->d_bcount);
@@ -526,6 +549,12 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
   pl->R = n_rows;
   pl->C = n_chan;
   pl->n = n_rows * n_chan;
+  pl->rank = cf->separable ? cf->rank : 1;
+  pl->n_rec = pl->n * pl->rank;
+  if (pl->n_rec > ((int64_t)1 << 31) - 1) {
+    delete pl;
+    return set_error(AWG_ERR_UNSUPPORTED, "more than 2^31 - 1 samples x CF terms per plan");
+  }
   cudaGetDevice(&pl->device);
   if (phase_shift) {
     const double dl = phase_shift[0], dm = phase_shift[1];
@@ -536,15 +565,17 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
     pl->dn = std::sqrt(1.0 - dl * dl - dm * dm) - 1.0;
   }
   pl->n_buckets = cf->slots.base[cf->slots.n];
-  pl->max_items = (int64_t)pl->n_buckets + pl->n / kItemChunk + 1;
+  pl->max_items = (int64_t)pl->n_buckets + pl->n_rec / kItemChunk + 1;
   const size_t n = (size_t)std::max<int64_t>(pl->n, 1);
+  const size_t nr = (size_t)std::max<int64_t>(pl->n_rec, 1);
   const size_t nb = (size_t)pl->n_buckets + 1;
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
-  A((void**)&pl->d_rec, n * sizeof(SampleRec));
-  A((void**)&pl->d_rec_tmp, n * sizeof(SampleRec));
-  A((void**)&pl->d_key, n * sizeof(int32_t));
+  A((void**)&pl->d_rec, nr * sizeof(SampleRec));
+  A((void**)&pl->d_rec_tmp, nr * sizeof(SampleRec));
+  A((void**)&pl->d_key, nr * sizeof(int32_t));
   A((void**)&pl->d_drop, n * sizeof(int32_t));
+  if (pl->rank > 1) A((void**)&pl->d_part, nr * 4 * sizeof(float2));
   A((void**)&pl->d_bcount, nb * sizeof(int32_t));
   A((void**)&pl->d_boff, nb * sizeof(int32_t));
   A((void**)&pl->d_icount, nb * sizeof(int32_t));

@@ -159,13 +159,10 @@ void taper_image(const awg_cf_params& p, std::vector<double>& out) {
   for (int j = 0; j < N; ++j) out[j] = taper_at(ps, 2.0 * (double)(j - N / 2) / N, norm);
 }
 
-void build_cf_table(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa,
-                    int sb, int ks, std::vector<double>& out) {
-  const int S = support_of_plane(p, ks);
-  const int M = screen_size(S);
-  const int OS = p.oversampling;
+// Image-plane screen s[j][i] = T(x_i) T(y_j) A W at x_i = (i - M/2) N / M pixels (row j: y).
+static void cf_screen(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa, int sb,
+                      int ks, int M, std::vector<cd>& scr) {
   const int N = p.grid_n;
-  // Image-plane screen s[j][i]: T(x_i) T(y_j) A W at x_i = (i - M/2) N / M pixels.
   std::vector<double> t1(M, 1.0);
   if (p.use_ps) {
     Pswf0 ps(kPi * p.ps_support / 2.0);
@@ -173,7 +170,7 @@ void build_cf_table(const awg_cf_params& p, const double* pa_centers, const doub
     for (int i = 0; i < M; ++i) t1[i] = taper_at(ps, 2.0 * (double)(i - M / 2) / M, norm);
   }
   const double w = p.use_w ? (double)(ks - (p.n_wplanes - 1)) * p.w_max_lambda / (double)(p.n_wplanes - 1) : 0.0;
-  std::vector<cd> scr((size_t)M * M);
+  scr.assign((size_t)M * M, cd(0.0));
   const double chi = p.use_a ? pa_centers[pa] : 0.0;
   const double cchi = std::cos(chi), schi = std::sin(chi);
   const double nu = p.use_a ? sb_freqs[sb] : 0.0;
@@ -201,94 +198,284 @@ void build_cf_table(const awg_cf_params& p, const double* pa_centers, const doub
       scr[(size_t)j * M + i] = v;
     }
   }
+}
+
+// Twiddles of the axis transform: tw[o][i] = exp(-2 pi i (S/2 - o/OS) (i - M/2) / M).
+static void axis_twiddles(int M, int S, int OS, std::vector<cd>& tw) {
+  tw.resize((size_t)(OS + 1) * M);
+  for (int o = 0; o <= OS; ++o) {
+    const double shift = 0.5 * S - (double)o / OS;
+    for (int i = 0; i < M; ++i) tw[(size_t)o * M + i] = expi_turns(-shift * (double)(i - M / 2) / M);
+  }
+}
+
+// One axis of the CF transform: out[o][t] = (1/M) (-1)^t sum_i v_i tw[o][i] exp(2 pi i t i / M), the
+// taps t < S of the screen row v at oversampling offset o (shift S/2 - o/OS pixels).
+static void axis_transform(const cd* v, int M, int S, int OS, const std::vector<cd>& tw, cd* out) {
+  std::vector<cd> b(M);
+  for (int o = 0; o <= OS; ++o) {
+    for (int i = 0; i < M; ++i) b[i] = v[i] * tw[(size_t)o * M + i];
+    fft_inverse(b);
+    for (int t = 0; t < S; ++t) out[(size_t)o * S + t] = b[t] * ((t & 1) ? -1.0 : 1.0) / (double)M;
+  }
+}
+
+void build_cf_table(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa,
+                    int sb, int ks, std::vector<double>& out) {
+  const int S = support_of_plane(p, ks);
+  const int M = screen_size(S);
+  const int OS = p.oversampling;
+  std::vector<cd> scr, tw;
+  cf_screen(p, pa_centers, sb_freqs, pa, sb, ks, M, scr);
+  axis_twiddles(M, S, OS, tw);
   // Pass over rows (u): X[ox][j][tx].
-  std::vector<cd> X((size_t)(OS + 1) * M * S), b(M), tw(M);
-  for (int ox = 0; ox <= OS; ++ox) {
-    const double shift = 0.5 * S - (double)ox / OS;
-    for (int i = 0; i < M; ++i) tw[i] = expi_turns(-shift * (double)(i - M / 2) / M);
-    for (int j = 0; j < M; ++j) {
-      for (int i = 0; i < M; ++i) b[i] = scr[(size_t)j * M + i] * tw[i];
-      fft_inverse(b);
-      for (int tx = 0; tx < S; ++tx) X[((size_t)ox * M + j) * S + tx] = b[tx] * ((tx & 1) ? -1.0 : 1.0) / (double)M;
-    }
+  const int Q = (OS + 1) * S;
+  std::vector<cd> X((size_t)(OS + 1) * M * S), row(Q), col(M), colt(Q);
+  for (int j = 0; j < M; ++j) {
+    axis_transform(&scr[(size_t)j * M], M, S, OS, tw, row.data());
+    for (int ox = 0; ox <= OS; ++ox)
+      for (int tx = 0; tx < S; ++tx) X[((size_t)ox * M + j) * S + tx] = row[(size_t)ox * S + tx];
   }
   // Pass over columns (v): out[oy][ox][ty][tx].
   out.assign((size_t)2 * (OS + 1) * (OS + 1) * S * S, 0.0);
-  for (int oy = 0; oy <= OS; ++oy) {
-    const double shift = 0.5 * S - (double)oy / OS;
-    for (int j = 0; j < M; ++j) tw[j] = expi_turns(-shift * (double)(j - M / 2) / M);
-    for (int ox = 0; ox <= OS; ++ox) {
-      for (int tx = 0; tx < S; ++tx) {
-        for (int j = 0; j < M; ++j) b[j] = X[((size_t)ox * M + j) * S + tx] * tw[j];
-        fft_inverse(b);
+  for (int ox = 0; ox <= OS; ++ox) {
+    for (int tx = 0; tx < S; ++tx) {
+      for (int j = 0; j < M; ++j) col[j] = X[((size_t)ox * M + j) * S + tx];
+      axis_transform(col.data(), M, S, OS, tw, colt.data());
+      for (int oy = 0; oy <= OS; ++oy)
         for (int ty = 0; ty < S; ++ty) {
-          const cd c = b[ty] * ((ty & 1) ? -1.0 : 1.0) / (double)M;
+          const cd c = colt[(size_t)oy * S + ty];
           const size_t at = ((((size_t)oy * (OS + 1) + ox) * S + ty) * S + tx) * 2;
           out[at] = c.real();
           out[at + 1] = c.imag();
         }
-      }
     }
   }
 }
 
-bool factor_rank1(const std::vector<double>& tab, int S, int OS, double tol, std::vector<double>& fx,
-                  std::vector<double>& fy) {
-  // The table seen as a Q x Q matrix C[(oy, ty)][(ox, tx)], Q = (OS + 1) S.  A separable CF
-  // c(du, dv) = g(dv) f(du) makes C = g f^T; alternating least squares from the strongest column
-  // finds g and f, and the fit is accepted when max |C - g f^T| <= tol max |C|.
-  const int Q = (OS + 1) * S;
-  auto at = [&](int qy, int qx) {
-    const int oy = qy / S, ty = qy - oy * S, ox = qx / S, tx = qx - ox * S;
-    const size_t i = ((((size_t)oy * (OS + 1) + ox) * S + ty) * S + tx) * 2;
-    return cd(tab[i], tab[i + 1]);
-  };
-  double cmax = 0.0;
+// Greedy rank-1 terms of a rows x cols matrix E (row-major), subtracted in place: alternating
+// least squares from the strongest column (power iteration on E^H E) for the leading pair.
+static void leading_term(std::vector<cd>& E, int rows, int cols, std::vector<cd>& g, std::vector<cd>& f) {
+  g.assign(rows, cd(0.0));
+  f.assign(cols, cd(0.0));
+  double emax = 0.0;
   int jbest = 0;
-  for (int qy = 0; qy < Q; ++qy)
-    for (int qx = 0; qx < Q; ++qx) {
-      const double a = std::abs(at(qy, qx));
-      if (a > cmax) { cmax = a; jbest = qx; }
-    }
-  if (cmax == 0.0) return false;
-  std::vector<cd> g(Q), f(Q);
-  for (int qy = 0; qy < Q; ++qy) g[qy] = at(qy, jbest);
-  for (int it = 0; it < 4; ++it) {
+  for (size_t i = 0; i < E.size(); ++i) {
+    const double a = std::abs(E[i]);
+    if (a > emax) { emax = a; jbest = (int)(i % cols); }
+  }
+  if (emax == 0.0) return;
+  for (int r = 0; r < rows; ++r) g[r] = E[(size_t)r * cols + jbest];
+  double prev = 0.0;
+  for (int it = 0; it < 40; ++it) {
     double gg = 0.0;
     for (const cd& v : g) gg += std::norm(v);
-    for (int qx = 0; qx < Q; ++qx) {
-      cd acc = 0.0;
-      for (int qy = 0; qy < Q; ++qy) acc += std::conj(g[qy]) * at(qy, qx);
-      f[qx] = acc / gg;
+    std::fill(f.begin(), f.end(), cd(0.0));
+    for (int r = 0; r < rows; ++r) {
+      const cd cg = std::conj(g[r]);
+      const cd* e = &E[(size_t)r * cols];
+      for (int c = 0; c < cols; ++c) f[c] += cg * e[c];
     }
+    for (cd& v : f) v /= gg;
     double ff = 0.0;
     for (const cd& v : f) ff += std::norm(v);
-    for (int qy = 0; qy < Q; ++qy) {
+    double g2 = 0.0;
+    for (int r = 0; r < rows; ++r) {
       cd acc = 0.0;
-      for (int qx = 0; qx < Q; ++qx) acc += at(qy, qx) * std::conj(f[qx]);
-      g[qy] = acc / ff;
+      const cd* e = &E[(size_t)r * cols];
+      for (int c = 0; c < cols; ++c) acc += e[c] * std::conj(f[c]);
+      g[r] = acc / ff;
+      g2 += std::norm(g[r]);
+    }
+    const double sigma = std::sqrt(g2 * ff);
+    if (it >= 3 && std::fabs(sigma - prev) <= 1e-13 * sigma) break;
+    prev = sigma;
+  }
+  for (int r = 0; r < rows; ++r) {
+    cd* e = &E[(size_t)r * cols];
+    for (int c = 0; c < cols; ++c) e[c] -= g[r] * f[c];
+  }
+}
+
+int build_cf_factors(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa, int sb,
+                     int ks, double tol, int r_max, std::vector<double>& fx, std::vector<double>& fy) {
+  // The CF is the 2-D transform of the screen, separable as C = Fy scr Fx^T with one axis
+  // transform per axis; a term g f^T of the screen therefore gives the CF term (Fy g)(Fx f)^T.
+  // Terms are taken greedily from the screen's residual; after each term the CF residual is
+  // evaluated on the offset slices (oy, ox) in {0, OS/2, OS}^2 (each S x S: the CF's own slices,
+  // computed directly from the screen, minus the terms so far) and the fit stops once it is
+  // within tol of the CF's peak there.
+  const int S = support_of_plane(p, ks);
+  const int M = screen_size(S);
+  const int OS = p.oversampling;
+  const int Q = (OS + 1) * S;
+  std::vector<cd> E, tw;
+  cf_screen(p, pa_centers, sb_freqs, pa, sb, ks, M, E);
+  axis_twiddles(M, S, OS, tw);
+  // axis transform as explicit rows for the checked offsets: Fo[t][i]
+  const int chk[3] = {0, OS / 2, OS};
+  std::vector<cd> Fo((size_t)3 * S * M);
+  {
+    std::vector<cd> e(M, cd(0.0)), o((size_t)Q);
+    for (int i = 0; i < M; ++i) {
+      e[i] = 1.0;
+      axis_transform(e.data(), M, S, OS, tw, o.data());
+      for (int c = 0; c < 3; ++c)
+        for (int t = 0; t < S; ++t) Fo[((size_t)c * S + t) * M + i] = o[(size_t)chk[c] * S + t];
+      e[i] = 0.0;
     }
   }
-  // balance the two factors' magnitudes
-  double gm = 0.0, fm = 0.0;
-  for (const cd& v : g) gm = std::fmax(gm, std::abs(v));
-  for (const cd& v : f) fm = std::fmax(fm, std::abs(v));
-  const double sc = std::sqrt(fm / gm);
-  for (cd& v : g) v *= sc;
-  for (cd& v : f) v /= sc;
-  double res = 0.0;
-  for (int qy = 0; qy < Q; ++qy)
-    for (int qx = 0; qx < Q; ++qx) res = std::fmax(res, std::abs(at(qy, qx) - g[qy] * f[qx]));
-  if (res > tol * cmax) return false;
-  fx.resize(2 * (size_t)Q);
-  fy.resize(2 * (size_t)Q);
-  for (int q = 0; q < Q; ++q) {
-    fx[2 * q] = f[q].real();
-    fx[2 * q + 1] = f[q].imag();
-    fy[2 * q] = g[q].real();
-    fy[2 * q + 1] = g[q].imag();
+  // slices of a screen-space matrix: out[cy][cx][ty][tx] = sum_j Fo[cy][ty][j] sum_i Z[j][i] Fo[cx][tx][i]
+  auto slices = [&](const std::vector<cd>& Z, std::vector<cd>& out) {
+    std::vector<cd> A((size_t)3 * M * S, cd(0.0));   // A[cx][j][tx]
+    for (int cx = 0; cx < 3; ++cx)
+      for (int j = 0; j < M; ++j)
+        for (int tx = 0; tx < S; ++tx) {
+          cd acc = 0.0;
+          const cd* z = &Z[(size_t)j * M];
+          const cd* fo = &Fo[((size_t)cx * S + tx) * M];
+          for (int i = 0; i < M; ++i) acc += z[i] * fo[i];
+          A[((size_t)cx * M + j) * S + tx] = acc;
+        }
+    out.assign((size_t)9 * S * S, cd(0.0));
+    for (int cy = 0; cy < 3; ++cy)
+      for (int cx = 0; cx < 3; ++cx)
+        for (int ty = 0; ty < S; ++ty) {
+          const cd* fo = &Fo[((size_t)cy * S + ty) * M];
+          for (int tx = 0; tx < S; ++tx) {
+            cd acc = 0.0;
+            for (int j = 0; j < M; ++j) acc += fo[j] * A[((size_t)cx * M + j) * S + tx];
+            out[(((size_t)cy * 3 + cx) * S + ty) * S + tx] = acc;
+          }
+        }
+  };
+  std::vector<cd> sl;
+  slices(E, sl);
+  double peak = 0.0;
+  for (const cd& v : sl) peak = std::fmax(peak, std::abs(v));
+  fx.clear();
+  fy.clear();
+  std::vector<cd> g, f, tg(Q), tf(Q);
+  for (int r = 0; r < r_max; ++r) {
+    leading_term(E, M, M, g, f);
+    axis_transform(g.data(), M, S, OS, tw, tg.data());
+    axis_transform(f.data(), M, S, OS, tw, tf.data());
+    for (int q = 0; q < Q; ++q) {
+      fx.push_back(tf[q].real());
+      fx.push_back(tf[q].imag());
+    }
+    for (int q = 0; q < Q; ++q) {
+      fy.push_back(tg[q].real());
+      fy.push_back(tg[q].imag());
+    }
+    // the term's own slices are outer products of its transformed factors
+    double res = 0.0;
+    for (int cy = 0; cy < 3; ++cy)
+      for (int cx = 0; cx < 3; ++cx)
+        for (int ty = 0; ty < S; ++ty)
+          for (int tx = 0; tx < S; ++tx) {
+            cd& v = sl[(((size_t)cy * 3 + cx) * S + ty) * S + tx];
+            v -= tg[(size_t)chk[cy] * S + ty] * tf[(size_t)chk[cx] * S + tx];
+            res = std::fmax(res, std::abs(v));
+          }
+    if (res <= tol * peak) return r + 1;
   }
-  return true;
+  fx.clear();
+  fy.clear();
+  return 0;
+}
+
+int factor_low_rank(const std::vector<double>& tab, int S, int OS, double tol, int r_max, std::vector<double>& fx,
+                    std::vector<double>& fy) {
+  // The table seen as a Q x Q matrix C[(oy, ty)][(ox, tx)], Q = (OS + 1) S.  A separable CF
+  // c(du, dv) = g(dv) f(du) makes C = g f^T; a sum of r such terms makes C = sum_k g_k f_k^T.
+  // Terms are taken greedily from the residual E (starting at E = C): alternating least squares
+  // from E's strongest column (power iteration on E^H E) gives the leading pair, which is
+  // subtracted.  The fit stops at the first r with max |E| <= tol max |C|.
+  const int Q = (OS + 1) * S;
+  std::vector<cd> E((size_t)Q * Q);
+  double cmax = 0.0;
+  for (int oy = 0; oy <= OS; ++oy)
+    for (int ox = 0; ox <= OS; ++ox)
+      for (int ty = 0; ty < S; ++ty)
+        for (int tx = 0; tx < S; ++tx) {
+          const size_t i = ((((size_t)oy * (OS + 1) + ox) * S + ty) * S + tx) * 2;
+          const cd v(tab[i], tab[i + 1]);
+          E[(size_t)(oy * S + ty) * Q + ox * S + tx] = v;
+          cmax = std::fmax(cmax, std::abs(v));
+        }
+  fx.clear();
+  fy.clear();
+  if (cmax == 0.0) {   // the zero table: one zero term
+    fx.assign(2 * (size_t)Q, 0.0);
+    fy.assign(2 * (size_t)Q, 0.0);
+    return 1;
+  }
+  std::vector<cd> g(Q), f(Q);
+  for (int r = 0; r < r_max; ++r) {
+    double emax = 0.0;
+    int jbest = 0;
+    for (size_t i = 0; i < E.size(); ++i) {
+      const double a = std::abs(E[i]);
+      if (a > emax) { emax = a; jbest = (int)(i % Q); }
+    }
+    for (int qy = 0; qy < Q; ++qy) g[qy] = E[(size_t)qy * Q + jbest];
+    double prev = 0.0;
+    for (int it = 0; it < 40; ++it) {
+      double gg = 0.0;
+      for (const cd& v : g) gg += std::norm(v);
+      std::fill(f.begin(), f.end(), cd(0.0));
+      for (int qy = 0; qy < Q; ++qy) {
+        const cd cg = std::conj(g[qy]);
+        const cd* row = &E[(size_t)qy * Q];
+        for (int qx = 0; qx < Q; ++qx) f[qx] += cg * row[qx];
+      }
+      for (cd& v : f) v /= gg;
+      double ff = 0.0;
+      for (const cd& v : f) ff += std::norm(v);
+      for (int qy = 0; qy < Q; ++qy) {
+        cd acc = 0.0;
+        const cd* row = &E[(size_t)qy * Q];
+        for (int qx = 0; qx < Q; ++qx) acc += row[qx] * std::conj(f[qx]);
+        g[qy] = acc / ff;
+      }
+      // sigma of the current pair; stop once it no longer moves
+      double g2 = 0.0;
+      for (const cd& v : g) g2 += std::norm(v);
+      const double sigma = std::sqrt(g2 * ff);
+      if (it >= 3 && std::fabs(sigma - prev) <= 1e-13 * sigma) break;
+      prev = sigma;
+    }
+    // balance the two factors' magnitudes
+    double gm = 0.0, fm = 0.0;
+    for (const cd& v : g) gm = std::fmax(gm, std::abs(v));
+    for (const cd& v : f) fm = std::fmax(fm, std::abs(v));
+    if (gm > 0.0 && fm > 0.0) {
+      const double sc = std::sqrt(fm / gm);
+      for (cd& v : g) v *= sc;
+      for (cd& v : f) v /= sc;
+    }
+    double res = 0.0;
+    for (int qy = 0; qy < Q; ++qy) {
+      cd* row = &E[(size_t)qy * Q];
+      for (int qx = 0; qx < Q; ++qx) {
+        row[qx] -= g[qy] * f[qx];
+        res = std::fmax(res, std::abs(row[qx]));
+      }
+    }
+    for (int q = 0; q < Q; ++q) {
+      fx.push_back(f[q].real());
+      fx.push_back(f[q].imag());
+    }
+    for (int q = 0; q < Q; ++q) {
+      fy.push_back(g[q].real());
+      fy.push_back(g[q].imag());
+    }
+    if (res <= tol * cmax) return r + 1;
+  }
+  fx.clear();
+  fy.clear();
+  return 0;
 }
 
 }  // namespace awg

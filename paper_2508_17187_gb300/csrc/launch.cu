@@ -111,6 +111,24 @@ __global__ void k_zero_dropped(const int32_t* __restrict__ drop, const unsigned 
   }
 }
 
+// vis_out[s] = sum over the rank terms of sample s (the CF's outer-product terms).
+__global__ void k_sum_terms(const float2* __restrict__ part, float2* __restrict__ vis_out, int64_t n, int rank,
+                            int P) {
+  const int64_t total = n * P;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t s = i / P;
+    const int p = (int)(i - s * P);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < rank; ++k) {
+      const float2 v = part[(s * rank + k) * P + p];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    vis_out[i] = acc;
+  }
+}
+
 awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float* weight, int P, void* grid,
                        void* grid_lo, double* sumwt, int flags, cudaStream_t st) {
   if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
@@ -140,6 +158,7 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   a.sumwt = sumwt;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
+  a.rank = pl->rank;
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
@@ -180,9 +199,11 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   a.uvw = pl->d_uvw;
   a.freq = pl->d_freq;
   a.grid = (const float*)grid;
-  a.vis_out = (float*)vis_out;
+  // with several terms per CF every record writes its own row of the per-term buffer, summed below
+  a.vis_out = pl->rank > 1 ? (float*)pl->d_part : (float*)vis_out;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
+  a.rank = pl->rank;
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
@@ -198,6 +219,11 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
       awg_status s = bf16 ? degrid_class<true>(c, P, a, sms, st) : degrid_class<false>(c, P, a, sms, st);
       if (s != AWG_OK) return s;
     }
+  }
+  if (pl->rank > 1) {   // dropped samples' rows are stale here and are zeroed next
+    k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, P);
+    AWG_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
   }
   k_zero_dropped<<<sms * 4, 256, 0, st>>>(pl->d_drop, pl->d_counters, (float*)vis_out, P);
   AWG_CUDA_TRY(cudaGetLastError());

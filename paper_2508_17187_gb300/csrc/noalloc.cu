@@ -18,7 +18,7 @@
 namespace awg {
 namespace {
 
-constexpr int64_t kNoAllocMaxSamples = 65536;   // rows x channels per call
+constexpr int64_t kNoAllocMaxSamples = 65536;   // records (rows x channels x CF terms) per call
 constexpr int kNoAllocMaxBuckets = 65536;       // (support, tile) buckets of the CF set and grid
 constexpr int kMaxDevices = 64;
 
@@ -70,10 +70,12 @@ extern "C" awg_status grid_visibilities_noalloc(awg_cf_set hc, const double* uvw
   if (n_rows < 0 || n_chan < 1) return set_error(AWG_ERR_INVALID_ARG, "n_rows must be >= 0 and n_chan >= 1");
   if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
   const int64_t n = n_rows * (int64_t)n_chan;
-  if (n > kNoAllocMaxSamples)
+  const int rank = cf->separable ? cf->rank : 1;   // records per sample
+  if (n * rank > kNoAllocMaxSamples)
     return set_error(AWG_ERR_INVALID_ARG, "grid_visibilities_noalloc takes at most " +
-                                              std::to_string(kNoAllocMaxSamples) + " samples (rows x channels) per call, got " +
-                                              std::to_string(n) + "; use plan_create + grid_visibilities");
+                                              std::to_string(kNoAllocMaxSamples) +
+                                              " samples (rows x channels, times the CF terms) per call, got " +
+                                              std::to_string(n * rank) + "; use plan_create + grid_visibilities");
   const int nb = cf->slots.base[cf->slots.n];
   if (nb > kNoAllocMaxBuckets)
     return set_error(AWG_ERR_INVALID_ARG, "grid_visibilities_noalloc supports at most " +
@@ -96,6 +98,8 @@ extern "C" awg_status grid_visibilities_noalloc(awg_cf_set hc, const double* uvw
   pl.R = n_rows;
   pl.C = n_chan;
   pl.n = n;
+  pl.rank = rank;
+  pl.n_rec = n * rank;
   pl.device = cf->device;
   pl.n_buckets = nb;
   pl.max_items = kNoAllocMaxItems;

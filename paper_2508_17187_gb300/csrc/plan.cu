@@ -20,6 +20,7 @@ namespace {
 
 struct IndexParams {
   int64_t n;
+  int rank;   // records per sample (terms per CF of a separable set)
   int C, N, OS, use_w, n_w, n_pa, n_sb, n_signed;
   double inv_dw, scale, half;
 };
@@ -86,7 +87,7 @@ __global__ void k_index(IndexParams ip, const double* __restrict__ uvw, const do
       const int oy = (int)floor(__dadd_rn(__dmul_rn(fy, OSd), 0.5));
       const int p0x = (int)px, p0y = (int)py;
       rc.src = (int32_t)s;
-      rc.cf = cf;
+      rc.cf = cf * ip.rank;   // term 0; term k is record s * rank + k with cf * rank + k
       rc.p0x = (uint16_t)p0x;
       rc.p0y = (uint16_t)p0y;
       rc.ox = (uint8_t)ox;
@@ -96,13 +97,16 @@ __global__ void k_index(IndexParams ip, const double* __restrict__ uvw, const do
       const int slot = st.slot_of_S[S];
       const int T = st.tile[slot];
       key = st.base[slot] + (p0y / T) * st.nt[slot] + p0x / T;
-      rec_tmp[s] = rc;
+      for (int k = 0; k < ip.rank; ++k) {
+        rec_tmp[s * ip.rank + k] = rc;
+        rc.cf += 1;
+      }
       kept += 1;
       taps += (unsigned long long)S * S;
     }
-    key_out[s] = key;
+    for (int k = 0; k < ip.rank; ++k) key_out[s * ip.rank + k] = key;
     if (key >= 0) {
-      warp_aggregated_add(bcount, key, 1);
+      warp_aggregated_add(bcount, key, ip.rank);
     } else {
       const unsigned active = __activemask();
       const unsigned peers = __match_any_sync(active, key);   // all dropping lanes
@@ -333,6 +337,7 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_counters, 0, 4 * sizeof(unsigned long long), st));
   IndexParams ip;
   ip.n = pl->n;
+  ip.rank = pl->rank;
   ip.C = pl->C;
   ip.N = cf->p.grid_n;
   ip.OS = cf->p.oversampling;
@@ -378,8 +383,8 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
     count_launches(1);
   if (pl->n > 0 && nb > 0) {
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_bcount, pl->d_boff, sizeof(int32_t) * nb, cudaMemcpyDeviceToDevice, st));
-    const int blocks = (int)std::min<int64_t>((pl->n + 255) / 256, (int64_t)sms * 8);
-    k_scatter<<<blocks, 256, 0, st>>>(pl->n, pl->d_key, pl->d_rec_tmp, pl->d_bcount, pl->d_rec);
+    const int blocks = (int)std::min<int64_t>((pl->n_rec + 255) / 256, (int64_t)sms * 8);
+    k_scatter<<<blocks, 256, 0, st>>>(pl->n_rec, pl->d_key, pl->d_rec_tmp, pl->d_bcount, pl->d_rec);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     k_sort_items<<<sms * 8, kItemChunk, 0, st>>>(pl->d_ioff + nb, pl->d_items, pl->d_rec);

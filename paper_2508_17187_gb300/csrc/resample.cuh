@@ -45,6 +45,7 @@ struct GridArgs {
   double* sumwt;         // [P]
   const float* sep;      // separable CF factors (c64), or NULL
   const int64_t* sep_off;
+  int rank;              // records per sample; only term 0 (cf % rank == 0) adds its weight
 };
 
 struct DegridArgs {
@@ -59,9 +60,10 @@ struct DegridArgs {
   const double* uvw;
   const double* freq;
   const float* grid;     // c64 [N][N][P]
-  float* vis_out;        // c64 [n][P]
+  float* vis_out;        // c64 [n][P]; with rank > 1 the per-term values [n][rank][P]
   const float* sep;      // separable CF factors (c64), or NULL
   const int64_t* sep_off;
+  int rank;              // records per sample (term k of sample s writes vis_out row s * rank + k)
 };
 
 template <bool BF16>

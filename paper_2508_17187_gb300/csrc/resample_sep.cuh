@@ -2,7 +2,9 @@
 //
 // PS and W-projection CFs are outer products to FP32 precision (the W screen's non-separable
 // part is below 1e-7 of the peak for fields of a fraction of a degree), so a sample needs only
-// its two factor rows (2 S values) instead of an S x S slice.  The work decomposition is that of
+// its two factor rows (2 S values) instead of an S x S slice.  A-term CFs are sums of a few such
+// terms; the plan then holds one record per (sample, term), each a rank-1 sample of its own, so
+// these kernels see only outer products.  The work decomposition is that of
 // resample.cuh; the tap ownership is arranged so the factorisation also saves arithmetic:
 //
 // Thread t of NT owns column residue rx = t mod S and rows ry = t div S + k G, G = NT div S
@@ -16,6 +18,8 @@
 // Degridding: per sample the thread sums fy[ty] grid[Y][X][p] over its rows and multiplies by
 // fx[tx] once; a warp reduce-scatter and a shared-memory pass finish the sum as in resample.cuh.
 #pragma once
+
+#include <type_traits>
 
 #include "resample.cuh"
 
@@ -123,7 +127,10 @@ __device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, in
     sl.fxo()[j] = base + (long long)rc.ox * S;
     sl.fyo()[j] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
     sl.pack()[j] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
-    sl.src()[j] = rc.src;
+    if constexpr (std::is_same<Args, DegridArgs>::value)   // the output row of this record
+      sl.src()[j] = a.rank > 1 ? rc.src * a.rank + rc.cf % a.rank : rc.src;
+    else   // the visibility / weight row
+      sl.src()[j] = rc.src;
     sl.ph()[j] = a.has_phase ? sample_phasor(a.uvw, a.freq, a.C, rc.src, a.dl, a.dm, a.dn) : make_float2(1.f, 0.f);
   }
 }
@@ -203,11 +210,11 @@ struct RowState {
 
 // alpha[j][rx][p] = conj(fx[j][(rx - mx_j) mod S]) * w_jp V_jp (* phasor): formed once per
 // chunk for every (sample, column residue) instead of by each of the G threads of a column.  The
-// threads below nst also add the chunk's weights to the sum of weights.
+// threads below nst also add the chunk's weights to the sum of weights (term 0 of each sample).
 template <int SMAX, int TILE, int P, int ST, int NT>
 __device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P, ST>& sl, float2* alpha, int nst, int S,
-                                           double (&wsum)[P]) {
-  if ((int)threadIdx.x < nst) {
+                                           int rank, double (&wsum)[P]) {
+  if ((int)threadIdx.x < nst && (rank == 1 || sl.rec()[threadIdx.x].cf % rank == 0)) {
 #pragma unroll
     for (int p = 0; p < P; ++p) wsum[p] += (double)sl.w()[threadIdx.x * P + p];
   }
@@ -295,7 +302,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      form_alpha<SMAX, TILE, P, ST, NT>(s0, alpha, nst_of(0), S, wsum);
+      form_alpha<SMAX, TILE, P, ST, NT>(s0, alpha, nst_of(0), S, a.rank, wsum);
       __syncthreads();
     }
 
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       __syncthreads();
       // slot A is free: derive chunk c+2 into it; chunk c+1's payload has landed in B: form w V
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
-      if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT>(B, alpha, nst_of(c + 1), S, wsum);
+      if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT>(B, alpha, nst_of(c + 1), S, a.rank, wsum);
       __syncthreads();
     }
 #pragma unroll
