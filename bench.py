@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--config", choices=["wproj", "awproj"], default="wproj",
                     help="wproj: the W-projection workload (default); awproj: the batched AW-projection workload "
                          "(20 PA bins x 32 w-planes x 16 sub-bands, CFs as sums of outer products)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernel configuration of every support instead of timing both")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="CF storage / accumulation variants against the FP64 oracle (one JSON line each)")
     return ap.parse_args()
@@ -438,6 +440,11 @@ def main():
     pa_bin = torch.as_tensor(wl.pa_bin, device=dev) if wl.use_a else None
     chan_sb = torch.as_tensor(wl.chan_subband, device=dev) if wl.use_a else None
     vis, wt = wl.vis, wl.weight
+    tuned, t_tune = None, None
+    if not args.no_autotune:
+        t_tune = time.perf_counter()
+        tuned, _ = cf.autotune(uvw, freq, pa_bin, chan_sb, n_pol=wl.n_pol)
+        t_tune = time.perf_counter() - t_tune
     plan = awg.plan_create(cf, uvw, freq, pa_bin, chan_sb)
     kept, dropped, sum_taps = plan.stats()
     grid = torch.zeros((N, N, P), dtype=torch.complex64, device=dev)
@@ -509,6 +516,28 @@ def main():
         barrier()
     launches = lib.awg_kernel_launches() - launches0
     ms = t_start.elapsed_time(t_end) / args.steps
+    # the same step captured once as a CUDA graph and replayed (single rank: no collective inside)
+    graph_ms = None
+    if world == 1:
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        del graph
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -597,11 +626,14 @@ def main():
         "data": "synthetic VLA A-array-like uvw, 200 point sources + 1 mJy noise, natural weights",
         "config": {"workload": WORKLOADS[CONFIG], "cf_terms": max(cf.rank, 1), "cf_storage":
                    "separable factors" if cf.separable else "full tables", "cf_build_s": t_cf,
+                   "kernel_config_per_support": tuned, "autotune_s": t_tune,
                    "visibilities_per_step": vis_per_step, "kept_samples": kept, "dropped_samples": dropped,
                    "mean_taps": sum_taps / max(kept, 1), "l2": "inputs larger than L2 (2.7 GB per step)",
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "cf_gmac_per_s": 2 * P * sum_taps * world / (ms / 1e3) / 1e9,
         "ops_ms": {k: statistics.mean(v) for k, v in op_ms.items()},
+        "cuda_graph": None if graph_ms is None else {"ms_per_step": graph_ms,
+                                                     "value": vis_per_step / (graph_ms / 1e3)},
         "ops": ops,
         "roofline": {"bound": "alu", "kernel": f"{dom}_visibilities (all supports)", "achieved": achieved,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,

@@ -128,6 +128,31 @@ awg_status cf_set_destroy(awg_cf_set cf);
  * outer-product terms per CF, or 0 for full tables. */
 awg_status cf_set_info(awg_cf_set cf, int32_t* n_cf, int64_t* n_values, int32_t* separable);
 
+/*
+ * Per-support autotuner of the separable kernels (a project addition; the paper fixes no kernel
+ * shapes).  Every support of the W-projection schedule (8, 16, ..., 64) has two compiled kernel
+ * configurations (tile of first-tap positions per work item, threads per CTA, samples staged per
+ * chunk).  For each configuration this builds a plan of the given geometry (uvw_m, freq_hz,
+ * pa_bin, chan_subband: device arrays as for plan_create, typically the data to be imaged or a
+ * slice of it), grids and degrids unit visibilities with n_pol pols once, then times every
+ * support's gridding and degridding launch three times (CUDA events on `stream`), and keeps the
+ * fastest configuration per support in the CF set.  Plans created before the call are invalid
+ * afterwards (their calls return INVALID_ARG); create plans after tuning.  Blocking.  Allocates
+ * scratch of about (R C n_pol) 20 B plus one grid and two plans, and frees it before returning.
+ * choice_out: host int32 [65] or NULL, the chosen configuration (0 or 1) per support, -1 where
+ * none was timed; ms_out: host float [2][65] or NULL, grid + degrid milliseconds of each
+ * configuration per support (0 where not timed).  Full-table CF sets have nothing to tune
+ * (choices -1).  Errors: INVALID_ARG, OOM, CUDA.
+ */
+awg_status cf_set_autotune(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const double* freq_hz, int32_t n_chan,
+                           const int32_t* pa_bin, const int32_t* chan_subband, int32_t n_pol, void* stream,
+                           int32_t* choice_out, float* ms_out);
+
+/* Select configuration `config` (0 or 1) of the separable kernels for one support of the
+ * W-projection schedule by hand (what cf_set_autotune does by timing); plans created before the
+ * call are invalid afterwards.  Errors: INVALID_ARG (no configurations for that support). */
+awg_status cf_set_choose(awg_cf_set cf, int32_t support, int32_t config);
+
 /* Host copy of the support of every CF: supports_out host [n_cf]. */
 awg_status cf_set_get_supports(awg_cf_set cf, int32_t* supports_out);
 

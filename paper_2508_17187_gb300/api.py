@@ -64,6 +64,30 @@ class CFSet:
             raise RuntimeError("CF set already destroyed")
         return self._h
 
+    def autotune(self, uvw_m: torch.Tensor, freq_hz: torch.Tensor, pa_bin: Optional[torch.Tensor] = None,
+                 chan_subband: Optional[torch.Tensor] = None, n_pol: int = 4, stream=None):
+        """Pick the faster compiled kernel configuration per support by timing both on a plan of
+        this geometry (see cf_set_autotune in awgrid.h); plans made earlier become invalid.
+        Returns ({support: choice}, {support: (ms of configuration 0, ms of configuration 1)})."""
+        _need(uvw_m, "uvw_m", torch.float64)
+        _need(freq_hz, "freq_hz", torch.float64)
+        if pa_bin is not None:
+            _need(pa_bin, "pa_bin", torch.int32, (uvw_m.shape[0],))
+        if chan_subband is not None:
+            _need(chan_subband, "chan_subband", torch.int32, (freq_hz.shape[0],))
+        choice = np.zeros(65, dtype=np.int32)
+        ms = np.zeros((2, 65), dtype=np.float32)
+        check(_lib.load().cf_set_autotune(self.handle, _ptr(uvw_m), uvw_m.shape[0], _ptr(freq_hz), freq_hz.shape[0],
+                                          _ptr(pa_bin), _ptr(chan_subband), int(n_pol), _stream_ptr(stream),
+                                          choice.ctypes.data_as(ctypes.c_void_p), ms.ctypes.data_as(ctypes.c_void_p)),
+              "cf_set_autotune")
+        picked = {S: int(choice[S]) for S in range(65) if choice[S] >= 0}
+        return picked, {S: (float(ms[0, S]), float(ms[1, S])) for S in picked}
+
+    def choose(self, support: int, config: int):
+        """Select kernel configuration 0 or 1 for one support by hand (see cf_set_choose)."""
+        check(_lib.load().cf_set_choose(self.handle, int(support), int(config)), "cf_set_choose")
+
     def supports(self) -> np.ndarray:
         out = np.zeros(self.n_cf, dtype=np.int32)
         check(_lib.load().cf_set_get_supports(self.handle, out.ctypes.data_as(ctypes.c_void_p)), "cf_set_get_supports")

@@ -33,23 +33,37 @@ __host__ __device__ constexpr int class_of_support(int S) {
 // row groups G of the gridding and degridding kernels (each thread owns S / G rows of one column
 // residue; S * G threads per CTA, a whole number of warps), the tile of first-tap positions per
 // work item, which the plan uses for these supports when the CF set is separable, and the
-// samples staged per chunk.  Small tiles and shallow stages let two CTAs share an SM.  The
-// supports listed here and AWG_FOR_EXACT_AND_POLS must agree.
+// samples staged per chunk.  Small tiles and shallow stages let two CTAs share an SM.  Every
+// support has kNumCand compiled candidates; candidate 0 is the default and cf_set_autotune picks
+// per support by timing.  The supports listed here and AWG_FOR_EXACT_AND_POLS must agree.
 struct ExactCfg {
   int S, g_grid, g_degrid, tile, stage;
 };
-constexpr ExactCfg kExact[] = {
-    {8, 8, 8, 32, 16},
-    {16, 8, 8, 16, 8},
-    {24, 8, 8, 16, 8},
-    {32, 8, 8, 16, 8},
-    {40, 8, 8, 8, 8},
-    {48, 16, 8, 16, 16},
-    {56, 8, 8, 16, 8},
-    {64, 8, 8, 8, 8},
+constexpr int kNumCand = 2;
+constexpr ExactCfg kExactCand[kNumCand][8] = {
+    {
+        {8, 8, 8, 32, 16},
+        {16, 8, 8, 16, 8},
+        {24, 8, 8, 16, 8},
+        {32, 8, 8, 16, 8},
+        {40, 8, 8, 8, 8},
+        {48, 16, 8, 16, 16},
+        {56, 8, 8, 16, 8},
+        {64, 8, 8, 8, 8},
+    },
+    {
+        {8, 8, 8, 16, 8},
+        {16, 16, 16, 32, 16},
+        {24, 8, 8, 8, 8},
+        {32, 8, 8, 8, 8},
+        {40, 8, 8, 16, 8},
+        {48, 8, 8, 8, 8},
+        {56, 8, 8, 8, 8},
+        {64, 8, 8, 8, 4},
+    },
 };
-constexpr ExactCfg exact_cfg(int S) {
-  for (const ExactCfg& e : kExact)
+constexpr ExactCfg exact_cfg(int S, int cand = 0) {
+  for (const ExactCfg& e : kExactCand[cand])
     if (e.S == S) return e;
   return ExactCfg{S, 0, 0, 0, 0};
 }
@@ -98,6 +112,8 @@ struct CfSetImpl {
   SlotTable slots{};
   // Separable storage: CF = fy[oy][ty] * fx[ox][tx]; per CF, fx [OS+1][S] then fy [OS+1][S] c64.
   int separable = 0;
+  int8_t cand[kMaxSupport + 1] = {};   // exact-kernel candidate per support (cf_set_autotune)
+  int slots_version = 0;               // bumped whenever the slot table (tiles) changes
   int rank = 1;                      // outer-product terms per CF when separable
   std::vector<int64_t> sep_offsets;  // [n_cf * rank]: element offset of term k of CF c at c * rank + k
   void* d_sep = nullptr;
@@ -109,6 +125,7 @@ struct PlanImpl {
   int64_t R = 0;
   int C = 0;
   int64_t n = 0;
+  int slots_version = 0;   // the CF set's slot table this plan was binned with
   int rank = 1;        // records per sample: the CF set's terms per CF
   int64_t n_rec = 0;   // n * rank
   float2* d_part = nullptr;   // rank > 1: per-term degridded values [n][rank][4 pols]
@@ -178,6 +195,13 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
                        void* grid, void* grid_lo, double* sumwt, int flags, cudaStream_t st);
 awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vis_out, int P,
                          cudaStream_t st);
+// Times every candidate of the exact-support kernels on a plan of the given geometry (unit data)
+// and keeps the fastest per support in cf->cand; choice[S] = the pick or -1, ms_out (optional)
+// [kNumCand][kMaxSupport + 1] the grid + degrid milliseconds of each.
+awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, const double* freq, int n_chan,
+                             const int32_t* pa_bin, const int32_t* chan_sb, int P, cudaStream_t st, int32_t* choice,
+                             float* ms_out);
+void fill_slots(CfSetImpl* cf);
 awg_status launch_normalize(CfSetImpl* cf, void* image, int P, const double* sumwt, int direction,
                             cudaStream_t st);
 

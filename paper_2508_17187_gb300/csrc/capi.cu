@@ -78,7 +78,7 @@ static awg_status check_params(const awg_cf_params* p, bool from_table) {
   return AWG_OK;
 }
 
-static void fill_slots(CfSetImpl* cf) {
+void fill_slots(CfSetImpl* cf) {
   bool present[kMaxSupport + 1] = {false};
   for (int s : cf->supports) present[s] = true;
   SlotTable& st = cf->slots;
@@ -90,7 +90,7 @@ static void fill_slots(CfSetImpl* cf) {
     if (!present[s]) continue;
     const int i = st.n++;
     st.S[i] = s;
-    st.tile[i] = cf->separable && has_exact(s) ? exact_cfg(s).tile : kClasses[class_of_support(s)].tile;
+    st.tile[i] = cf->separable && has_exact(s) ? exact_cfg(s, cf->cand[s]).tile : kClasses[class_of_support(s)].tile;
     const int span = N - s + 1;    // possible first-tap positions per axis
     st.nt[i] = span > 0 ? (span + st.tile[i] - 1) / st.tile[i] : 0;
     st.base[i] = base;
@@ -98,6 +98,7 @@ static void fill_slots(CfSetImpl* cf) {
     base += st.nt[i] * st.nt[i];
   }
   st.base[st.n] = base;
+  cf->slots_version += 1;
 }
 
 static void free_cf(CfSetImpl* cf) {
@@ -451,6 +452,36 @@ awg_status cf_set_destroy(awg_cf_set h) {
   return AWG_OK;
 }
 
+awg_status cf_set_autotune(awg_cf_set h, const double* uvw_m, int64_t n_rows, const double* freq_hz, int32_t n_chan,
+                           const int32_t* pa_bin, const int32_t* chan_subband, int32_t n_pol, void* stream,
+                           int32_t* choice_out, float* ms_out) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
+  if (n_rows < 0 || n_chan < 1) return set_error(AWG_ERR_INVALID_ARG, "n_rows must be >= 0 and n_chan >= 1");
+  if (n_rows > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
+  if (cf->p.n_pa_bins > 1 && !pa_bin) return set_error(AWG_ERR_INVALID_ARG, "pa_bin is required with n_pa_bins > 1");
+  if (cf->p.n_subbands > 1 && !chan_subband)
+    return set_error(AWG_ERR_INVALID_ARG, "chan_subband is required with n_subbands > 1");
+  if (cudaSetDevice(cf->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
+  int32_t choice[kMaxSupport + 1];
+  awg_status s = autotune_supports(cf, uvw_m, n_rows, freq_hz, n_chan, pa_bin, chan_subband, n_pol,
+                                   (cudaStream_t)stream, choice, ms_out);
+  if (choice_out) std::memcpy(choice_out, choice, sizeof(choice));
+  return s;
+}
+
+awg_status cf_set_choose(awg_cf_set h, int32_t support, int32_t config) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  if (support < 1 || support > kMaxSupport || !has_exact(support))
+    return set_error(AWG_ERR_INVALID_ARG, "support " + std::to_string(support) + " has no kernel configurations");
+  if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0 or 1");
+  cf->cand[support] = (int8_t)config;
+  fill_slots(cf);
+  return AWG_OK;
+}
+
 awg_status cf_set_info(awg_cf_set h, int32_t* n_cf, int64_t* n_values, int32_t* separable) {
   if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
   CfSetImpl* cf = (CfSetImpl*)h;
@@ -550,6 +581,7 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
   pl->C = n_chan;
   pl->n = n_rows * n_chan;
   pl->rank = cf->separable ? cf->rank : 1;
+  pl->slots_version = cf->slots_version;
   pl->n_rec = pl->n * pl->rank;
   if (pl->n_rec > ((int64_t)1 << 31) - 1) {
     delete pl;
@@ -610,6 +642,8 @@ awg_status plan_update(awg_plan h, const double* uvw_m, const double* freq_hz, c
   if (pl->n > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
   if (pl->cf->p.n_pa_bins > 1 && !pa_bin) return set_error(AWG_ERR_INVALID_ARG, "pa_bin is required");
   if (pl->cf->p.n_subbands > 1 && !chan_subband) return set_error(AWG_ERR_INVALID_ARG, "chan_subband is required");
+  if (pl->slots_version != pl->cf->slots_version)
+    return set_error(AWG_ERR_INVALID_ARG, "the CF set was retuned after this plan was made; create a new plan");
   return plan_build(pl, uvw_m, freq_hz, pa_bin, chan_subband, (cudaStream_t)stream);
 }
 

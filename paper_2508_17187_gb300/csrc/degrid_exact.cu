@@ -1,6 +1,6 @@
-// Instantiations of the exact-support separable degridding kernels (S = 8, 16, ..., 64).
+// Instantiations of the exact-support separable degridding kernels (S = 8, 16, ..., 64), candidate 0.
 #include "resample_sep.cuh"
 
 namespace awg {
-AWG_FOR_EXACT_AND_POLS(AWG_INSTANTIATE_DEGRID_EXACT)
+AWG_FOR_EXACT_AND_POLS(AWG_INSTANTIATE_DEGRID_EXACT, 0)
 }  // namespace awg

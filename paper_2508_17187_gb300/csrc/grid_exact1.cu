@@ -1,0 +1,6 @@
+// Instantiations of the exact-support separable gridding kernels (S = 8, 16, ..., 64), candidate 1.
+#include "resample_sep.cuh"
+
+namespace awg {
+AWG_FOR_EXACT_AND_POLS(AWG_INSTANTIATE_GRID_EXACT, 1)
+}  // namespace awg

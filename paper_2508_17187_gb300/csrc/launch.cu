@@ -2,6 +2,8 @@
 // samples after degridding, and the taper normalisation kernel (grid_normalize).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "resample_sep.cuh"
 
 namespace awg {
@@ -12,8 +14,10 @@ AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_DEGRID, false)
 AWG_FOR_CLASSES_AND_POLS(AWG_DECLARE_DEGRID, true)
 AWG_FOR_SEP_CLASSES_AND_POLS(AWG_DECLARE_GRID_SEP)
 AWG_FOR_SEP_CLASSES_AND_POLS(AWG_DECLARE_DEGRID_SEP)
-AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT)
-AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 0)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 0)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 1)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 1)
 
 namespace {
 
@@ -40,11 +44,12 @@ awg_status grid_class(int c, int P, const GridArgs& a, int sms, cudaStream_t st)
 
 // Separable kernels run once per distinct support (slot): the exact-support kernel when there is
 // one for S, else the class kernel restricted to the slot's items.
-awg_status grid_slot_sep(int S, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
+awg_status grid_slot_sep(int S, int cand, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
   if (has_exact(S)) {   // the plan binned this support by its exact-kernel tile
-#define AWG_CASE(SS, PP) \
-  if (S == SS && P == PP) return run_grid_exact<SS, PP>(a, slot, sms, st);
-    AWG_FOR_EXACT_AND_POLS(AWG_CASE)
+#define AWG_CASE(SS, PP, CC) \
+  if (S == SS && P == PP && cand == CC) return run_grid_exact<SS, PP, CC>(a, slot, sms, st);
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 0)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 1)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
   }
@@ -56,11 +61,12 @@ awg_status grid_slot_sep(int S, int slot, int P, const GridArgs& a, int sms, cud
   return set_error(AWG_ERR_UNSUPPORTED, "no separable gridding kernel for this support / pol count");
 }
 
-awg_status degrid_slot_sep(int S, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+awg_status degrid_slot_sep(int S, int cand, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
   if (has_exact(S)) {   // the plan binned this support by its exact-kernel tile
-#define AWG_CASE(SS, PP) \
-  if (S == SS && P == PP) return run_degrid_exact<SS, PP>(a, slot, sms, st);
-    AWG_FOR_EXACT_AND_POLS(AWG_CASE)
+#define AWG_CASE(SS, PP, CC) \
+  if (S == SS && P == PP && cand == CC) return run_degrid_exact<SS, PP, CC>(a, slot, sms, st);
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 0)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 1)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
   }
@@ -129,15 +135,12 @@ __global__ void k_sum_terms(const float2* __restrict__ part, float2* __restrict_
   }
 }
 
-awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float* weight, int P, void* grid,
-                       void* grid_lo, double* sumwt, int flags, cudaStream_t st) {
-  if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
-  pl->last_stream = st;
-  if (pl->n == 0) return AWG_OK;
+static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* vis, const float* weight, void* grid,
+                          void* grid_lo, double* sumwt, int flags) {
   GridArgs a;
   a.rec = pl->d_rec;
   a.items = pl->d_items;
-  a.class_range = pl->d_class_range;
+  a.class_range = cf->separable ? pl->d_slot_range : pl->d_class_range;
   a.queue = pl->d_queue;
   a.cf = cf->d_data;
   a.cf_off = cf->d_off;
@@ -159,33 +162,14 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
   a.rank = pl->rank;
-  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
-  const int sms = sm_count(pl->device);
-  const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
-  if (cf->separable) {
-    a.class_range = pl->d_slot_range;
-    for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
-      awg_status s = grid_slot_sep(cf->slots.S[i], i, P, a, sms, st);
-      if (s != AWG_OK) return s;
-    }
-    return AWG_OK;
-  }
-  for (int c = kNumClasses - 1; c >= 0; --c) {   // largest supports first
-    if (!class_present(cf, c)) continue;
-    awg_status s = bf16 ? grid_class<true>(c, P, a, sms, st) : grid_class<false>(c, P, a, sms, st);
-    if (s != AWG_OK) return s;
-  }
-  return AWG_OK;
+  return a;
 }
 
-awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vis_out, int P, cudaStream_t st) {
-  if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
-  pl->last_stream = st;
-  if (pl->n == 0) return AWG_OK;
+static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* grid, void* vis_out) {
   DegridArgs a;
   a.rec = pl->d_rec;
   a.items = pl->d_items;
-  a.class_range = pl->d_class_range;
+  a.class_range = cf->separable ? pl->d_slot_range : pl->d_class_range;
   a.queue = pl->d_queue;
   a.cf = cf->d_data;
   a.cf_off = cf->d_off;
@@ -199,27 +183,48 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   a.uvw = pl->d_uvw;
   a.freq = pl->d_freq;
   a.grid = (const float*)grid;
-  // with several terms per CF every record writes its own row of the per-term buffer, summed below
+  // with several terms per CF every record writes its own row of the per-term buffer, summed later
   a.vis_out = pl->rank > 1 ? (float*)pl->d_part : (float*)vis_out;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
   a.rank = pl->rank;
+  return a;
+}
+
+static awg_status check_version(const CfSetImpl* cf, const PlanImpl* pl) {
+  if (pl->slots_version != cf->slots_version)
+    return set_error(AWG_ERR_INVALID_ARG, "the CF set was retuned after this plan was made; create a new plan");
+  return AWG_OK;
+}
+
+awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float* weight, int P, void* grid,
+                       void* grid_lo, double* sumwt, int flags, cudaStream_t st) {
+  if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
+  awg_status s = check_version(cf, pl);
+  if (s != AWG_OK) return s;
+  pl->last_stream = st;
+  if (pl->n == 0) return AWG_OK;
+  const GridArgs a = grid_args(cf, pl, vis, weight, grid, grid_lo, sumwt, flags);
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
   if (cf->separable) {
-    a.class_range = pl->d_slot_range;
-    for (int i = cf->slots.n - 1; i >= 0; --i) {
-      awg_status s = degrid_slot_sep(cf->slots.S[i], i, P, a, sms, st);
+    for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
+      s = grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
       if (s != AWG_OK) return s;
     }
-  } else {
-    for (int c = kNumClasses - 1; c >= 0; --c) {
-      if (!class_present(cf, c)) continue;
-      awg_status s = bf16 ? degrid_class<true>(c, P, a, sms, st) : degrid_class<false>(c, P, a, sms, st);
-      if (s != AWG_OK) return s;
-    }
+    return AWG_OK;
   }
+  for (int c = kNumClasses - 1; c >= 0; --c) {   // largest supports first
+    if (!class_present(cf, c)) continue;
+    s = bf16 ? grid_class<true>(c, P, a, sms, st) : grid_class<false>(c, P, a, sms, st);
+    if (s != AWG_OK) return s;
+  }
+  return AWG_OK;
+}
+
+// Per-term values summed, then dropped samples zeroed (after the kernels of launch_degrid).
+static awg_status degrid_finish(PlanImpl* pl, void* vis_out, int P, int sms, cudaStream_t st) {
   if (pl->rank > 1) {   // dropped samples' rows are stale here and are zeroed next
     k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, P);
     AWG_CUDA_TRY(cudaGetLastError());
@@ -229,6 +234,150 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return AWG_OK;
+}
+
+awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vis_out, int P, cudaStream_t st) {
+  if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
+  awg_status s = check_version(cf, pl);
+  if (s != AWG_OK) return s;
+  pl->last_stream = st;
+  if (pl->n == 0) return AWG_OK;
+  const DegridArgs a = degrid_args(cf, pl, grid, vis_out);
+  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+  const int sms = sm_count(pl->device);
+  const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
+  if (cf->separable) {
+    for (int i = cf->slots.n - 1; i >= 0; --i) {
+      s = degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
+      if (s != AWG_OK) return s;
+    }
+  } else {
+    for (int c = kNumClasses - 1; c >= 0; --c) {
+      if (!class_present(cf, c)) continue;
+      s = bf16 ? degrid_class<true>(c, P, a, sms, st) : degrid_class<false>(c, P, a, sms, st);
+      if (s != AWG_OK) return s;
+    }
+  }
+  return degrid_finish(pl, vis_out, P, sms, st);
+}
+
+__global__ void k_fill_ones(float* vis, float* weight, int64_t n_vis) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vis; i += stride) {
+    vis[2 * i] = 1.f;
+    vis[2 * i + 1] = 0.f;
+    weight[i] = 1.f;
+  }
+}
+
+awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, const double* freq, int n_chan,
+                             const int32_t* pa_bin, const int32_t* chan_sb, int P, cudaStream_t st, int32_t* choice,
+                             float* ms_out) {
+  for (int S = 0; S <= kMaxSupport; ++S) choice[S] = -1;
+  if (ms_out)
+    for (int i = 0; i < kNumCand * (kMaxSupport + 1); ++i) ms_out[i] = 0.f;
+  if (!cf->separable) return AWG_OK;   // full-table sets have one kernel per class
+  const int N = cf->p.grid_n;
+  const int64_t n = n_rows * (int64_t)n_chan;
+  // unit visibilities and weights (a value-independent timing; zeros would skip the flushes)
+  float *vis = nullptr, *wt = nullptr, *grid = nullptr, *out = nullptr;
+  double* sumwt = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  A((void**)&vis, sizeof(float2) * std::max<int64_t>(n * P, 1));
+  A((void**)&wt, sizeof(float) * std::max<int64_t>(n * P, 1));
+  A((void**)&out, sizeof(float2) * std::max<int64_t>(n * P, 1));
+  A((void**)&grid, sizeof(float2) * (size_t)N * N * P);
+  A((void**)&sumwt, sizeof(double) * P);
+  cudaEvent_t ev[4] = {};
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  auto cleanup = [&]() {
+    cudaFree(vis); cudaFree(wt); cudaFree(out); cudaFree(grid); cudaFree(sumwt);
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_error(e, "autotune allocation");
+  }
+  const int sms = sm_count(cf->device);
+  awg_status s = AWG_OK;
+  float best[kMaxSupport + 1];
+  for (int S = 0; S <= kMaxSupport; ++S) best[S] = 3.4e38f;
+  int8_t pick[kMaxSupport + 1] = {};
+  for (int c = 0; c < kNumCand && s == AWG_OK; ++c) {
+    for (int S = 1; S <= kMaxSupport; ++S)
+      if (has_exact(S)) cf->cand[S] = (int8_t)c;
+    fill_slots(cf);
+    awg_plan h = nullptr;
+    s = plan_create((awg_cf_set)cf, uvw, n_rows, freq, n_chan, pa_bin, chan_sb, nullptr, st, &h);
+    if (s != AWG_OK) break;
+    PlanImpl* pl = (PlanImpl*)h;
+    if (n > 0) {
+      k_fill_ones<<<sms * 4, 256, 0, st>>>(vis, wt, n * P);
+      count_launches(1);
+      if ((e = cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)N * N * P, st)) != cudaSuccess ||
+          (e = cudaMemsetAsync(sumwt, 0, sizeof(double) * P, st)) != cudaSuccess) {
+        s = cuda_error(e, "autotune memset");
+      }
+      // warm-up pass over every support, then three timed passes of each support's launches
+      if (s == AWG_OK) s = launch_grid(cf, pl, vis, wt, P, grid, nullptr, sumwt, 0, st);
+      if (s == AWG_OK) s = launch_degrid(cf, pl, grid, out, P, st);
+      const GridArgs ga = grid_args(cf, pl, vis, wt, grid, nullptr, sumwt, 0);
+      const DegridArgs da = degrid_args(cf, pl, grid, out);
+      for (int i = 0; i < cf->slots.n && s == AWG_OK; ++i) {
+        const int S = cf->slots.S[i];
+        if (!has_exact(S)) continue;
+        float t = 3.4e38f;
+        for (int rep = 0; rep < 3 && s == AWG_OK; ++rep) {
+          if ((e = cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st)) != cudaSuccess) {
+            s = cuda_error(e, "autotune memset");
+            break;
+          }
+          cudaEventRecord(ev[0], st);
+          s = grid_slot_sep(S, c, i, P, ga, sms, st);
+          cudaEventRecord(ev[1], st);
+          if (s != AWG_OK) break;
+          if ((e = cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st)) != cudaSuccess) {
+            s = cuda_error(e, "autotune memset");
+            break;
+          }
+          cudaEventRecord(ev[2], st);
+          s = degrid_slot_sep(S, c, i, P, da, sms, st);
+          cudaEventRecord(ev[3], st);
+          if (s != AWG_OK) break;
+          if ((e = cudaEventSynchronize(ev[3])) != cudaSuccess) {
+            s = cuda_error(e, "autotune timing");
+            break;
+          }
+          float tg = 0.f, td = 0.f;
+          cudaEventElapsedTime(&tg, ev[0], ev[1]);
+          cudaEventElapsedTime(&td, ev[2], ev[3]);
+          t = std::min(t, tg + td);
+        }
+        if (ms_out) ms_out[c * (kMaxSupport + 1) + S] = t;
+        if (t < best[S]) {
+          best[S] = t;
+          pick[S] = (int8_t)c;
+        }
+      }
+    }
+    if (s == AWG_OK) {
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) s = cuda_error(e, "autotune");
+    }
+    plan_destroy(h);
+  }
+  // the fastest candidate of every timed support (candidate 0 where nothing was timed)
+  for (int S = 1; S <= kMaxSupport; ++S)
+    if (has_exact(S)) {
+      cf->cand[S] = s == AWG_OK ? pick[S] : 0;
+      if (s == AWG_OK && best[S] < 3.4e38f) choice[S] = pick[S];
+    }
+  fill_slots(cf);
+  cleanup();
+  return s;
 }
 
 awg_status launch_normalize(CfSetImpl* cf, void* image, int P, const double* sumwt, int direction, cudaStream_t st) {

@@ -99,6 +99,7 @@ extern "C" awg_status grid_visibilities_noalloc(awg_cf_set hc, const double* uvw
   pl.C = n_chan;
   pl.n = n;
   pl.rank = rank;
+  pl.slots_version = cf->slots_version;
   pl.n_rec = n * rank;
   pl.device = cf->device;
   pl.n_buckets = nb;

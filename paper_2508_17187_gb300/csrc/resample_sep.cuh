@@ -658,11 +658,11 @@ awg_status run_degrid_sep(const DegridArgs& a, int slot, int sms, cudaStream_t s
   return AWG_OK;
 }
 
-// Exact-support kernels (the kExact table): S is a compile-time constant and the row groups
+// Exact-support kernels (the kExactCand table): S is a compile-time constant and the row groups
 // divide S, so every thread owns the same number of rows.
-template <int S, int P>
+template <int S, int P, int C>
 awg_status run_grid_exact(const GridArgs& a, int slot, int sms, cudaStream_t st) {
-  constexpr ExactCfg e = exact_cfg(S);
+  constexpr ExactCfg e = exact_cfg(S, C);
   constexpr int nt = S * e.g_grid;
   static_assert(e.tile > 0 && S % e.g_grid == 0 && nt <= 1024 && e.stage >= 1 && e.stage <= nt,
                 "bad exact-support configuration");
@@ -681,9 +681,9 @@ awg_status run_grid_exact(const GridArgs& a, int slot, int sms, cudaStream_t st)
   return AWG_OK;
 }
 
-template <int S, int P>
+template <int S, int P, int C>
 awg_status run_degrid_exact(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
-  constexpr ExactCfg e = exact_cfg(S);
+  constexpr ExactCfg e = exact_cfg(S, C);
   constexpr int nt = S * e.g_degrid;
   static_assert(e.tile > 0 && S % e.g_degrid == 0 && nt <= 1024 && e.stage >= 1 && e.stage <= nt,
                 "bad exact-support configuration");
@@ -702,16 +702,18 @@ awg_status run_degrid_exact(const DegridArgs& a, int slot, int sms, cudaStream_t
   return AWG_OK;
 }
 
-#define AWG_FOR_EXACT_AND_POLS(M) \
-  M(8, 1) M(8, 2) M(8, 4) M(16, 1) M(16, 2) M(16, 4) M(24, 1) M(24, 2) M(24, 4) M(32, 1) M(32, 2) M(32, 4) \
-  M(40, 1) M(40, 2) M(40, 4) M(48, 1) M(48, 2) M(48, 4) M(56, 1) M(56, 2) M(56, 4) M(64, 1) M(64, 2) M(64, 4)
-#define AWG_DECLARE_GRID_EXACT(S, P) \
-  extern template awg_status run_grid_exact<S, P>(const GridArgs&, int, int, cudaStream_t);
-#define AWG_DECLARE_DEGRID_EXACT(S, P) \
-  extern template awg_status run_degrid_exact<S, P>(const DegridArgs&, int, int, cudaStream_t);
-#define AWG_INSTANTIATE_GRID_EXACT(S, P) template awg_status run_grid_exact<S, P>(const GridArgs&, int, int, cudaStream_t);
-#define AWG_INSTANTIATE_DEGRID_EXACT(S, P) \
-  template awg_status run_degrid_exact<S, P>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_FOR_EXACT_AND_POLS(M, C)                                                                        \
+  M(8, 1, C) M(8, 2, C) M(8, 4, C) M(16, 1, C) M(16, 2, C) M(16, 4, C) M(24, 1, C) M(24, 2, C) M(24, 4, C)      \
+  M(32, 1, C) M(32, 2, C) M(32, 4, C) M(40, 1, C) M(40, 2, C) M(40, 4, C) M(48, 1, C) M(48, 2, C) M(48, 4, C) \
+  M(56, 1, C) M(56, 2, C) M(56, 4, C) M(64, 1, C) M(64, 2, C) M(64, 4, C)
+#define AWG_DECLARE_GRID_EXACT(S, P, C) \
+  extern template awg_status run_grid_exact<S, P, C>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_DECLARE_DEGRID_EXACT(S, P, C) \
+  extern template awg_status run_degrid_exact<S, P, C>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_EXACT(S, P, C) \
+  template awg_status run_grid_exact<S, P, C>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_DEGRID_EXACT(S, P, C) \
+  template awg_status run_degrid_exact<S, P, C>(const DegridArgs&, int, int, cudaStream_t);
 
 #define AWG_FOR_SEP_CLASSES_AND_POLS(M) \
   M(0, 1) M(0, 2) M(0, 4) M(1, 1) M(1, 2) M(1, 4) M(2, 1) M(2, 2) M(2, 4) M(3, 1) M(3, 2) M(3, 4) M(4, 1) M(4, 2) M(4, 4) \

@@ -205,7 +205,7 @@ def test_awproj_parity(awg, separable):
     assert np.all(res["vis"][~orc["idx"].valid] == 0)
 
 
-def _random_tables_case(awg, P, rank1):
+def _random_tables_case(awg, P, rank1, config=0):
     sups = [1, 3, 7, 8, 9, 15, 16, 17, 24, 25, 31, 32, 33, 40, 48, 49, 56, 63, 64]
     wl = synth.make_workload("standard", n_int=16, n_chan=3, f_lo=2.8e9, f_hi=3.2e9, with_vis=False)
     N = 384
@@ -239,6 +239,10 @@ def _random_tables_case(awg, P, rank1):
     cfset = awg.cf_set_create_from_table(sups, buf.astype(np.complex64), grid_n=N, cell_rad=op.cell_rad,
                                          oversampling=OS, n_pa_bins=len(sups), separable=True)
     assert cfset.separable == rank1
+    if config:
+        for S in sups:
+            if S % 8 == 0:
+                cfset.choose(S, config)
     res = _run_library(awg, op, wl.uvw_m, wl.freq_hz, V, W, pa_bin=pa_bin, cf=cfset)
     g_o, sw_o = oops.grid(idx, buf, offs, OS, N, V.astype(np.complex128), W.astype(np.float64))
     assert rel_rms(res["grid"], g_o) < 1e-5
@@ -269,11 +273,13 @@ def test_every_support_class_random_tables(awg, P):
     _random_tables_case(awg, P, rank1=False)
 
 
+@pytest.mark.parametrize("config", [0, 1])
 @pytest.mark.parametrize("P", [1, 2, 4])
-def test_every_support_separable_random_factors(awg, P):
+def test_every_support_separable_random_factors(awg, P, config):
     """Random outer-product tables with the same supports: the separable path, every exact-support
-    kernel (8, 16, ..., 64) and every class kernel for the supports in between."""
-    _random_tables_case(awg, P, rank1=True)
+    kernel (8, 16, ..., 64) in both compiled configurations and every class kernel for the
+    supports in between."""
+    _random_tables_case(awg, P, rank1=True, config=config)
 
 
 @pytest.mark.parametrize("separable", [True, False])
