@@ -4,7 +4,7 @@ Tolerances.  Inputs are FP32 (visibilities, weights, CF values); the oracle sums
 in FP64.  Each FP32 product and add carries a relative rounding of at most 2^-24 ~ 6e-8, and a
 pixel's sum of n contributions in FP32 has a relative RMS error of order 6e-8 sqrt(n); with
 n <= 10^5 that is below 2e-5 in the worst pixel and about 1e-6 over the grid.  The gate used for
-whole grids, images and visibility vectors is the benchmark spec's 1e-5 relative RMS; BF16 CF tables
+whole grids, images and visibility vectors is the 1e-5 relative RMS accuracy target; BF16 CF tables
 (8-bit mantissa, 2^-9 relative) get their own, looser gate.  Integer-valued inputs make FP32 sums
 exact, and there the comparison is bit for bit.
 """
