@@ -284,6 +284,26 @@ awg_status degrid_visibilities_plain_fp64(awg_cf_set cf, const double* uvw_m, in
  */
 awg_status awg_fp32_fma_probe(float* out, int32_t n_blocks, int64_t iters, void* stream, double* flop);
 
+/*
+ * Hogbom CLEAN minor cycle (the deconvolution step of the major cycle, Sec. 5.2; Eq. ModelUpdate
+ * with point components).  n_iter iterations, each: find the pixel p of largest |residual| inside
+ * the search window (ties: the lowest linear index y N + x), stop for good once that value is
+ * below `threshold`; else g = gain * residual[p] (FP32), model[p] += g, and residual[y][x] -=
+ * g * psf[y - py + psf_n/2][x - px + psf_n/2] wherever that PSF pixel exists.  Products and sums
+ * are separately rounded FP32 operations (no fused multiply-add).
+ * residual, model: device f32 [N][N] (row y, column x), updated in place; psf: device f32
+ * [psf_n][psf_n], peak at (psf_n/2, psf_n/2) (psf_n = 2N covers every shift); window: host
+ * int32 {x0, x1, y0, y1} (half-open) or NULL for the whole image; gain in (0, 1]; threshold >= 0.
+ * workspace: device, clean_hogbom_workspace_bytes() bytes, 16-byte aligned, caller-owned.
+ * Asynchronous on `stream` (3 launches per iteration, no host synchronisation, graph-capturable).
+ * Errors: INVALID_ARG, UNSUPPORTED (N^2 >= 2^31), CUDA.
+ */
+int64_t clean_hogbom_workspace_bytes(void);
+awg_status clean_hogbom(float* residual, float* model, int32_t N, const float* psf, int32_t psf_n, int32_t n_iter,
+                        float gain, float threshold, const int32_t* window, void* workspace, void* stream);
+/* Number of components the last clean_hogbom on this workspace found (synchronises). */
+awg_status clean_hogbom_components(const void* workspace, int32_t* n_done);
+
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* awg_last_error(void);
 

@@ -19,7 +19,8 @@ EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_s
             "cf_set_copy_table", "plan_create", "plan_update", "plan_destroy", "plan_stats", "grid_visibilities",
             "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
             "grid_visibilities_noalloc", "grid_visibilities_plain_fp64", "degrid_visibilities_plain_fp64",
-            "awg_fp32_fma_probe", "cf_set_autotune", "cf_set_choose"]
+            "awg_fp32_fma_probe", "cf_set_autotune", "cf_set_choose", "clean_hogbom_workspace_bytes",
+            "clean_hogbom", "clean_hogbom_components"]
 
 
 class AwgError(RuntimeError):
@@ -89,6 +90,9 @@ def load():
             "awg_fp32_fma_probe": ([vp, i32, i64, vp, ctypes.POINTER(ctypes.c_double)], st),
             "cf_set_autotune": ([vp, vp, i64, vp, i32, vp, vp, i32, vp, vp, vp], st),
             "cf_set_choose": ([vp, i32, i32], st),
+            "clean_hogbom_workspace_bytes": ([], ctypes.c_int64),
+            "clean_hogbom": ([vp, vp, i32, vp, i32, i32, ctypes.c_float, ctypes.c_float, vp, vp, vp], st),
+            "clean_hogbom_components": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

@@ -12,7 +12,8 @@ import torch
 from . import _lib
 from ._lib import AWG_CF_BF16, AWG_CF_FP32, AWG_GRID_FP64, AWG_GRID_KAHAN, CfParams, check
 
-__all__ = ["CFSet", "Plan", "cf_set_create", "cf_set_create_from_table", "plan_create", "grid_visibilities",
+__all__ = ["CFSet", "Plan", "CleanWorkspace", "cf_set_create", "cf_set_create_from_table", "plan_create",
+           "clean_hogbom", "grid_visibilities",
            "degrid_visibilities", "grid_normalize", "AWG_CF_FP32", "AWG_CF_BF16", "AWG_GRID_KAHAN", "AWG_GRID_FP64"]
 
 
@@ -269,3 +270,39 @@ def grid_normalize(cf: CFSet, image: torch.Tensor, sumwt: Optional[torch.Tensor]
         _need(sumwt, "sumwt", torch.float64, (P,))
     check(_lib.load().grid_normalize(cf.handle, _ptr(image), P, _ptr(sumwt), int(direction), _stream_ptr(stream)),
           "grid_normalize")
+
+
+class CleanWorkspace:
+    """Device workspace of clean_hogbom (holds the iteration state and the component count)."""
+
+    def __init__(self, device="cuda"):
+        nbytes = int(_lib.load().clean_hogbom_workspace_bytes())
+        self.buf = torch.zeros((nbytes + 15) // 16 * 4, dtype=torch.float32, device=device)
+
+    def components(self) -> int:
+        n = ctypes.c_int32()
+        check(_lib.load().clean_hogbom_components(_ptr(self.buf), ctypes.byref(n)), "clean_hogbom_components")
+        return int(n.value)
+
+
+def clean_hogbom(residual: torch.Tensor, model: torch.Tensor, psf: torch.Tensor, n_iter: int, gain: float = 0.1,
+                 threshold: float = 0.0, window=None, workspace: Optional[CleanWorkspace] = None,
+                 stream=None) -> CleanWorkspace:
+    """Hogbom minor cycle in place on residual / model (f32 [N, N]) with psf (f32 [Np, Np], peak at
+    Np/2); window = (x0, x1, y0, y1) or None.  Asynchronous; returns the workspace (component count)."""
+    N = residual.shape[0]
+    _need(residual, "residual", torch.float32, (N, N))
+    _need(model, "model", torch.float32, (N, N))
+    if psf.dim() != 2 or psf.shape[0] != psf.shape[1]:
+        raise ValueError("psf must be square")
+    _need(psf, "psf", torch.float32)
+    ws = workspace or CleanWorkspace(residual.device)
+    win = None
+    if window is not None:
+        win = np.ascontiguousarray(window, dtype=np.int32)
+        if win.shape != (4,):
+            raise ValueError("window must be (x0, x1, y0, y1)")
+    check(_lib.load().clean_hogbom(_ptr(residual), _ptr(model), N, _ptr(psf), psf.shape[0], int(n_iter), float(gain),
+                                   float(threshold), None if win is None else win.ctypes.data_as(ctypes.c_void_p),
+                                   _ptr(ws.buf), _stream_ptr(stream)), "clean_hogbom")
+    return ws

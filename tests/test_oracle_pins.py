@@ -336,3 +336,60 @@ def test_degrid_model_matches_analytic_visibilities(oracle_built):
     uvw2[:, 2] = 0.0                                 # plain 2-D degridding has no w-term
     ref = image.point_source_vis(uvw2, wl.freq_hz, l, m, fl)[:, 0]
     assert np.abs(d - ref).max() < 2e-3 * fl.sum()
+
+
+# ------------------------------------------------------------------------------------ Hogbom CLEAN
+
+def _compact_psf(Np, half=4, width=4.0):
+    yy, xx = np.mgrid[0:Np, 0:Np]
+    psf = np.exp(-(((yy - Np // 2) ** 2 + (xx - Np // 2) ** 2) / width)).astype(np.float32)
+    psf[np.abs(yy - Np // 2) > half] = 0
+    psf[np.abs(xx - Np // 2) > half] = 0
+    return psf
+
+
+def _place(psf, N, y, x):
+    Np = psf.shape[0]
+    return psf[Np // 2 - y:Np // 2 - y + N, Np // 2 - x:Np // 2 - x + N]
+
+
+def test_clean_gain_one_recovers_separated_sources_exactly():
+    """Sources further apart than the PSF, gain 1: each iteration removes one source completely
+    (textbook Hogbom), so the model is the source list and the residual is exactly zero."""
+    from oracle import clean
+    N = 64
+    psf = _compact_psf(2 * N)
+    src = [(10, 12, 1.0), (30, 40, 0.5), (50, 20, -0.75), (5, 58, 0.25)]
+    img = np.zeros((N, N), np.float32)
+    for y, x, a in src:
+        img += np.float32(a) * _place(psf, N, y, x)
+    res, model, comps = clean.hogbom(img, psf, len(src), 1.0)
+    assert sorted((y, x, a) for y, x, a in comps) == sorted(src)
+    assert np.all(res == 0)
+    assert model[10, 12] == 1.0 and model[50, 20] == -0.75 and np.count_nonzero(model) == len(src)
+
+
+def test_clean_single_source_geometric_decay_and_threshold():
+    """One point source: after n iterations the peak residual is a (1 - g)^n and the model holds
+    a (1 - (1 - g)^n) at the source; with a threshold t the loop stops after the first n with
+    a (1 - g)^n < t."""
+    from oracle import clean
+    N, a, g = 48, 2.0, 0.2
+    psf = _compact_psf(2 * N)
+    img = np.float32(a) * _place(psf, N, 20, 27)
+    res, model, comps = clean.hogbom(img, psf, 12, g)
+    assert len(comps) == 12 and all((y, x) == (20, 27) for y, x, _ in comps)
+    assert abs(res[20, 27] - a * (1 - g) ** 12) < 1e-5
+    assert abs(model[20, 27] - a * (1 - (1 - g) ** 12)) < 1e-5
+    t = 0.3
+    _, _, comps = clean.hogbom(img, psf, 100, g, threshold=t)
+    assert len(comps) == int(np.ceil(np.log(t / a) / np.log(1 - g)))
+
+
+def test_clean_search_window_excludes_outside_peaks():
+    from oracle import clean
+    N = 48
+    psf = _compact_psf(2 * N)
+    img = 5.0 * _place(psf, N, 5, 5) + 1.0 * _place(psf, N, 30, 30)
+    _, model, comps = clean.hogbom(img.astype(np.float32), psf, 1, 1.0, window=(20, 40, 20, 40))
+    assert comps == [(30, 30, 1.0)] and model[5, 5] == 0
