@@ -57,6 +57,8 @@ def parse():
                          "(20 PA bins x 32 w-planes x 16 sub-bands, CFs as sums of outer products)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel configuration of every support instead of timing both")
+    ap.add_argument("--minor-cycle", action="store_true",
+                    help="time the Hogbom minor cycle on a 4096^2 image (one JSON line, HBM roofline)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="CF storage / accumulation variants against the FP64 oracle (one JSON line each)")
     return ap.parse_args()
@@ -277,6 +279,58 @@ def reference_arm(args):
     return 0
 
 
+def minor_cycle_bench(args):
+    """Hogbom minor cycle on a 4096 x 4096 FP32 residual with an 8192 x 8192 PSF (every shift
+    covered): iterations per second, and the HBM roofline of one iteration, whose algorithmic
+    traffic is the window search (4 B per window pixel) plus the subtraction (residual read and
+    written, PSF read: 12 B per image pixel)."""
+    import torch
+
+    import paper_2508_17187_gb300 as awg
+    N, n_iter = 4096, 1000
+    Np = 2 * N
+    g = torch.Generator(device="cuda").manual_seed(7)
+    r = torch.hypot(*torch.meshgrid(torch.arange(Np, device="cuda", dtype=torch.float32) - Np // 2,
+                                    torch.arange(Np, device="cuda", dtype=torch.float32) - Np // 2, indexing="ij"))
+    psf = (torch.exp(-r ** 2 / 8.0) + 0.15 * torch.cos(r / 2.5) * torch.exp(-r / 400.0)).contiguous()
+    del r
+    base = torch.randn((N, N), device="cuda", generator=g) * 0.01
+    ys = torch.randint(N // 8, 7 * N // 8, (300,), generator=g, device="cuda")
+    xs = torch.randint(N // 8, 7 * N // 8, (300,), generator=g, device="cuda")
+    amp = torch.rand(300, generator=g, device="cuda") * 0.8 + 0.2
+    for y, x, a in zip(ys.tolist(), xs.tolist(), amp.tolist()):
+        base += a * psf[Np // 2 - y:Np // 2 - y + N, Np // 2 - x:Np // 2 - x + N]
+    window = (N // 4, 3 * N // 4, N // 4, 3 * N // 4)
+    res, model = base.clone(), torch.zeros_like(base)
+    ws = awg.CleanWorkspace()
+    for _ in range(3):                       # warm-up
+        res.copy_(base)
+        model.zero_()
+        awg.clean_hogbom(res, model, psf, 50, 0.1, 0.0, window, ws)
+    torch.cuda.synchronize()
+    res.copy_(base)
+    model.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    awg.clean_hogbom(res, model, psf, n_iter, 0.1, 0.0, window, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    per_it = ms / n_iter
+    nbytes = (window[1] - window[0]) * (window[3] - window[2]) * 4 + N * N * 12
+    achieved = nbytes / (per_it / 1e3) / 1e9
+    peak = measured_peaks().get("hbm_gbs")
+    line = {"metric": "Hogbom minor-cycle iterations/s", "value": n_iter / (ms / 1e3), "unit": "iterations/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": n_iter, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4096x4096 residual, 8192x8192 PSF, 300 sources, inner-half search window, gain 0.1"},
+            "components": ws.components(), "us_per_iteration": per_it * 1e3,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "bytes_per_iteration": nbytes, "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def precision_sweep(args):
     """Per-variant dirty-image and degridding error against the FP64 oracle, and throughput.
 
@@ -415,6 +469,8 @@ def main():
         return reference_arm(args)
     if args.precision_sweep:
         return precision_sweep(args)
+    if args.minor_cycle:
+        return minor_cycle_bench(args)
     import torch
     import torch.distributed as dist
 

@@ -169,6 +169,27 @@ __device__ __forceinline__ void stage_payload(const float* sep, const float* vis
   }
 }
 
+// Column residue rx and first row ry0 of thread t (it owns rows ry0 + k G).  Generic: rx = t mod S,
+// ry0 = t div S.  For an exact support that is a multiple of 8 whose warps tile the columns in
+// blocks of 8 (NT / 32 a multiple of S / 8), a warp instead covers 8 consecutive columns x 4 row
+// groups: its per-sample column loads (alpha, beta) then touch 8 distinct addresses, one
+// shared-memory wavefront, instead of 32.  Both mappings give every (column, row group) pair to
+// exactly one thread.  Degridding without the register grid cache reads the window for every
+// tap, where 4 rows per warp cost bank conflicts; it keeps the generic mapping.
+template <int SMIN, int SMAX, int NT, bool BLOCKED_OK>
+__device__ __forceinline__ void tap_owner(int t, int S, int& rx, int& ry0) {
+  constexpr bool kBlocked = BLOCKED_OK && SMIN + 1 == SMAX && SMAX % 8 == 0 && (NT / 32) % (SMAX / 8) == 0;
+  if constexpr (kBlocked) {
+    constexpr int kColBlocks = SMAX / 8;
+    const int lane = t & 31, w = t >> 5;
+    rx = (w % kColBlocks) * 8 + (lane & 7);
+    ry0 = (w / kColBlocks) * 4 + (lane >> 3);
+  } else {
+    rx = t % S;
+    ry0 = t / S;
+  }
+}
+
 // P consecutive complex values from shared memory (16-byte loads where the layout allows).
 template <int P>
 __device__ __forceinline__ void load_pols(const float2* src, float2 (&out)[P]) {
@@ -278,7 +299,8 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     const int X0 = wi.tile_x * TILE, Y0 = wi.tile_y * TILE;
     const int G = row_groups(S, NT);
     const bool active = tid < G * S;
-    const int rx = tid % S, ry0 = tid / S;
+    int rx, ry0;
+    tap_owner<SMIN, SMAX, NT, true>(tid, S, rx, ry0);
     unsigned vmask = 0;
 #pragma unroll
     for (int k = 0; k < R; ++k) vmask |= (ry0 + k * G < S) ? (1u << k) : 0u;
@@ -464,7 +486,8 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     const int X0 = wi.tile_x * TILE, Y0 = wi.tile_y * TILE;
     const int G = row_groups(S, NT);
     const bool active = tid < G * S;
-    const int rx = tid % S, ry0 = tid / S;
+    int rx, ry0;
+    tap_owner<SMIN, SMAX, NT, CACHE>(tid, S, rx, ry0);
     unsigned vmask = 0;
 #pragma unroll
     for (int k = 0; k < R; ++k) vmask |= (ry0 + k * G < S) ? (1u << k) : 0u;
