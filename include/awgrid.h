@@ -179,6 +179,21 @@ awg_status plan_create(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const
                        const double* phase_shift, void* stream, awg_plan* out);
 
 /*
+ * Per-row phase centres: mosaic pointings and antenna pointing offsets (the phase-gradient term
+ * of Eq. CIJ with s(P) and (Delta s_i + Delta s_j) / 2 per row; Tab. AWPSETUP-MOSAICKING).
+ * row_dlm: device f64 [R][2], (dl, dm) of the image centre relative to row r's phase centre,
+ * dl^2 + dm^2 < 1 (not checked); from here on G multiplies w V of every sample of row r by
+ * exp(+2 pi i (u dl_r + v dm_r + w dn_r)), dn_r = sqrt(1 - dl_r^2 - dm_r^2) - 1, and D by its
+ * conjugate, replacing the plan-wide shift of plan_create.  uvw_m [R][3] and freq_hz [C] (device)
+ * are the plan's current geometry, copied together with row_dlm into plan-owned memory (allocated
+ * on the first call; later plan_update calls refresh the geometry copy).  row_dlm = NULL returns
+ * to the plan-wide shift (or none) and frees the per-row copy (synchronising `stream`).
+ * Asynchronous otherwise.  Errors: INVALID_ARG, CUDA.
+ */
+awg_status plan_set_row_phase(awg_plan plan, const double* row_dlm, const double* uvw_m, const double* freq_hz,
+                              void* stream);
+
+/*
  * Recompute the plan for new uvw / frequency / bin data of the same R and C (no allocation;
  * stream-ordered; capturable in a CUDA graph).
  */

@@ -43,8 +43,14 @@ class SampleIndex:
 
 
 def sample_index(p: CFParams, uvw_m, freq_hz, pa_bin=None, chan_subband=None,
-                 phase_shift=None, supports=None) -> SampleIndex:
-    """Index every (row, channel) sample; `supports` overrides the schedule (caller-made tables)."""
+                 phase_shift=None, supports=None, row_phase=None) -> SampleIndex:
+    """Index every (row, channel) sample; `supports` overrides the schedule (caller-made tables).
+
+    Phase term of Eq. CIJ (reading: exp(+2 pi i u.(s_0 - s(P) - (Delta s_i + Delta s_j)/2)) with the
+    offset of the image centre from the phase centre, w included through dn = sqrt(1 - dl^2 - dm^2)
+    - 1): `phase_shift` (dl, dm) applies to every row; `row_phase` [R, 2] gives each row its own
+    (dl, dm) - the pointing of a mosaic field and the mean pointing offset of the row's antennas
+    (Tab. AWPSETUP-MOSAICKING) - and replaces `phase_shift`."""
     uvw_m = np.asarray(uvw_m, dtype=np.float64)
     freq_hz = np.asarray(freq_hz, dtype=np.float64)
     R, C = uvw_m.shape[0], freq_hz.shape[0]
@@ -85,7 +91,13 @@ def sample_index(p: CFParams, uvw_m, freq_hz, pa_bin=None, chan_subband=None,
     ox = np.floor(fx * OS + 0.5)
     oy = np.floor(fy * OS + 0.5)
     ph = None
-    if phase_shift is not None:
+    if row_phase is not None:
+        rp = np.asarray(row_phase, dtype=np.float64)
+        dl, dm = rp[:, 0:1], rp[:, 1:2]
+        dn = np.sqrt(1.0 - dl * dl - dm * dm) - 1.0
+        turns = u * dl + v * dm + w * dn
+        ph = np.exp(2j * math.pi * turns).reshape(-1)
+    elif phase_shift is not None:
         dl, dm = float(phase_shift[0]), float(phase_shift[1])
         dn = math.sqrt(1.0 - dl * dl - dm * dm) - 1.0
         turns = u * dl + v * dm + w * dn

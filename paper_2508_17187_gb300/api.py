@@ -201,6 +201,16 @@ class Plan:
             raise RuntimeError("plan already destroyed")
         return self._h
 
+    def set_row_phase(self, row_dlm: Optional[torch.Tensor], uvw_m: torch.Tensor, freq_hz: torch.Tensor, stream=None):
+        """Per-row phase centres (mosaic pointings / pointing offsets): row_dlm f64 [R, 2] on the
+        device, or None to return to the plan-wide shift (see plan_set_row_phase)."""
+        _need(uvw_m, "uvw_m", torch.float64, (self.n_rows, 3))
+        _need(freq_hz, "freq_hz", torch.float64, (self.n_chan,))
+        if row_dlm is not None:
+            _need(row_dlm, "row_dlm", torch.float64, (self.n_rows, 2))
+        check(_lib.load().plan_set_row_phase(self.handle, _ptr(row_dlm), _ptr(uvw_m), _ptr(freq_hz),
+                                             _stream_ptr(stream)), "plan_set_row_phase")
+
     def update(self, uvw_m, freq_hz, pa_bin=None, chan_subband=None, stream=None):
         _need(uvw_m, "uvw_m", torch.float64, (self.n_rows, 3))
         _need(freq_hz, "freq_hz", torch.float64, (self.n_chan,))

@@ -152,6 +152,8 @@ struct PlanImpl {
   unsigned long long* d_counters = nullptr;  // [0] kept, [1] dropped, [2] sum of S^2
   double* d_uvw = nullptr;        // plan-owned copies of uvw / freq (only with a phase shift,
   double* d_freq = nullptr;       // whose phasor the compute kernels form per sample)
+  double* d_row_dlm = nullptr;    // per-row phase centres [R][2] (plan_set_row_phase) or NULL
+  int global_phase = 0;           // a plan-wide phase shift was given to plan_create
   cudaStream_t last_stream = nullptr;
 };
 

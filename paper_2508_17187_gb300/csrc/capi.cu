@@ -556,6 +556,7 @@ static awg_status plan_free(PlanImpl* pl) {
   cudaFree(pl->d_counters);
   cudaFree(pl->d_uvw);
   cudaFree(pl->d_freq);
+  cudaFree(pl->d_row_dlm);
   delete pl;
   return AWG_OK;
 }
@@ -592,6 +593,7 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
     const double dl = phase_shift[0], dm = phase_shift[1];
     if (!(dl * dl + dm * dm < 1.0)) { delete pl; return set_error(AWG_ERR_INVALID_ARG, "phase shift outside the sky"); }
     pl->has_phase = 1;
+    pl->global_phase = 1;
     pl->dl = dl;
     pl->dm = dm;
     pl->dn = std::sqrt(1.0 - dl * dl - dm * dm) - 1.0;
@@ -632,6 +634,35 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
     return s;
   }
   *out = (awg_plan)pl;
+  return AWG_OK;
+}
+
+awg_status plan_set_row_phase(awg_plan h, const double* row_dlm, const double* uvw_m, const double* freq_hz,
+                              void* stream) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "plan is NULL");
+  PlanImpl* pl = (PlanImpl*)h;
+  if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!row_dlm) {   // back to the plan-wide shift (or none)
+    if (pl->d_row_dlm) {
+      AWG_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(pl->d_row_dlm);
+      pl->d_row_dlm = nullptr;
+    }
+    pl->has_phase = pl->global_phase;
+    return AWG_OK;
+  }
+  if (pl->R > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
+  const size_t R = (size_t)std::max<int64_t>(pl->R, 1);
+  if (!pl->d_row_dlm) AWG_CUDA_TRY(cudaMalloc(&pl->d_row_dlm, R * 2 * sizeof(double)));
+  if (!pl->d_uvw) AWG_CUDA_TRY(cudaMalloc(&pl->d_uvw, R * 3 * sizeof(double)));
+  if (!pl->d_freq) AWG_CUDA_TRY(cudaMalloc(&pl->d_freq, (size_t)pl->C * sizeof(double)));
+  if (pl->R > 0) {
+    AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_row_dlm, row_dlm, R * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_uvw, uvw_m, R * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_freq, freq_hz, (size_t)pl->C * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  pl->has_phase = 1;
   return AWG_OK;
 }
 

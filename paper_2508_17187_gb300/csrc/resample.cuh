@@ -38,6 +38,7 @@ struct GridArgs {
   double dl, dm, dn;
   const double* uvw;
   const double* freq;
+  const double* row_dlm; // per-row (dl, dm) [R][2] or NULL (then dl, dm, dn apply to every row)
   const float* vis;      // interleaved c64 [n][P]
   const float* weight;   // [n][P]
   float* grid;           // c64 [N][N][P] (or complex128 with AWG_GRID_FP64)
@@ -59,6 +60,7 @@ struct DegridArgs {
   double dl, dm, dn;
   const double* uvw;
   const double* freq;
+  const double* row_dlm; // per-row (dl, dm) [R][2] or NULL
   const float* grid;     // c64 [N][N][P]
   float* vis_out;        // c64 [n][P]; with rank > 1 the per-term values [n][rank][P]
   const float* sep;      // separable CF factors (c64), or NULL
@@ -92,6 +94,19 @@ __device__ __forceinline__ float2 sample_phasor(const double* uvw, const double*
   float s, co;
   sincospif(2.0f * (float)t, &s, &co);
   return make_float2(co, s);
+}
+
+// Per-row phase centres (mosaic pointings, antenna pointing offsets): row r of the plan has its
+// own (dl, dm) at row_dlm[2 r], and dn = sqrt(1 - dl^2 - dm^2) - 1 in a cancellation-free form.
+template <class Args>
+__device__ __forceinline__ float2 phasor_of(const Args& a, int src) {
+  if (a.row_dlm) {
+    const int r = src / a.C;
+    const double dl = a.row_dlm[2 * r], dm = a.row_dlm[2 * r + 1];
+    const double q = dl * dl + dm * dm;
+    return sample_phasor(a.uvw, a.freq, a.C, src, dl, dm, -q / (1.0 + sqrt(1.0 - q)));
+  }
+  return sample_phasor(a.uvw, a.freq, a.C, src, a.dl, a.dm, a.dn);
 }
 
 template <int SMAX, int TILE, int P>
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(NT) k_grid(const GridArgs a, const int cls) {
           wt[0] = __ldg(wp);
         }
         float2 ph = make_float2(1.f, 0.f);
-        if (a.has_phase) ph = sample_phasor(a.uvw, a.freq, a.C, rc.src, a.dl, a.dm, a.dn);
+        if (a.has_phase) ph = phasor_of(a, rc.src);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           wsum[p] += (double)wt[p];
@@ -376,7 +391,7 @@ __global__ void __launch_bounds__(NT) k_degrid(const DegridArgs a, const int cls
         s_pack[tid] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
         s_src[tid] = rc.src;
         float2 ph = make_float2(1.f, 0.f);
-        if (a.has_phase) ph = sample_phasor(a.uvw, a.freq, a.C, rc.src, a.dl, a.dm, a.dn);
+        if (a.has_phase) ph = phasor_of(a, rc.src);
         s_ph[tid] = ph;
       }
       __syncthreads();

@@ -41,3 +41,16 @@ def inner_half(img):
     """
     N = img.shape[0]
     return img[N // 4:3 * N // 4, N // 4:3 * N // 4]
+
+
+def mosaic_row_phase(wl, seed=4) -> np.ndarray:
+    """Per-row (dl, dm) of a two-field mosaic: pointings on alternating integrations, +-30 / +-20
+    cells from the image centre, plus a per-row jitter of up to 2 cells (the mean pointing offset of
+    the row's two antennas).  float64 [R, 2]."""
+    rng = np.random.default_rng(seed)
+    R = wl.n_rows
+    field = (np.arange(R) // wl.n_bl) % 2
+    dl = np.where(field == 0, 30.0, -30.0) * wl.cell_rad
+    dm = np.where(field == 0, -20.0, 20.0) * wl.cell_rad
+    jit = rng.uniform(-2.0, 2.0, (R, 2)) * wl.cell_rad
+    return np.stack([dl + jit[:, 0], dm + jit[:, 1]], -1)

@@ -297,6 +297,43 @@ def test_phase_shift_parity(awg, separable):
 
 
 @pytest.mark.parametrize("separable", [True, False])
+def test_mosaic_row_phase_parity(awg, separable):
+    """Per-row phase centres (mosaic pointings plus pointing offsets, Tab. AWPSETUP-MOSAICKING):
+    against the oracle, and switching back to no shift restores the plain result."""
+    from tests.helpers import mosaic_row_phase
+    wl = synth.make_workload("wproj", n_int=12, n_chan=6, grid_n=512, n_wplanes=6, max_support=32)
+    op = oracle_params(wl)
+    rp = mosaic_row_phase(wl)
+    cf = awg.cf_set_create(**library_params(op, separable=separable))
+    R, C, P, N = wl.n_rows, wl.n_chan, wl.n_pol, wl.grid_n
+    uvw, freq = _dev(wl.uvw_m), _dev(wl.freq_hz)
+    plan = awg.plan_create(cf, uvw, freq)
+    plan.set_row_phase(_dev(rp), uvw, freq)
+    vis = _dev(wl.vis.reshape(R, C, P), torch.complex64)
+    wt = _dev(wl.weight.reshape(R, C, P), torch.float32)
+    g = torch.zeros((N, N, P), dtype=torch.complex64, device="cuda")
+    sw = torch.zeros(P, dtype=torch.float64, device="cuda")
+    awg.grid_visibilities(cf, plan, vis, wt, g, sw)
+    out = torch.empty_like(vis)
+    awg.degrid_visibilities(cf, plan, g, out)
+    idx = oindex.sample_index(op, wl.uvw_m, wl.freq_hz, row_phase=rp)
+    buf, off, _ = ocf.flatten_cf_set(op, ocf.cf_set(op, which=set(np.unique(idx.cf[idx.valid]).tolist())))
+    g_o, _ = oops.grid(idx, buf, off, op.oversampling, N, wl.vis.reshape(-1, P).astype(np.complex128),
+                       wl.weight.reshape(-1, P).astype(np.float64))
+    assert rel_rms(g.cpu().numpy(), g_o) < 2e-5
+    d_o = oops.degrid(idx, buf, off, op.oversampling, g.cpu().numpy().astype(np.complex128))
+    assert rel_rms(out.cpu().numpy().reshape(-1, P), d_o) < 2e-5
+    # back to no shift: the plain operator
+    plan.set_row_phase(None, uvw, freq)
+    g2 = torch.zeros_like(g)
+    awg.grid_visibilities(cf, plan, vis, wt, g2, sw)
+    idx0 = oindex.sample_index(op, wl.uvw_m, wl.freq_hz)
+    g0, _ = oops.grid(idx0, buf, off, op.oversampling, N, wl.vis.reshape(-1, P).astype(np.complex128),
+                      wl.weight.reshape(-1, P).astype(np.float64))
+    assert rel_rms(g2.cpu().numpy(), g0) < 1e-5
+
+
+@pytest.mark.parametrize("separable", [True, False])
 @pytest.mark.parametrize("flags", ["kahan", "fp64"])
 def test_precision_variants(awg, flags, separable):
     wl = synth.make_workload("wproj", n_int=16, n_chan=6, grid_n=512, n_wplanes=6, max_support=32)

@@ -393,3 +393,38 @@ def test_clean_search_window_excludes_outside_peaks():
     img = 5.0 * _place(psf, N, 5, 5) + 1.0 * _place(psf, N, 30, 30)
     _, model, comps = clean.hogbom(img.astype(np.float32), psf, 1, 1.0, window=(20, 40, 20, 40))
     assert comps == [(30, 30, 1.0)] and model[5, 5] == 0
+
+
+# ------------------------------------------------------------------------ mosaic phase gradients
+
+def test_per_row_phase_undoes_rephasing_to_pointing_centres():
+    """Visibilities of one sky re-phased to per-row pointing centres (the data a mosaic records),
+    gridded with those rows' phase gradients, give the grid of the original visibilities gridded
+    with none; degridding with the gradients gives the original model visibilities re-phased."""
+    from oracle import cf as ocf
+    from oracle import index as oindex
+    from oracle import ops as oops
+    from tests.helpers import mosaic_row_phase, oracle_params
+    wl = synth.make_workload("wproj", n_int=6, n_chan=4, grid_n=256, n_wplanes=4, max_support=16, with_vis=True)
+    op = oracle_params(wl)
+    rp = mosaic_row_phase(wl)
+    idx0 = oindex.sample_index(op, wl.uvw_m, wl.freq_hz)
+    idx1 = oindex.sample_index(op, wl.uvw_m, wl.freq_hz, row_phase=rp)
+    assert np.array_equal(idx0.valid, idx1.valid) and np.array_equal(idx0.p0x, idx1.p0x)
+    # the data as recorded at each row's phase centre: V0 exp(-2 pi i (u dl + v dm + w dn)), written
+    # out here from the direction cosines of the shift rather than from the oracle's phasor
+    sc = wl.freq_hz / synth.C_LIGHT
+    u, v, w = (wl.uvw_m[:, k:k + 1] * sc[None, :] for k in range(3))
+    dl, dm = rp[:, 0:1], rp[:, 1:2]
+    n_shift = np.sqrt(1.0 - dl ** 2 - dm ** 2)
+    rephase = np.exp(-2j * np.pi * (u * dl + v * dm + w * (n_shift - 1.0))).reshape(-1, 1)
+    V0 = np.asarray(wl.vis, dtype=np.complex128).reshape(-1, wl.n_pol)
+    W = np.asarray(wl.weight, dtype=np.float64).reshape(-1, wl.n_pol)
+    tabs = ocf.cf_set(op, which=set(np.unique(idx0.cf[idx0.valid]).tolist()))
+    buf, off, _ = ocf.flatten_cf_set(op, tabs)
+    g0, _ = oops.grid(idx0, buf, off, op.oversampling, op.grid_n, V0, W)
+    g1, _ = oops.grid(idx1, buf, off, op.oversampling, op.grid_n, V0 * rephase, W)
+    assert np.abs(g1 - g0).max() <= 1e-10 * np.abs(g0).max()
+    d0 = oops.degrid(idx0, buf, off, op.oversampling, g0)
+    d1 = oops.degrid(idx1, buf, off, op.oversampling, g0)
+    assert np.abs(d1 - d0 * rephase).max() <= 1e-10 * np.abs(d0).max()
