@@ -59,6 +59,8 @@ def parse():
                     help="keep the default kernel configuration of every support instead of timing both")
     ap.add_argument("--minor-cycle", action="store_true",
                     help="time the Hogbom minor cycle on a 4096^2 image (one JSON line, HBM roofline)")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="time the G-Jones solve on the W-projection workload with degridded model visibilities")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="CF storage / accumulation variants against the FP64 oracle (one JSON line each)")
     return ap.parse_args()
@@ -331,6 +333,82 @@ def minor_cycle_bench(args):
     return 0
 
 
+def calibrate_bench(args):
+    """G-Jones calibration (Eq. VAvg, Eq. CalUpdateDir, Eq. CalUpdateModel) of the full W-projection
+    workload: model visibilities from degridding a point-source model grid (Eq. VMod), observed data =
+    per-antenna gains x model + 1% noise, solution intervals of 10 integrations x 16 channels for
+    both parallel hands (200 x 4 x 2 solutions of 27 antennas).  Reports visibilities/s of the
+    solve and the HBM roofline of its averaging pass (20 B per parallel-hand sample: V, M, w)."""
+    import torch
+
+    import paper_2508_17187_gb300 as awg
+    n_int = args.n_int or synth.CONFIGS["wproj"]["n_int"]
+    wl = rank_workload(1, 0, n_int, "cuda")
+    N, P, R, C = wl.grid_n, wl.n_pol, wl.n_rows, wl.n_chan
+    cf = awg.cf_set_create(**cf_kwargs(wl))
+    uvw, freq = torch.as_tensor(wl.uvw_m, device="cuda"), torch.as_tensor(wl.freq_hz, device="cuda")
+    plan = awg.plan_create(cf, uvw, freq)
+    model = torch.zeros((N, N, P), dtype=torch.complex64, device="cuda")
+    ii = ((torch.as_tensor(wl.sky_m) / wl.cell_rad).round().long() + N // 2).clamp(0, N - 1).cuda()
+    jj = ((torch.as_tensor(wl.sky_l) / wl.cell_rad).round().long() + N // 2).clamp(0, N - 1).cuda()
+    for p in (0, P - 1):
+        model[ii, jj, p] = torch.as_tensor(wl.sky_flux, dtype=torch.complex64, device="cuda")
+    awg.grid_normalize(cf, model, None, direction=1)
+    mgrid = torch.fft.fftshift(torch.fft.fft2(torch.fft.ifftshift(model, dim=(0, 1)), dim=(0, 1)), dim=(0, 1)).contiguous()
+    del model
+    M = torch.empty((R, C, P), dtype=torch.complex64, device="cuda")
+    awg.degrid_visibilities(cf, plan, mgrid, M)
+    a1, a2 = synth.baseline_antennas(27)
+    n_bl, sol_int, sol_chan = len(a1), 10, 16
+    n_ts, n_fs = -(-n_int // sol_int), -(-C // sol_chan)
+    g = torch.as_tensor(synth.antenna_gains((n_ts, n_fs, 2, 27), seed=5), device="cuda")
+    rows = torch.arange(R, device="cuda")
+    t_of = (rows // n_bl) // sol_int
+    b_of = rows % n_bl
+    A1, A2 = torch.as_tensor(a1, device="cuda")[b_of], torch.as_tensor(a2, device="cuda")[b_of]
+    f_of = torch.arange(C, device="cuda") // sol_chan
+    V = M.clone()
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    sigma = 0.01 * float(M.abs().mean())
+    for q, p in enumerate((0, P - 1)):
+        fac = g[t_of[:, None], f_of[None, :], q, A1[:, None]] * torch.conj(g[t_of[:, None], f_of[None, :], q, A2[:, None]])
+        V[:, :, p] = (M[:, :, p].to(torch.complex128) * fac).to(torch.complex64)
+        del fac
+    V += sigma * torch.complex(torch.randn(V.shape, device="cuda", generator=gen),
+                               torch.randn(V.shape, device="cuda", generator=gen))
+    W = wl.weight
+    ant1, ant2 = torch.as_tensor(a1, device="cuda"), torch.as_tensor(a2, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        G, its = awg.gcal_solve(V, M, W, ant1, ant2, 27, sol_int, sol_chan, alpha=0.5, delta=1e-10, max_iter=200)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        G, its = awg.gcal_solve(V, M, W, ant1, ant2, 27, sol_int, sol_chan, alpha=0.5, delta=1e-10, max_iter=200)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    gt = g * torch.conj(g[..., :1]) / g[..., :1].abs()
+    err = float((G - gt).abs().max())
+    nbytes = R * C * 2 * (8 + 8 + 4)
+    peak = measured_peaks().get("hbm_gbs")
+    achieved = nbytes / (ms / 1e3) / 1e9
+    line = {"metric": "calibrated visibilities/s (G-Jones solve)", "value": R * C * P / (ms / 1e3),
+            "unit": "visibilities/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "dtype": "f64 sums of f32 data", "data": "synthetic",
+            "config": {"workload": f"W-projection data {R} rows x {C} channels x {P} pols, model from degridding; "
+                                   f"solution intervals {sol_int} integrations x {sol_chan} channels, 2 hands, 27 antennas",
+                       "solutions": n_ts * n_fs * 2},
+            "iterations_max": int(its.max()), "iterations_mean": float(its.float().mean()),
+            "max_gain_error": err,
+            "roofline": {"bound": "hbm", "kernel": "gcal_solve (averaging pass + gain iterations)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "bytes_per_step": nbytes, "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def precision_sweep(args):
     """Per-variant dirty-image and degridding error against the FP64 oracle, and throughput.
 
@@ -471,6 +549,8 @@ def main():
         return precision_sweep(args)
     if args.minor_cycle:
         return minor_cycle_bench(args)
+    if args.calibrate:
+        return calibrate_bench(args)
     import torch
     import torch.distributed as dist
 

@@ -319,6 +319,31 @@ awg_status clean_hogbom(float* residual, float* model, int32_t N, const float* p
 /* Number of components the last clean_hogbom on this workspace found (synchronises). */
 awg_status clean_hogbom_components(const void* workspace, int32_t* n_done);
 
+/*
+ * Direction-independent G-Jones calibration (Sec. 5.1): Eq. VAvg, then Eq. CalUpdateDir and
+ * Eq. CalUpdateModel iterated to the exit test of the same section, for every solution interval.
+ * vis (observed, corrected), model (Eq. VMod, e.g. from degrid_visibilities): device c64
+ * [n_rows][n_chan][n_pol]; weight: device f32, same shape (<= 0: flagged).  Rows are time-major:
+ * row = t n_bl + b, baseline b joining antennas ant1[b] and ant2[b] (device int32 [n_bl], values in
+ * [0, n_ant)).  The parallel hands are pols 0 and n_pol - 1 (one product when n_pol = 1).
+ * A solution interval is sol_int integrations x sol_chan channels (the last ones may be shorter);
+ * per interval, hand and baseline X = sum w V conj(M) / sum w |M|^2 with weight sum w |M|^2 (the
+ * weighted average of V / M), then from g = 1: g_i <- (1 - alpha) g_i + alpha sum_{j != i} g_j
+ * X_ij w_ij / sum_{j != i} |g_j|^2 w_ij (X_ji = conj(X_ij)) until max_i |change| < delta or
+ * max_iter iterations; finally every g_i is multiplied by conj(g_ref) / |g_ref| (ref_ant's phase
+ * is zero).  All sums FP64.  gains: device c128 [n_ts][n_fs][n_hands][n_ant] with n_ts =
+ * ceil(n_int / sol_int), n_fs = ceil(n_chan / sol_chan); iterations: device int32
+ * [n_ts][n_fs][n_hands], the iterations run.  workspace: device, gcal_workspace_bytes(...) bytes,
+ * 16-byte aligned.  Asynchronous (two launches).  Errors: INVALID_ARG, UNSUPPORTED (> 128
+ * antennas), CUDA.
+ */
+int64_t gcal_workspace_bytes(int64_t n_rows, int32_t n_chan, int32_t n_pol, int32_t n_bl, int32_t sol_int,
+                             int32_t sol_chan);
+awg_status gcal_solve(const void* vis, const void* model, const float* weight, int64_t n_rows, int32_t n_chan,
+                      int32_t n_pol, int32_t n_bl, const int32_t* ant1, const int32_t* ant2, int32_t n_ant,
+                      int32_t sol_int, int32_t sol_chan, double alpha, double delta, int32_t max_iter, int32_t ref_ant,
+                      void* gains, int32_t* iterations, void* workspace, void* stream);
+
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* awg_last_error(void);
 

@@ -22,9 +22,11 @@ What it computes, and the passages it follows:
   image and analytic point-source visibilities (Eq. ME with a point-source sky).
 * ``clean``  - the Hogbom minor cycle (Sec. 5.2, Eq. ModelUpdate with point components), in
   FP32 because its peak search decides integer positions.
+* ``gcal``   - the direction-independent G-Jones solver (Sec. 5.1: Eq. VAvg, Eq. CalUpdateDir,
+  Eq. CalUpdateModel) in FP64.
 
 Every function states the passage it follows.  Where the paper is silent, the
 reading taken is stated beside the function that takes it.  Parity of the
 synthetic A-term model is unpinned (the paper gives no A-term formula).
 """
-from . import pswf, cf, index, ops, image, clean  # noqa: F401
+from . import pswf, cf, index, ops, image, clean, gcal  # noqa: F401

@@ -20,7 +20,7 @@ EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_s
             "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
             "grid_visibilities_noalloc", "grid_visibilities_plain_fp64", "degrid_visibilities_plain_fp64",
             "awg_fp32_fma_probe", "cf_set_autotune", "cf_set_choose", "clean_hogbom_workspace_bytes",
-            "clean_hogbom", "clean_hogbom_components", "plan_set_row_phase"]
+            "clean_hogbom", "clean_hogbom_components", "plan_set_row_phase", "gcal_workspace_bytes", "gcal_solve"]
 
 
 class AwgError(RuntimeError):
@@ -94,6 +94,9 @@ def load():
             "clean_hogbom": ([vp, vp, i32, vp, i32, i32, ctypes.c_float, ctypes.c_float, vp, vp, vp], st),
             "clean_hogbom_components": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
             "plan_set_row_phase": ([vp, vp, vp, vp, vp], st),
+            "gcal_workspace_bytes": ([i64, i32, i32, i32, i32, i32], ctypes.c_int64),
+            "gcal_solve": ([vp, vp, vp, i64, i32, i32, i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
+                            i32, i32, vp, vp, vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

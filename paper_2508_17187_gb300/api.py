@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import AWG_CF_BF16, AWG_CF_FP32, AWG_GRID_FP64, AWG_GRID_KAHAN, CfParams, check
 
 __all__ = ["CFSet", "Plan", "CleanWorkspace", "cf_set_create", "cf_set_create_from_table", "plan_create",
-           "clean_hogbom", "grid_visibilities",
+           "clean_hogbom", "gcal_solve", "grid_visibilities",
            "degrid_visibilities", "grid_normalize", "AWG_CF_FP32", "AWG_CF_BF16", "AWG_GRID_KAHAN", "AWG_GRID_FP64"]
 
 
@@ -316,3 +316,30 @@ def clean_hogbom(residual: torch.Tensor, model: torch.Tensor, psf: torch.Tensor,
                                    float(threshold), None if win is None else win.ctypes.data_as(ctypes.c_void_p),
                                    _ptr(ws.buf), _stream_ptr(stream)), "clean_hogbom")
     return ws
+
+
+def gcal_solve(vis: torch.Tensor, model: torch.Tensor, weight: torch.Tensor, ant1: torch.Tensor, ant2: torch.Tensor,
+               n_ant: int, sol_int: int, sol_chan: int, alpha: float = 0.5, delta: float = 1e-10,
+               max_iter: int = 200, ref_ant: int = 0, stream=None):
+    """G-Jones solve (see gcal_solve in awgrid.h).  vis / model c64 [R, C, P], weight f32 [R, C, P]
+    on the device, rows time-major over the len(ant1) baselines.  Returns (gains c128
+    [n_ts, n_fs, n_hands, n_ant], iterations int32 [n_ts, n_fs, n_hands]); asynchronous."""
+    R, C, P = vis.shape
+    _need(vis, "vis", torch.complex64, (R, C, P))
+    _need(model, "model", torch.complex64, (R, C, P))
+    _need(weight, "weight", torch.float32, (R, C, P))
+    n_bl = ant1.shape[0]
+    _need(ant1, "ant1", torch.int32, (n_bl,))
+    _need(ant2, "ant2", torch.int32, (n_bl,))
+    if R % n_bl:
+        raise ValueError("the number of rows must be a multiple of the number of baselines")
+    n_int = R // n_bl
+    n_ts, n_fs, n_h = -(-n_int // sol_int), -(-C // sol_chan), (1 if P == 1 else 2)
+    gains = torch.empty((n_ts, n_fs, n_h, n_ant), dtype=torch.complex128, device=vis.device)
+    iters = torch.empty((n_ts, n_fs, n_h), dtype=torch.int32, device=vis.device)
+    nbytes = int(_lib.load().gcal_workspace_bytes(R, C, P, n_bl, sol_int, sol_chan))
+    ws = torch.empty(max(nbytes, 16) // 8 + 2, dtype=torch.float64, device=vis.device)
+    check(_lib.load().gcal_solve(_ptr(vis), _ptr(model), _ptr(weight), R, C, P, n_bl, _ptr(ant1), _ptr(ant2),
+                                 int(n_ant), int(sol_int), int(sol_chan), float(alpha), float(delta), int(max_iter),
+                                 int(ref_ant), _ptr(gains), _ptr(iters), _ptr(ws), _stream_ptr(stream)), "gcal_solve")
+    return gains, iters

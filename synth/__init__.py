@@ -320,3 +320,15 @@ def gaussian_blob_sky(n: int, cell_rad: float, l, m, flux, seed: int = SEED_SKY)
     yy, xx = np.mgrid[0:n, 0:n] - n // 2
     img += 0.5 * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2.0 * (0.02 * n) ** 2))
     return img.astype(np.float32)
+
+
+def baseline_antennas(n_ant: int = 27):
+    """Antenna indices (ant1 < ant2) of the baselines in the order baselines_xyz produces them."""
+    a1, a2 = np.triu_indices(n_ant, k=1)
+    return a1.astype(np.int32), a2.astype(np.int32)
+
+
+def antenna_gains(shape, seed: int = 5) -> np.ndarray:
+    """Seeded complex antenna gains: amplitude U(0.8, 1.2), phase U(-pi, pi); complex128 [shape]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.8, 1.2, shape) * np.exp(1j * rng.uniform(-np.pi, np.pi, shape))

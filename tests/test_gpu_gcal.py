@@ -1,0 +1,101 @@
+"""G-Jones calibration on the GPU (gcal_solve: Eq. VAvg, Eq. CalUpdateDir, Eq. CalUpdateModel)
+against the FP64 oracle on the same FP32 inputs, and end to end with model visibilities from the
+library's degridding (Eq. VMod)."""
+import numpy as np
+import pytest
+
+import synth
+from tests.helpers import library_params, oracle_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _apply_gains(M, g, a1, a2, n_bl, sol_int, sol_chan):
+    R, C, P = M.shape
+    V = np.array(M, dtype=np.complex128, copy=True)
+    hands = [0] if P == 1 else [0, P - 1]
+    for t in range(R // n_bl):
+        for c in range(C):
+            for q, p in enumerate(hands):
+                gg = g[t // sol_int, c // sol_chan, q]
+                V[t * n_bl:(t + 1) * n_bl, c, p] *= gg[a1] * np.conj(gg[a2])
+    return V
+
+
+@pytest.mark.parametrize("P", [1, 4])
+def test_gcal_matches_oracle(P):
+    import paper_2508_17187_gb300 as awg
+    from oracle import gcal
+    rng = np.random.default_rng(20 + P)
+    n_ant, n_int, C, sol_int, sol_chan = 27, 6, 16, 3, 8
+    a1, a2 = synth.baseline_antennas(n_ant)
+    n_bl = len(a1)
+    g = synth.antenna_gains((2, 2, 1 if P == 1 else 2, n_ant), seed=30 + P)
+    M = (rng.standard_normal((n_int * n_bl, C, P)) + 1j * rng.standard_normal((n_int * n_bl, C, P)) + 0.5)
+    V = _apply_gains(M, g, a1, a2, n_bl, sol_int, sol_chan) + 0.1 * (rng.standard_normal(M.shape) + 1j * rng.standard_normal(M.shape))
+    W = rng.uniform(0.5, 2.0, M.shape)
+    W[rng.random(M.shape) < 0.05] = 0.0   # some flagged samples
+    V32, M32, W32 = V.astype(np.complex64), M.astype(np.complex64), W.astype(np.float32)
+    G, its = awg.gcal_solve(torch.as_tensor(V32).cuda(), torch.as_tensor(M32).cuda(), torch.as_tensor(W32).cuda(),
+                            torch.as_tensor(a1).cuda(), torch.as_tensor(a2).cuda(), n_ant, sol_int, sol_chan,
+                            alpha=0.5, delta=1e-12, max_iter=400)
+    Go, itso = gcal.gcal(V32, M32, W32, a1, a2, n_ant, sol_int, sol_chan, 0.5, 1e-12, 400)
+    assert np.abs(G.cpu().numpy() - Go).max() < 1e-9
+    assert np.abs(its.cpu().numpy() - itso).max() <= 1
+    gt = g * np.conj(g[..., :1]) / np.abs(g[..., :1])
+    assert np.abs(Go - gt).max() < 0.05
+
+
+def test_gcal_end_to_end_with_degridded_model():
+    """Eq. VMod from the library's degridding of a model grid, observed data = gains x model +
+    noise; the solve recovers the gains to the noise level and matches the oracle."""
+    import paper_2508_17187_gb300 as awg
+    from oracle import gcal
+    wl = synth.make_workload("wproj", n_int=8, n_chan=8, grid_n=1024, n_wplanes=8, max_support=32)
+    op = oracle_params(wl)
+    cf = awg.cf_set_create(**library_params(op))
+    uvw, freq = torch.as_tensor(wl.uvw_m).cuda(), torch.as_tensor(wl.freq_hz).cuda()
+    plan = awg.plan_create(cf, uvw, freq)
+    N, P = wl.grid_n, wl.n_pol
+    # model grid: F of the point-source sky (pixel-centred), divided by the taper
+    model = torch.zeros((N, N, P), dtype=torch.complex64, device="cuda")
+    ii = torch.as_tensor(np.round(np.asarray(wl.sky_m) / wl.cell_rad).astype(np.int64) + N // 2).clamp(0, N - 1)
+    jj = torch.as_tensor(np.round(np.asarray(wl.sky_l) / wl.cell_rad).astype(np.int64) + N // 2).clamp(0, N - 1)
+    for p in (0, P - 1):
+        model[ii.cuda(), jj.cuda(), p] = torch.as_tensor(wl.sky_flux, dtype=torch.complex64).cuda()
+    awg.grid_normalize(cf, model, None, direction=1)
+    mgrid = torch.fft.fftshift(torch.fft.fft2(torch.fft.ifftshift(model, dim=(0, 1)), dim=(0, 1)), dim=(0, 1)).contiguous()
+    M = torch.empty((wl.n_rows, wl.n_chan, P), dtype=torch.complex64, device="cuda")
+    awg.degrid_visibilities(cf, plan, mgrid, M)
+    Mh = M.cpu().numpy()
+    a1, a2 = synth.baseline_antennas(27)
+    sol_int, sol_chan = 4, 8
+    g = synth.antenna_gains((2, 1, 2, 27), seed=41)
+    rng = np.random.default_rng(42)
+    sigma = 0.01 * np.abs(Mh).mean()
+    V = _apply_gains(Mh, g, a1, a2, len(a1), sol_int, sol_chan) + sigma * (rng.standard_normal(Mh.shape) + 1j * rng.standard_normal(Mh.shape))
+    V32 = V.astype(np.complex64)
+    W32 = np.ones(Mh.shape, dtype=np.float32)
+    G, its = awg.gcal_solve(torch.as_tensor(V32).cuda(), M, torch.as_tensor(W32).cuda(), torch.as_tensor(a1).cuda(),
+                            torch.as_tensor(a2).cuda(), 27, sol_int, sol_chan, alpha=0.5, delta=1e-12, max_iter=400)
+    Go, _ = gcal.gcal(V32, Mh, W32, a1, a2, 27, sol_int, sol_chan, 0.5, 1e-12, 400)
+    assert np.abs(G.cpu().numpy() - Go).max() < 1e-9
+    gt = g * np.conj(g[..., :1]) / np.abs(g[..., :1])
+    assert np.abs(Go - gt).max() < 0.02
+
+
+def test_gcal_argument_errors():
+    import paper_2508_17187_gb300 as awg
+    from paper_2508_17187_gb300._lib import AwgError
+    a1, a2 = synth.baseline_antennas(4)
+    z = torch.zeros((13, 2, 1), dtype=torch.complex64, device="cuda")   # 13 rows: not a multiple of 6
+    w = torch.ones((13, 2, 1), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        awg.gcal_solve(z, z, w, torch.as_tensor(a1).cuda(), torch.as_tensor(a2).cuda(), 4, 1, 1)
+    z = torch.zeros((12, 2, 1), dtype=torch.complex64, device="cuda")
+    w = torch.ones((12, 2, 1), dtype=torch.float32, device="cuda")
+    with pytest.raises(AwgError):
+        awg.gcal_solve(z, z, w, torch.as_tensor(a1).cuda(), torch.as_tensor(a2).cuda(), 4, 1, 1, alpha=0.0)
+    with pytest.raises(AwgError):
+        awg.gcal_solve(z, z, w, torch.as_tensor(a1).cuda(), torch.as_tensor(a2).cuda(), 4, 1, 1, ref_ant=7)

@@ -428,3 +428,90 @@ def test_per_row_phase_undoes_rephasing_to_pointing_centres():
     d0 = oops.degrid(idx0, buf, off, op.oversampling, g0)
     d1 = oops.degrid(idx1, buf, off, op.oversampling, g0)
     assert np.abs(d1 - d0 * rephase).max() <= 1e-10 * np.abs(d0).max()
+
+
+# ------------------------------------------------------------------------- G-Jones calibration
+
+def _gcal_problem(n_ant=27, n_int=4, C=8, P=4, sol_int=2, sol_chan=4, noise=0.0, seed=6):
+    rng = np.random.default_rng(seed)
+    a1, a2 = synth.baseline_antennas(n_ant)
+    n_bl = len(a1)
+    n_ts, n_fs, n_h = -(-n_int // sol_int), -(-C // sol_chan), (1 if P == 1 else 2)
+    g = synth.antenna_gains((n_ts, n_fs, n_h, n_ant), seed=seed)
+    M = (rng.standard_normal((n_int * n_bl, C, P)) + 1j * rng.standard_normal((n_int * n_bl, C, P))) + 0.5
+    V = np.array(M, copy=True)
+    hands = [0] if P == 1 else [0, P - 1]
+    for t in range(n_int):
+        for c in range(C):
+            for q, p in enumerate(hands):
+                gg = g[t // sol_int, c // sol_chan, q]
+                V[t * n_bl:(t + 1) * n_bl, c, p] *= gg[a1] * np.conj(gg[a2])
+    if noise:
+        V += noise * (rng.standard_normal(V.shape) + 1j * rng.standard_normal(V.shape))
+    W = rng.uniform(0.5, 2.0, V.shape)
+    return V, M, W, a1, a2, g
+
+
+def test_gcal_recovers_noise_free_gains():
+    """V_ij = g_i conj(g_j) M_ij exactly: Eq. VAvg gives X_ij = g_i conj(g_j), and the iteration of
+    Eq. CalUpdateDir / Eq. CalUpdateModel converges to the true gains up to the common phase."""
+    from oracle import gcal
+    V, M, W, a1, a2, g = _gcal_problem()
+    G, its = gcal.gcal(V, M, W, a1, a2, 27, 2, 4, alpha=0.5, delta=1e-13, max_iter=500)
+    ref = g * np.conj(g[..., :1]) / np.abs(g[..., :1])
+    assert np.abs(G - ref).max() < 1e-9
+    assert np.all(its < 500)
+
+
+def test_gcal_average_of_constant_ratio_and_weights():
+    from oracle import gcal
+    rng = np.random.default_rng(8)
+    n_bl, n_int, C = 6, 3, 5
+    M = rng.standard_normal((n_int * n_bl, C, 1)) + 1j * rng.standard_normal((n_int * n_bl, C, 1))
+    r = np.exp(1j * rng.uniform(-3, 3, n_bl)) * rng.uniform(0.5, 2, n_bl)
+    V = M * np.tile(r, n_int)[:, None, None]
+    W = rng.uniform(0.1, 1.0, M.shape)
+    W[0, 0, 0] = 0.0   # flagged: skipped
+    X, Wt = gcal.average(V, M, W, n_bl, sol_int=n_int, sol_chan=C)
+    assert np.allclose(X[0, 0, 0], r, rtol=1e-13, atol=0)
+    w = W.reshape(n_int, n_bl, C)
+    assert np.allclose(Wt[0, 0, 0], (w * np.abs(M.reshape(n_int, n_bl, C)) ** 2).sum(axis=(0, 2)), rtol=1e-13)
+
+
+def test_gcal_first_step_closed_form():
+    """From g = 1 with alpha = 1, one step of Eq. CalUpdateDir gives g_i = sum_j X_ij w_ij / sum_j w_ij
+    (X_ij = conj(X_ji)), written out here as a plain loop."""
+    from oracle import gcal
+    rng = np.random.default_rng(9)
+    n_ant = 4
+    a1, a2 = synth.baseline_antennas(n_ant)
+    X = rng.standard_normal(len(a1)) + 1j * rng.standard_normal(len(a1))
+    Wt = rng.uniform(0.5, 2.0, len(a1))
+    g, it = gcal.solve_gains(X, Wt, a1, a2, n_ant, alpha=1.0, delta=0.0, max_iter=1, ref_ant=0)
+    want = []
+    for i in range(n_ant):
+        num = den = 0
+        for b in range(len(a1)):
+            if a1[b] == i:
+                num += X[b] * Wt[b]
+                den += Wt[b]
+            elif a2[b] == i:
+                num += np.conj(X[b]) * Wt[b]
+                den += Wt[b]
+        want.append(num / den)
+    want = np.array(want)
+    want = want * np.conj(want[0]) / abs(want[0])
+    assert it == 1 and np.allclose(g, want, rtol=1e-14, atol=1e-14)
+
+
+def test_gcal_lowers_chi2_with_noise():
+    """Eq. XChisq, sum w |X_ij - g_i conj(g_j)|^2, falls from the starting gains to the solution."""
+    from oracle import gcal
+    V, M, W, a1, a2, g = _gcal_problem(noise=0.3, seed=10)
+    X, Wt = gcal.average(V, M, W, len(a1), 2, 4)
+    for idx in np.ndindex(*X.shape[:3]):
+        gs, _ = gcal.solve_gains(X[idx], Wt[idx], a1, a2, 27, 0.5, 1e-12, 500)
+        chi = lambda gg: float((Wt[idx] * np.abs(X[idx] - gg[a1] * np.conj(gg[a2])) ** 2).sum())
+        assert chi(gs) < 0.1 * chi(np.ones(27))
+        gt = g[idx] * np.conj(g[idx][0]) / abs(g[idx][0])
+        assert np.abs(gs - gt).max() < 0.05
