@@ -467,12 +467,14 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
   float2* beta = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST>::al_off);
-  __shared__ float s_red[2][NW][32];
+  // per-warp butterfly results of every batch of the chunk; combined once per chunk
+  constexpr int NB = (ST + B - 1) / B;          // batches per chunk
+  constexpr int NBW = (NB + NW - 1) / NW;       // batches combined by one warp
+  __shared__ float s_red[NB][NW][32];
   __shared__ int s_item;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int begin = a.class_range[cls], end = a.class_range[cls + 1];
-  int buf = 0;
 
   for (;;) {
     __syncthreads();
@@ -538,6 +540,10 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
       cp_async_commit();
       const int nst = nst_of(c);
+      int cap_src[NBW];
+      float2 cap_ph[NBW];
+#pragma unroll
+      for (int q = 0; q < NBW; ++q) cap_src[q] = -1;
       for (int j0 = 0; j0 < nst; j0 += B) {
         float vals[32];
 #pragma unroll
@@ -611,25 +617,47 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
             vals[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
           }
         }
-        s_red[buf][wid][lane] = vals[0];
-        __syncthreads();
-        if (wid == 0) {
-          float v = 0.f;
+        const int bi = j0 / B;
+        s_red[bi][wid][lane] = vals[0];
+        if (bi % NW == wid) {   // this warp combines the batch: keep its output rows and phasors
+          const int j = j0 + lane / (2 * P);
+          const int src = j < nst ? A.src()[j] : -1;
+          const float2 ph = j < nst ? A.ph()[j] : make_float2(1.f, 0.f);
+          if constexpr (NBW == 1) {
+            cap_src[0] = src;
+            cap_ph[0] = ph;
+          } else {
 #pragma unroll
-          for (int w = 0; w < NW; ++w) v += s_red[buf][w][lane];
-          const int b = lane / (2 * P), comp = lane - b * 2 * P;
-          const int j = j0 + b;
-          const float partner = __shfl_xor_sync(0xffffffffu, v, 1);
-          if (j < nst) {
-            const float2 ph = A.ph()[j];
-            const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
-            a.vis_out[(size_t)A.src()[j] * 2 * P + comp] = out;
+            for (int q = 0; q < NBW; ++q)   // static indices keep the arrays in registers
+              if (q == bi / NW) {
+                cap_src[q] = src;
+                cap_ph[q] = ph;
+              }
           }
         }
-        buf ^= 1;
       }
       cp_async_wait_all();
       __syncthreads();
+      {
+        // warp w adds up the warps' partials of batches w, w + NW, ... and writes whole samples
+        const int nbat = (nst + B - 1) / B;
+        const int comp = lane - (lane / (2 * P)) * 2 * P;
+#pragma unroll
+        for (int q = 0; q < NBW; ++q) {
+          const int bi = wid + q * NW;
+          if (bi < nbat) {
+            float v = 0.f;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v += s_red[bi][w][lane];
+            const float partner = __shfl_xor_sync(0xffffffffu, v, 1);
+            if (cap_src[q] >= 0) {
+              const float2 ph = cap_ph[q];
+              const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
+              a.vis_out[(size_t)cap_src[q] * 2 * P + comp] = out;
+            }
+          }
+        }
+      }
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
       if (c + 1 < nch) form_beta<SMAX, TILE, P, ST, NT>(Bs, beta, nst_of(c + 1), S);
       __syncthreads();
