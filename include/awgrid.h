@@ -94,6 +94,17 @@ typedef struct {
                                        fy_k[oy][ty] fx_k[ox][tx] when every CF of the set fits one
                                        to 1e-6 of its peak (PS and W-projection CFs with r = 1,
                                        A-term CFs with r of about 4); 0: always full tables */
+  /* Full-polarisation A-terms (the sparse Mueller matrix of CFs, Sec. 2 and Sec. 6): with use_a and
+     use_pol, each antenna's Jones matrix is J = [[A_R, d A_R], [d A_L, A_L]] with A_R, A_L the
+     Airy voltage patterns of the R and L feeds squinted by +-squint_rad along the rotated l axis
+     and d = leakage_re + i leakage_im; Mueller element (p, q), pols ordered RR, RL, LR, LL
+     (p = (a, b), q = (c, d)), has the image-plane screen J_ac conj(J_bd) (times PS and W).  An
+     element is kept when |d|^n >= mueller_threshold, n the number of leakage factors in it (the
+     diagonal always).  Needs separable storage and 4 pols in gridding / degridding. */
+  int use_pol;
+  double squint_rad;
+  double leakage_re, leakage_im;
+  double mueller_threshold;
 } awg_cf_params;
 
 /*
@@ -152,6 +163,14 @@ awg_status cf_set_autotune(awg_cf_set cf, const double* uvw_m, int64_t n_rows, c
  * W-projection schedule by hand (what cf_set_autotune does by timing); plans created before the
  * call are invalid afterwards.  Errors: INVALID_ARG (no configurations for that support). */
 awg_status cf_set_choose(awg_cf_set cf, int32_t support, int32_t config);
+
+/* Mueller elements of a full-polarisation CF set (use_pol): *n_elem (0 otherwise) and, when not
+ * NULL, host int32 [16] arrays of each element's output pol p and input pol q (0..3 = RR, RL, LR,
+ * LL).  CF index = element * (n_pa_bins n_subbands n_signed) + the per-sample CF index.  Gridding
+ * with such a set adds conj(CF_pq) w_p V_p into grid pol q (the diagonal elements add the weights
+ * to sumwt[q]); degridding sets vis pol p to the sum over its elements of CF_pq applied to grid
+ * pol q.  Both need n_pol = 4. */
+awg_status cf_set_mueller(awg_cf_set cf, int32_t* n_elem, int32_t* elem_p, int32_t* elem_q);
 
 /* Host copy of the support of every CF: supports_out host [n_cf]. */
 awg_status cf_set_get_supports(awg_cf_set cf, int32_t* supports_out);

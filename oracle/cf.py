@@ -53,14 +53,23 @@ class CFParams:
     max_support: int = 7
     dish_diameter_m: float = 25.0
     ellipticity: float = 0.05
+    # full polarisation (the sparse Mueller matrix of CFs): feed squint, leakage, element cut
+    use_pol: bool = False
+    squint_rad: float = 0.0
+    leakage: complex = 0.0
+    mueller_threshold: float = 0.01
 
     @property
     def n_signed(self) -> int:
         return 2 * self.n_wplanes - 1 if self.use_w else 1
 
     @property
-    def n_cf(self) -> int:
+    def n_base(self) -> int:
         return self.n_pa_bins * self.n_subbands * self.n_signed
+
+    @property
+    def n_cf(self) -> int:
+        return self.n_base * (len(mueller_elements(self)) if self.use_pol else 1)
 
     def cf_index(self, pa: int, sb: int, ks: int) -> int:
         return (pa * self.n_subbands + sb) * self.n_signed + ks
@@ -85,10 +94,36 @@ def support_of_plane(p: CFParams, ks: int) -> int:
 
 def supports(p: CFParams) -> np.ndarray:
     out = np.zeros(p.n_cf, dtype=np.int32)
-    for pa in range(p.n_pa_bins):
-        for sb in range(p.n_subbands):
-            for ks in range(p.n_signed):
-                out[p.cf_index(pa, sb, ks)] = support_of_plane(p, ks)
+    for e in range(p.n_cf // p.n_base):
+        for pa in range(p.n_pa_bins):
+            for sb in range(p.n_subbands):
+                for ks in range(p.n_signed):
+                    out[e * p.n_base + p.cf_index(pa, sb, ks)] = support_of_plane(p, ks)
+    return out
+
+
+# Polarisation products in the order RR, RL, LR, LL: product k correlates feed k // 2 of the first
+# antenna with feed k % 2 of the second (R = 0, L = 1).
+def mueller_elements(p: CFParams):
+    """Kept Mueller elements (p, q), row-major: the element of output product p = (a, b) and sky
+    product q = (c, d) carries |d|^n with n = [a != c] + [b != d] leakage factors; it is kept when
+    that is at least the threshold (reading: the 'terms significant compared to the telescope
+    sensitivity' of the sparse Mueller matrix of CFs, Sec. 6)."""
+    dmag = abs(complex(p.leakage))
+    out = []
+    for pp in range(4):
+        for qq in range(4):
+            n = (pp // 2 != qq // 2) + (pp % 2 != qq % 2)
+            if n == 0 or dmag ** n >= p.mueller_threshold:
+                out.append((pp, qq))
+    return out
+
+
+def airy_voltage(rho_rad, freq_hz: float, dish_m: float) -> np.ndarray:
+    x = math.pi * dish_m * np.asarray(rho_rad) * freq_hz / C_LIGHT
+    out = np.ones_like(x)
+    nz = x != 0
+    out[nz] = 2.0 * j1(x[nz]) / x[nz]
     return out
 
 
@@ -107,8 +142,12 @@ def airy_power(rho_rad, freq_hz: float, dish_m: float) -> np.ndarray:
     return out
 
 
-def screen(p: CFParams, pa: int, sb: int, ks: int, M: int) -> np.ndarray:
-    """Image-plane product of the enabled terms, complex128 [M(y), M(x)]."""
+def screen(p: CFParams, pa: int, sb: int, ks: int, M: int, elem=None) -> np.ndarray:
+    """Image-plane product of the enabled terms, complex128 [M(y), M(x)].  With a Mueller element
+    elem = (p, q) the A factor is J_ac conj(J_bd) for p = (a, b), q = (c, d), from the Jones matrix
+    J = [[A_R, d A_R], [d A_L, A_L]] of voltage patterns squinted by -+squint along the rotated l
+    axis (the outer product of the two antennas' Jones matrices, Sec. 2, evaluated in the image
+    plane; reading: a synthetic feed model, the paper gives none)."""
     i = np.arange(M, dtype=np.float64)
     x = (i - M / 2) * p.grid_n / M                  # image pixels from the field centre
     lm = x * p.cell_rad                             # direction cosines
@@ -127,8 +166,20 @@ def screen(p: CFParams, pa: int, sb: int, ks: int, M: int) -> np.ndarray:
         lr = L * math.cos(chi) + Mm * math.sin(chi)
         mr = -L * math.sin(chi) + Mm * math.cos(chi)
         eps = p.ellipticity
-        rho = np.sqrt((lr / (1.0 + eps)) ** 2 + (mr / (1.0 - eps)) ** 2)
-        s = s * airy_power(rho, float(p.subband_freq_hz[sb]), p.dish_diameter_m)
+        nu = float(p.subband_freq_hz[sb])
+        if elem is None:
+            rho = np.sqrt((lr / (1.0 + eps)) ** 2 + (mr / (1.0 - eps)) ** 2)
+            s = s * airy_power(rho, nu, p.dish_diameter_m)
+        else:
+            rho_r = np.sqrt(((lr - p.squint_rad) / (1.0 + eps)) ** 2 + (mr / (1.0 - eps)) ** 2)
+            rho_l = np.sqrt(((lr + p.squint_rad) / (1.0 + eps)) ** 2 + (mr / (1.0 - eps)) ** 2)
+            ar = airy_voltage(rho_r, nu, p.dish_diameter_m)
+            al = airy_voltage(rho_l, nu, p.dish_diameter_m)
+            d = complex(p.leakage)
+            J = [[ar + 0j, d * ar], [d * al, al + 0j]]
+            pp, qq = elem
+            a, b, c, e = pp // 2, pp % 2, qq // 2, qq % 2
+            s = s * (J[a][c] * np.conj(J[b][e]))
     return s
 
 
@@ -139,12 +190,12 @@ def tap_positions(S: int, OS: int) -> np.ndarray:
     return S / 2.0 - t - o / OS
 
 
-def cf_table(p: CFParams, pa: int, sb: int, ks: int) -> np.ndarray:
+def cf_table(p: CFParams, pa: int, sb: int, ks: int, elem=None) -> np.ndarray:
     """complex128 [OS+1, OS+1, S, S] table of one CF (offset-major)."""
     S = support_of_plane(p, ks)
     OS = p.oversampling
     M = screen_size(S)
-    s = screen(p, pa, sb, ks, M)
+    s = screen(p, pa, sb, ks, M, elem)
     d = tap_positions(S, OS).reshape(-1)                     # Q = (OS+1) S
     i = np.arange(M, dtype=np.float64) - M / 2
     E = np.exp(-2j * math.pi * np.outer(d, i) / M) / M       # [Q, M]
@@ -153,14 +204,17 @@ def cf_table(p: CFParams, pa: int, sb: int, ks: int) -> np.ndarray:
 
 
 def cf_set(p: CFParams, which: Optional[Sequence[int]] = None):
-    """All (or the listed) CF tables: dict cf_index -> table."""
+    """All (or the listed) CF tables: dict cf_index -> table.  A full-polarisation set holds one
+    block of n_base CFs per kept Mueller element, element e at e * n_base + cf_index."""
     out = {}
-    for pa in range(p.n_pa_bins):
-        for sb in range(p.n_subbands):
-            for ks in range(p.n_signed):
-                ci = p.cf_index(pa, sb, ks)
-                if which is None or ci in which:
-                    out[ci] = cf_table(p, pa, sb, ks)
+    elems = mueller_elements(p) if p.use_pol else [None]
+    for e, el in enumerate(elems):
+        for pa in range(p.n_pa_bins):
+            for sb in range(p.n_subbands):
+                for ks in range(p.n_signed):
+                    ci = e * p.n_base + p.cf_index(pa, sb, ks)
+                    if which is None or ci in which:
+                        out[ci] = cf_table(p, pa, sb, ks, el)
     return out
 
 

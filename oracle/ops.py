@@ -9,6 +9,7 @@ D follows Eq. ME-MOD-GRIDDED: V = sum over the same taps of c * grid.  The loops
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 import subprocess
 import sysconfig
@@ -169,4 +170,32 @@ def degrid_numpy(idx: SampleIndex, cf_buf, cf_off, OS: int, grid_c):
         if idx.phasor is not None:
             v = v * np.conj(idx.phasor[s])
         out[s] = v
+    return out
+
+
+def grid_mueller(p, idx: SampleIndex, cf_buf, cf_off, OS: int, N: int, vis, weight, nthreads=None):
+    """Full-polarisation G with the sparse Mueller matrix of CFs (Sec. 2, Sec. 6): grid pol q
+    receives conj(CF_pq) w_p V_p for every kept element (p, q); sum of weights per pol from the
+    diagonal elements.  vis, weight [n, 4]; returns (grid complex128 [N, N, 4], sumwt [4])."""
+    from .cf import mueller_elements
+    vis = np.asarray(vis).reshape(-1, 4)
+    weight = np.asarray(weight, dtype=np.float64).reshape(-1, 4)
+    g = np.zeros((N, N, 4), dtype=np.complex128)
+    sw = np.zeros(4)
+    for e, (pp, qq) in enumerate(mueller_elements(p)):
+        idx_e = dataclasses.replace(idx, cf=idx.cf + e * p.n_base)
+        ge, swe = grid(idx_e, cf_buf, cf_off, OS, N, vis[:, pp:pp + 1], weight[:, pp:pp + 1], nthreads)
+        g[..., qq] += ge[..., 0]
+        if pp == qq:
+            sw[qq] += swe[0]
+    return g, sw
+
+
+def degrid_mueller(p, idx: SampleIndex, cf_buf, cf_off, OS: int, grid_c, nthreads=None):
+    """Full-polarisation D: vis pol p = sum over kept elements (p, q) of CF_pq applied to grid pol q."""
+    from .cf import mueller_elements
+    out = np.zeros((idx.valid.shape[0], 4), dtype=np.complex128)
+    for e, (pp, qq) in enumerate(mueller_elements(p)):
+        idx_e = dataclasses.replace(idx, cf=idx.cf + e * p.n_base)
+        out[:, pp] += degrid(idx_e, cf_buf, cf_off, OS, grid_c[..., qq:qq + 1], nthreads)[:, 0]
     return out

@@ -20,7 +20,8 @@ EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_s
             "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
             "grid_visibilities_noalloc", "grid_visibilities_plain_fp64", "degrid_visibilities_plain_fp64",
             "awg_fp32_fma_probe", "cf_set_autotune", "cf_set_choose", "clean_hogbom_workspace_bytes",
-            "clean_hogbom", "clean_hogbom_components", "plan_set_row_phase", "gcal_workspace_bytes", "gcal_solve"]
+            "clean_hogbom", "clean_hogbom_components", "plan_set_row_phase", "gcal_workspace_bytes", "gcal_solve",
+            "cf_set_mueller"]
 
 
 class AwgError(RuntimeError):
@@ -49,6 +50,11 @@ class CfParams(ctypes.Structure):
         ("ellipticity", ctypes.c_double),
         ("cf_dtype", ctypes.c_int),
         ("separable", ctypes.c_int),
+        ("use_pol", ctypes.c_int),
+        ("squint_rad", ctypes.c_double),
+        ("leakage_re", ctypes.c_double),
+        ("leakage_im", ctypes.c_double),
+        ("mueller_threshold", ctypes.c_double),
     ]
 
 
@@ -95,6 +101,7 @@ def load():
             "clean_hogbom_components": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
             "plan_set_row_phase": ([vp, vp, vp, vp, vp], st),
             "gcal_workspace_bytes": ([i64, i32, i32, i32, i32, i32], ctypes.c_int64),
+            "cf_set_mueller": ([vp, vp, vp, vp], st),
             "gcal_solve": ([vp, vp, vp, i64, i32, i32, i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
                             i32, i32, vp, vp, vp, vp], st),
         }

@@ -85,6 +85,15 @@ class CFSet:
         picked = {S: int(choice[S]) for S in range(65) if choice[S] >= 0}
         return picked, {S: (float(ms[0, S]), float(ms[1, S])) for S in picked}
 
+    def mueller(self):
+        """[(p, q), ...] Mueller elements of a full-polarisation set (empty otherwise)."""
+        n = ctypes.c_int32()
+        ep = np.zeros(16, dtype=np.int32)
+        eq = np.zeros(16, dtype=np.int32)
+        check(_lib.load().cf_set_mueller(self.handle, ctypes.byref(n), ep.ctypes.data_as(ctypes.c_void_p),
+                                         eq.ctypes.data_as(ctypes.c_void_p)), "cf_set_mueller")
+        return [(int(ep[i]), int(eq[i])) for i in range(n.value)]
+
     def choose(self, support: int, config: int):
         """Select kernel configuration 0 or 1 for one support by hand (see cf_set_choose)."""
         check(_lib.load().cf_set_choose(self.handle, int(support), int(config)), "cf_set_choose")
@@ -117,7 +126,7 @@ class CFSet:
 def _params(grid_n, cell_rad, oversampling=20, ps_support=7, use_ps=True, use_w=False, n_wplanes=1,
             w_max_lambda=0.0, use_a=False, n_pa_bins=1, pa_bin_centers_rad=None, n_subbands=1,
             subband_freq_hz=None, max_support=7, dish_diameter_m=25.0, ellipticity=0.05, cf_dtype=AWG_CF_FP32,
-            separable=True):
+            separable=True, use_pol=False, squint_rad=0.0, leakage=0.0, mueller_threshold=0.01):
     p = CfParams()
     p.grid_n = int(grid_n)
     p.cell_rad = float(cell_rad)
@@ -135,6 +144,11 @@ def _params(grid_n, cell_rad, oversampling=20, ps_support=7, use_ps=True, use_w=
     p.ellipticity = float(ellipticity)
     p.cf_dtype = int(cf_dtype)
     p.separable = int(bool(separable))
+    p.use_pol = int(bool(use_pol))
+    p.squint_rad = float(squint_rad)
+    p.leakage_re = float(complex(leakage).real)
+    p.leakage_im = float(complex(leakage).imag)
+    p.mueller_threshold = float(mueller_threshold)
     keep = []
     if pa_bin_centers_rad is not None:
         a = np.ascontiguousarray(pa_bin_centers_rad, dtype=np.float64)

@@ -113,6 +113,9 @@ struct CfSetImpl {
   SlotTable slots{};
   // Separable storage: CF = fy[oy][ty] * fx[ox][tx]; per CF, fx [OS+1][S] then fy [OS+1][S] c64.
   int separable = 0;
+  // Mueller elements (use_pol): CF index = element * n_base + (pa n_sb + sb) n_signed + ks
+  int n_elem = 1, n_base = 0;
+  int elem_p[16] = {}, elem_q[16] = {};   // output pol p and input pol q of each element
   int8_t cand[kMaxSupport + 1] = {};   // exact-kernel candidate per support (cf_set_autotune)
   int slots_version = 0;               // bumped whenever the slot table (tiles) changes
   int rank = 1;                      // outer-product terms per CF when separable
@@ -185,7 +188,10 @@ int factor_low_rank(const std::vector<double>& tab, int S, int OS, double tol, i
 // separable 2-D transform, so screen terms map to CF terms); the residual is checked on the CF's
 // offset slices (0, OS/2, OS)^2.  Returns the term count, or 0 when r_max terms do not reach tol.
 int build_cf_factors(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa, int sb,
-                     int ks, double tol, int r_max, std::vector<double>& fx, std::vector<double>& fy);
+                     int ks, int elem_p, int elem_q, double tol, int r_max, std::vector<double>& fx,
+                     std::vector<double>& fy);
+// The kept Mueller elements of params (use_pol): pairs (p, q), row-major; returns their number.
+int mueller_elements(const awg_cf_params& p, int* elem_p, int* elem_q);
 constexpr int kMaxRank = 6;        // outer-product terms per CF at most (separable storage)
 constexpr double kSepTol = 1e-6;   // largest accepted residual of the fit, relative to the peak
 

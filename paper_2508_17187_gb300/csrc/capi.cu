@@ -75,6 +75,14 @@ static awg_status check_params(const awg_cf_params* p, bool from_table) {
     if (!(p->dish_diameter_m > 0.0) || !(std::fabs(p->ellipticity) < 0.5))
       return set_error(AWG_ERR_INVALID_ARG, "dish_diameter_m must be > 0 and |ellipticity| < 0.5");
   }
+  if (p->use_pol) {
+    if (!p->use_a) return set_error(AWG_ERR_INVALID_ARG, "use_pol needs use_a");
+    if (!p->separable || p->cf_dtype != AWG_CF_FP32)
+      return set_error(AWG_ERR_UNSUPPORTED, "full-polarisation CF sets need separable FP32 storage");
+    if (!(std::fabs(p->squint_rad) < 0.1) || !(std::hypot(p->leakage_re, p->leakage_im) < 1.0) ||
+        !(p->mueller_threshold >= 0.0))
+      return set_error(AWG_ERR_INVALID_ARG, "need |squint_rad| < 0.1, |leakage| < 1 and mueller_threshold >= 0");
+  }
   return AWG_OK;
 }
 
@@ -228,28 +236,34 @@ static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<
 static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
   const awg_cf_params& p = cf->p;
   cf->n_signed = p.use_w ? 2 * p.n_wplanes - 1 : 1;
-  const int n_w = p.use_w ? p.n_wplanes : 1;
+  // Without full polarisation the non-W part of every screen is real, so a negative-w plane is the
+  // conjugate point reflection of the positive one and only n_w planes are fitted; Mueller elements
+  // with a complex leakage are not, and every signed plane is fitted.
+  const bool mirror = !p.use_pol;
+  const int n_w = !p.use_w ? 1 : mirror ? p.n_wplanes : 2 * p.n_wplanes - 1;
   const int n_pos = p.n_pa_bins * p.n_subbands * n_w;
   const int OS = p.oversampling;
   std::vector<std::vector<double>> fx(cf->n_cf), fy(cf->n_cf);
   int failed = 0;
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int j = 0; j < n_pos; ++j) {
+  for (int je = 0; je < n_pos * cf->n_elem; ++je) {
     if (failed) continue;
+    const int e = je / n_pos, j = je - e * n_pos;
     const int k = j % n_w, pasb = j / n_w;
     const int pa = pasb / p.n_subbands, sb = pasb % p.n_subbands;
-    const int ks = p.use_w ? p.n_wplanes - 1 + k : 0;
+    const int ks = !p.use_w ? 0 : mirror ? p.n_wplanes - 1 + k : k;
     const int S = support_of_plane(p, ks);
-    const int ci = pasb * cf->n_signed + ks;
-    if (build_cf_factors(p, cf->pa_centers.data(), cf->sb_freqs.data(), pa, sb, ks, kSepTol, kMaxRank, fx[ci],
-                         fy[ci]) == 0) {
+    const int ci = e * cf->n_base + pasb * cf->n_signed + ks;
+    const int ep = p.use_pol ? cf->elem_p[e] : -1, eq = p.use_pol ? cf->elem_q[e] : -1;
+    if (build_cf_factors(p, cf->pa_centers.data(), cf->sb_freqs.data(), pa, sb, ks, ep, eq, kSepTol, kMaxRank,
+                         fx[ci], fy[ci]) == 0) {
 #pragma omp atomic write
       failed = 1;
       continue;
     }
-    if (p.use_w && k > 0) {
+    if (mirror && p.use_w && k > 0) {
       // table(-w) = conj(table(+w)) point-reflected: each term's factors reversed and conjugated
-      const int cn = pasb * cf->n_signed + (p.n_wplanes - 1 - k);
+      const int cn = e * cf->n_base + pasb * cf->n_signed + (p.n_wplanes - 1 - k);
       const size_t q = (size_t)(OS + 1) * S;
       const size_t terms = fx[ci].size() / (2 * q);
       fx[cn].resize(fx[ci].size());
@@ -295,19 +309,25 @@ awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* 
   cf->p.subband_freq_hz = nullptr;
   cudaGetDevice(&cf->device);
   const int n_signed = params->use_w ? 2 * params->n_wplanes - 1 : 1;
-  cf->n_cf = params->n_pa_bins * params->n_subbands * n_signed;
+  cf->n_base = params->n_pa_bins * params->n_subbands * n_signed;
+  cf->n_elem = params->use_pol ? mueller_elements(cf->p, cf->elem_p, cf->elem_q) : 1;
+  cf->n_cf = cf->n_elem * cf->n_base;
   cf->supports.resize(cf->n_cf);
-  for (int pa = 0; pa < params->n_pa_bins; ++pa)
-    for (int sb = 0; sb < params->n_subbands; ++sb)
-      for (int ks = 0; ks < n_signed; ++ks)
-        cf->supports[(pa * params->n_subbands + sb) * n_signed + ks] = support_of_plane(cf->p, ks);
+  for (int e = 0; e < cf->n_elem; ++e)
+    for (int pa = 0; pa < params->n_pa_bins; ++pa)
+      for (int sb = 0; sb < params->n_subbands; ++sb)
+        for (int ks = 0; ks < n_signed; ++ks)
+          cf->supports[e * cf->n_base + (pa * params->n_subbands + sb) * n_signed + ks] = support_of_plane(cf->p, ks);
   if (params->separable && params->cf_dtype == AWG_CF_FP32) {
     s = build_separable(cf, st);
     if (s == AWG_OK) {
       *out = (awg_cf_set)cf;
       return AWG_OK;
     }
-    if (s != AWG_ERR_UNSUPPORTED) { free_cf(cf); return s; }
+    if (s != AWG_ERR_UNSUPPORTED || params->use_pol) {
+      free_cf(cf);
+      return s == AWG_ERR_UNSUPPORTED ? set_error(s, "a Mueller element CF needs more than 6 terms") : s;
+    }
     cf->separable = 0;   // some CF is not an outer product: keep full tables
   }
   s = alloc_cf(cf, st);
@@ -379,6 +399,7 @@ awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* 
   *out = nullptr;
   awg_status s = check_params(params, true);
   if (s != AWG_OK) return s;
+  if (params->use_pol) return set_error(AWG_ERR_UNSUPPORTED, "caller tables cannot form a Mueller set");
   if (!supports || !table) return set_error(AWG_ERR_INVALID_ARG, "supports and table must not be NULL");
   cudaStream_t st = (cudaStream_t)stream;
   CfSetImpl* cf = new (std::nothrow) CfSetImpl();
@@ -391,6 +412,7 @@ awg_status cf_set_create_from_table(const awg_cf_params* params, const int32_t* 
   cudaGetDevice(&cf->device);
   const int n_signed = params->use_w ? 2 * params->n_wplanes - 1 : 1;
   cf->n_cf = params->n_pa_bins * params->n_subbands * n_signed;
+  cf->n_base = cf->n_cf;
   cf->supports.assign(supports, supports + cf->n_cf);
   for (int v : cf->supports) {
     if (v < 1) { delete cf; return set_error(AWG_ERR_INVALID_ARG, "supports must be >= 1"); }
@@ -479,6 +501,17 @@ awg_status cf_set_choose(awg_cf_set h, int32_t support, int32_t config) {
   if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0 or 1");
   cf->cand[support] = (int8_t)config;
   fill_slots(cf);
+  return AWG_OK;
+}
+
+awg_status cf_set_mueller(awg_cf_set h, int32_t* n_elem, int32_t* elem_p, int32_t* elem_q) {
+  if (!h || !n_elem) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  *n_elem = cf->p.use_pol ? cf->n_elem : 0;
+  for (int e = 0; e < *n_elem; ++e) {
+    if (elem_p) elem_p[e] = cf->elem_p[e];
+    if (elem_q) elem_q[e] = cf->elem_q[e];
+  }
   return AWG_OK;
 }
 

@@ -159,9 +159,38 @@ void taper_image(const awg_cf_params& p, std::vector<double>& out) {
   for (int j = 0; j < N; ++j) out[j] = taper_at(ps, 2.0 * (double)(j - N / 2) / N, norm);
 }
 
-// Image-plane screen s[j][i] = T(x_i) T(y_j) A W at x_i = (i - M/2) N / M pixels (row j: y).
+// Airy voltage pattern 2 J1(z) / z of the dish at frequency nu, for the direction (lr, mr) in the
+// frame rotated by the parallactic angle, with the elliptical distortion of the A-term.
+static double airy_voltage(const awg_cf_params& p, double lr, double mr, double nu) {
+  const double a = lr / (1.0 + p.ellipticity), b = mr / (1.0 - p.ellipticity);
+  const double z = kPi * p.dish_diameter_m * std::sqrt(a * a + b * b) * nu / kCLight;
+  return z != 0.0 ? 2.0 * std::cyl_bessel_j(1.0, z) / z : 1.0;
+}
+
+int mueller_elements(const awg_cf_params& p, int* elem_p, int* elem_q) {
+  // pol index -> (a, b): RR = (0, 0), RL = (0, 1), LR = (1, 0), LL = (1, 1); R = 0, L = 1
+  const double d = std::hypot(p.leakage_re, p.leakage_im);
+  int n = 0;
+  for (int pp = 0; pp < 4; ++pp)
+    for (int qq = 0; qq < 4; ++qq) {
+      const int a = pp >> 1, b = pp & 1, c = qq >> 1, e = qq & 1;
+      const int n_leak = (a != c) + (b != e);
+      const double mag = n_leak == 0 ? 1.0 : std::pow(d, n_leak);
+      if (mag >= p.mueller_threshold || n_leak == 0) {
+        elem_p[n] = pp;
+        elem_q[n] = qq;
+        ++n;
+      }
+    }
+  return n;
+}
+
+// Image-plane screen s[j][i] = T(x_i) T(y_j) A W at x_i = (i - M/2) N / M pixels (row j: y).  For a
+// Mueller element (elem_p, elem_q >= 0) the A factor is J_ac conj(J_bd) with (a, b) the feeds of
+// pol elem_p and (c, d) those of elem_q, J = [[A_R, d A_R], [d A_L, A_L]] (A_R, A_L squinted by
+// +-squint_rad); otherwise the pol-shared Airy power pattern.
 static void cf_screen(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa, int sb,
-                      int ks, int M, std::vector<cd>& scr) {
+                      int ks, int elem_p, int elem_q, int M, std::vector<cd>& scr) {
   const int N = p.grid_n;
   std::vector<double> t1(M, 1.0);
   if (p.use_ps) {
@@ -186,14 +215,18 @@ static void cf_screen(const awg_cf_params& p, const double* pa_centers, const do
       }
       if (p.use_a) {
         const double lr = l * cchi + m * schi, mr = -l * schi + m * cchi;
-        const double a = lr / (1.0 + p.ellipticity), b = mr / (1.0 - p.ellipticity);
-        const double z = kPi * p.dish_diameter_m * std::sqrt(a * a + b * b) * nu / kCLight;
-        double amp = 1.0;
-        if (z != 0.0) {
-          const double j1 = std::cyl_bessel_j(1.0, z);
-          amp = (2.0 * j1 / z) * (2.0 * j1 / z);
+        if (elem_p >= 0) {
+          const cd dl(p.leakage_re, p.leakage_im);
+          const double vr = airy_voltage(p, lr - p.squint_rad, mr, nu);
+          const double vl = airy_voltage(p, lr + p.squint_rad, mr, nu);
+          // J[x][y]: row x = output feed, column y = sky feed
+          const cd J[2][2] = {{cd(vr, 0.0), dl * vr}, {dl * vl, cd(vl, 0.0)}};
+          const int a = elem_p >> 1, b = elem_p & 1, c = elem_q >> 1, e = elem_q & 1;
+          v *= J[a][c] * std::conj(J[b][e]);
+        } else {
+          const double amp = airy_voltage(p, lr, mr, nu);
+          v *= amp * amp;
         }
-        v *= amp;
       }
       scr[(size_t)j * M + i] = v;
     }
@@ -226,7 +259,7 @@ void build_cf_table(const awg_cf_params& p, const double* pa_centers, const doub
   const int M = screen_size(S);
   const int OS = p.oversampling;
   std::vector<cd> scr, tw;
-  cf_screen(p, pa_centers, sb_freqs, pa, sb, ks, M, scr);
+  cf_screen(p, pa_centers, sb_freqs, pa, sb, ks, -1, -1, M, scr);
   axis_twiddles(M, S, OS, tw);
   // Pass over rows (u): X[ox][j][tx].
   const int Q = (OS + 1) * S;
@@ -298,7 +331,8 @@ static void leading_term(std::vector<cd>& E, int rows, int cols, std::vector<cd>
 }
 
 int build_cf_factors(const awg_cf_params& p, const double* pa_centers, const double* sb_freqs, int pa, int sb,
-                     int ks, double tol, int r_max, std::vector<double>& fx, std::vector<double>& fy) {
+                     int ks, int elem_p, int elem_q, double tol, int r_max, std::vector<double>& fx,
+                     std::vector<double>& fy) {
   // The CF is the 2-D transform of the screen, separable as C = Fy scr Fx^T with one axis
   // transform per axis; a term g f^T of the screen therefore gives the CF term (Fy g)(Fx f)^T.
   // Terms are taken greedily from the screen's residual; after each term the CF residual is
@@ -310,7 +344,7 @@ int build_cf_factors(const awg_cf_params& p, const double* pa_centers, const dou
   const int OS = p.oversampling;
   const int Q = (OS + 1) * S;
   std::vector<cd> E, tw;
-  cf_screen(p, pa_centers, sb_freqs, pa, sb, ks, M, E);
+  cf_screen(p, pa_centers, sb_freqs, pa, sb, ks, elem_p, elem_q, M, E);
   axis_twiddles(M, S, OS, tw);
   // axis transform as explicit rows for the checked offsets: Fo[t][i]
   const int chk[3] = {0, OS / 2, OS};
@@ -355,6 +389,11 @@ int build_cf_factors(const awg_cf_params& p, const double* pa_centers, const dou
   for (const cd& v : sl) peak = std::fmax(peak, std::abs(v));
   fx.clear();
   fy.clear();
+  if (peak == 0.0) {   // an all-zero CF (e.g. a leakage element with d = 0): one zero term
+    fx.assign(2 * (size_t)Q, 0.0);
+    fy.assign(2 * (size_t)Q, 0.0);
+    return 1;
+  }
   std::vector<cd> g, f, tg(Q), tf(Q);
   for (int r = 0; r < r_max; ++r) {
     leading_term(E, M, M, g, f);

@@ -117,9 +117,10 @@ __global__ void k_zero_dropped(const int32_t* __restrict__ drop, const unsigned 
   }
 }
 
-// vis_out[s] = sum over the rank terms of sample s (the CF's outer-product terms).
+// vis_out[s] = sum over the rank terms of sample s (the CF's outer-product terms); pol p of sample
+// s lands at s ostride + ooff + p, added to what is there when accumulate is set.
 __global__ void k_sum_terms(const float2* __restrict__ part, float2* __restrict__ vis_out, int64_t n, int rank,
-                            int P) {
+                            int P, int ostride, int ooff, int accumulate) {
   const int64_t total = n * P;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
@@ -131,13 +132,22 @@ __global__ void k_sum_terms(const float2* __restrict__ part, float2* __restrict_
       acc.x += v.x;
       acc.y += v.y;
     }
-    vis_out[i] = acc;
+    float2* o = vis_out + s * ostride + ooff + p;
+    if (accumulate) {
+      const float2 prev = *o;
+      acc.x += prev.x;
+      acc.y += prev.y;
+    }
+    *o = acc;
   }
 }
 
 static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* vis, const float* weight, void* grid,
-                          void* grid_lo, double* sumwt, int flags) {
+                          void* grid_lo, double* sumwt, int flags, int P) {
   GridArgs a;
+  a.cf_shift = 0;
+  a.vstride = a.gstride = P;
+  a.voff = a.goff = 0;
   a.rec = pl->d_rec;
   a.items = pl->d_items;
   a.class_range = cf->separable ? pl->d_slot_range : pl->d_class_range;
@@ -166,8 +176,12 @@ static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* v
   return a;
 }
 
-static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* grid, void* vis_out) {
+static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* grid, void* vis_out, int P) {
   DegridArgs a;
+  a.cf_shift = 0;
+  a.vstride = a.gstride = P;
+  a.voff = a.goff = 0;
+  a.accumulate = 0;
   a.rec = pl->d_rec;
   a.items = pl->d_items;
   a.class_range = cf->separable ? pl->d_slot_range : pl->d_class_range;
@@ -187,6 +201,7 @@ static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const voi
   a.grid = (const float*)grid;
   // with several terms per CF every record writes its own row of the per-term buffer, summed later
   a.vis_out = pl->rank > 1 ? (float*)pl->d_part : (float*)vis_out;
+  if (pl->rank > 1) a.vstride = P;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
   a.rank = pl->rank;
@@ -206,10 +221,29 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   if (s != AWG_OK) return s;
   pl->last_stream = st;
   if (pl->n == 0) return AWG_OK;
-  const GridArgs a = grid_args(cf, pl, vis, weight, grid, grid_lo, sumwt, flags);
-  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+  const GridArgs a = grid_args(cf, pl, vis, weight, grid, grid_lo, sumwt, flags, P);
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
+  if (cf->n_elem > 1) {
+    // Mueller set: one single-pol pass per element (p, q): grid pol q += conj(CF_pq) w_p V_p, and
+    // the diagonal elements add their weights to sumwt[q]
+    if (P != 4) return set_error(AWG_ERR_INVALID_ARG, "a full-polarisation CF set needs 4 pols");
+    for (int e = 0; e < cf->n_elem; ++e) {
+      GridArgs ae = a;
+      ae.cf_shift = (int64_t)e * cf->n_base * pl->rank;
+      ae.vstride = ae.gstride = 4;
+      ae.voff = cf->elem_p[e];
+      ae.goff = cf->elem_q[e];
+      ae.sumwt = cf->elem_p[e] == cf->elem_q[e] ? sumwt + cf->elem_q[e] : nullptr;
+      AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+      for (int i = cf->slots.n - 1; i >= 0; --i) {
+        s = grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, 1, ae, sms, st);
+        if (s != AWG_OK) return s;
+      }
+    }
+    return AWG_OK;
+  }
+  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   if (cf->separable) {
     for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
       s = grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
@@ -228,7 +262,7 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
 // Per-term values summed, then dropped samples zeroed (after the kernels of launch_degrid).
 static awg_status degrid_finish(PlanImpl* pl, void* vis_out, int P, int sms, cudaStream_t st) {
   if (pl->rank > 1) {   // dropped samples' rows are stale here and are zeroed next
-    k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, P);
+    k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, P, P, 0, 0);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   }
@@ -244,10 +278,49 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   if (s != AWG_OK) return s;
   pl->last_stream = st;
   if (pl->n == 0) return AWG_OK;
-  const DegridArgs a = degrid_args(cf, pl, grid, vis_out);
-  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+  const DegridArgs a = degrid_args(cf, pl, grid, vis_out, P);
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
+  if (cf->n_elem > 1) {
+    // Mueller set: vis pol p = sum over elements (p, q) of CF_pq applied to grid pol q; dropped
+    // samples keep the zeros written first
+    if (P != 4) return set_error(AWG_ERR_INVALID_ARG, "a full-polarisation CF set needs 4 pols");
+    AWG_CUDA_TRY(cudaMemsetAsync(vis_out, 0, sizeof(float2) * 4 * (size_t)pl->n, st));
+    for (int e = 0; e < cf->n_elem; ++e) {
+      DegridArgs ae = a;
+      ae.cf_shift = (int64_t)e * cf->n_base * pl->rank;
+      ae.gstride = 4;
+      ae.goff = cf->elem_q[e];
+      if (pl->rank > 1) {   // per-term rows, one pol each, summed into vis pol p below
+        ae.vis_out = (float*)pl->d_part;
+        ae.vstride = 1;
+        ae.voff = 0;
+        ae.accumulate = 0;
+      } else {
+        ae.vis_out = (float*)vis_out;
+        ae.vstride = 4;
+        ae.voff = cf->elem_p[e];
+        ae.accumulate = 1;
+      }
+      AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+      for (int i = cf->slots.n - 1; i >= 0; --i) {
+        s = degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, 1, ae, sms, st);
+        if (s != AWG_OK) return s;
+      }
+      if (pl->rank > 1) {
+        k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, 1, 4, cf->elem_p[e], 1);
+        AWG_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+      }
+    }
+    // rows of dropped samples were never written by the kernels, but the sums above added their
+    // stale per-term rows: zero them again
+    k_zero_dropped<<<sms * 4, 256, 0, st>>>(pl->d_drop, pl->d_counters, (float*)vis_out, 4);
+    AWG_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AWG_OK;
+  }
+  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   if (cf->separable) {
     for (int i = cf->slots.n - 1; i >= 0; --i) {
       s = degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
@@ -326,8 +399,8 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
       // warm-up pass over every support, then three timed passes of each support's launches
       if (s == AWG_OK) s = launch_grid(cf, pl, vis, wt, P, grid, nullptr, sumwt, 0, st);
       if (s == AWG_OK) s = launch_degrid(cf, pl, grid, out, P, st);
-      const GridArgs ga = grid_args(cf, pl, vis, wt, grid, nullptr, sumwt, 0);
-      const DegridArgs da = degrid_args(cf, pl, grid, out);
+      const GridArgs ga = grid_args(cf, pl, vis, wt, grid, nullptr, sumwt, 0, P);
+      const DegridArgs da = degrid_args(cf, pl, grid, out, P);
       for (int i = 0; i < cf->slots.n && s == AWG_OK; ++i) {
         const int S = cf->slots.S[i];
         if (!has_exact(S)) continue;

@@ -47,6 +47,11 @@ struct GridArgs {
   const float* sep;      // separable CF factors (c64), or NULL
   const int64_t* sep_off;
   int rank;              // records per sample; only term 0 (cf % rank == 0) adds its weight
+  // Mueller element launches (separable kernels): factor offsets at sep_off[cf_shift + rc.cf];
+  // sample s reads vis / weight at s vstride + voff and pixel i of the grid is i gstride + goff
+  // (P pols from there); otherwise cf_shift = 0, vstride = gstride = P, voff = goff = 0.
+  int64_t cf_shift;
+  int vstride, voff, gstride, goff;
 };
 
 struct DegridArgs {
@@ -66,6 +71,9 @@ struct DegridArgs {
   const float* sep;      // separable CF factors (c64), or NULL
   const int64_t* sep_off;
   int rank;              // records per sample (term k of sample s writes vis_out row s * rank + k)
+  int64_t cf_shift;      // as in GridArgs; the output row r goes to vis_out at r vstride + voff,
+  int vstride, voff, gstride, goff;
+  int accumulate;        // 1: add to vis_out instead of writing it
 };
 
 template <bool BF16>

@@ -123,7 +123,7 @@ __device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, in
   const int j = threadIdx.x;
   if (j < nst) {
     const SampleRec rc = sl.rec()[j];
-    const long long base = a.sep_off[rc.cf];
+    const long long base = a.sep_off[a.cf_shift + rc.cf];
     sl.fxo()[j] = base + (long long)rc.ox * S;
     sl.fyo()[j] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
     sl.pack()[j] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
@@ -139,7 +139,7 @@ __device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, in
 // visibilities and weights (threads < nst).
 template <int SMAX, int TILE, int P, int ST, int NT>
 __device__ __forceinline__ void stage_payload(const float* sep, const float* vis, const float* weight, int nst, int S,
-                                              const SepSlot<SMAX, TILE, P, ST>& sl) {
+                                              const SepSlot<SMAX, TILE, P, ST>& sl, int vstride = P, int voff = 0) {
   const float2* sep2 = reinterpret_cast<const float2*>(sep);
   const long long* fxo = sl.fxo();
   const long long* fyo = sl.fyo();
@@ -153,8 +153,8 @@ __device__ __forceinline__ void stage_payload(const float* sep, const float* vis
   if (vis != nullptr && (int)threadIdx.x < nst) {
     const int j = threadIdx.x;
     const size_t s = (size_t)sl.src()[j];
-    const float* vp = vis + s * 2 * P;
-    const float* wp = weight + s * P;
+    const float* vp = vis + (s * vstride + voff) * 2;
+    const float* wp = weight + s * vstride + voff;
     if (P == 4) {
       cp_async(sl.v() + j * P, vp, 16);
       cp_async(sl.v() + j * P + 2, vp + 4, 16);
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       derive(a, nst_of(0), S, X0, Y0, s0);
       if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
       __syncthreads();
-      stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(0), S, s0);
+      stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(0), S, s0, a.vstride, a.voff);
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     }
     for (int c = 0; c < nch; ++c) {
       const Slot A(smem, c & 1), B(smem, (c & 1) ^ 1);
-      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(c + 1), S, B);
+      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(c + 1), S, B, a.vstride, a.voff);
       if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
       cp_async_commit();
       const int nst = nst_of(c);
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
         v[p] = tile[p * UU + i];
         nz |= (v[p].x != 0.f) || (v[p].y != 0.f);
       }
-      if (nz) flush_pixel<P>(a, ((size_t)gy * a.N + gx) * P, v);
+      if (nz) flush_pixel<P>(a, ((size_t)gy * a.N + gx) * a.gstride + a.goff, v);
     }
   }
   const int lane = tid & 31, wid = tid >> 5;
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     if (lane == 0) s_wsum[wid][p] = v;
   }
   __syncthreads();
-  if (tid < P) {
+  if (tid < P && a.sumwt) {
     double v = 0.0;
     for (int w = 0; w < NT / 32; ++w) v += s_wsum[w][tid];
     if (v != 0.0) atomicAdd(a.sumwt + tid, v);
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
         const int ly = i / U, lx = i - ly * U;
         const int gy = Y0 + ly, gx = X0 + lx;
         const bool in = gy < a.N && gx < a.N;
-        const float2* src = reinterpret_cast<const float2*>(a.grid) + ((size_t)gy * a.N + gx) * P;
+        const float2* src = reinterpret_cast<const float2*>(a.grid) + ((size_t)gy * a.N + gx) * a.gstride + a.goff;
 #pragma unroll
         for (int p = 0; p < P; ++p) tile[p * UU + i] = in ? __ldg(src + p) : make_float2(0.f, 0.f);
       }
@@ -653,7 +653,8 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
             if (cap_src[q] >= 0) {
               const float2 ph = cap_ph[q];
               const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
-              a.vis_out[(size_t)cap_src[q] * 2 * P + comp] = out;
+              float* o = a.vis_out + ((size_t)cap_src[q] * a.vstride + a.voff) * 2 + comp;
+              *o = a.accumulate ? *o + out : out;
             }
           }
         }

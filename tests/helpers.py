@@ -23,7 +23,8 @@ def library_params(op: ocf.CFParams, cf_dtype: int = 0, separable: bool = True) 
                 n_subbands=op.n_subbands,
                 subband_freq_hz=(np.asarray(op.subband_freq_hz, dtype=np.float64) if op.subband_freq_hz is not None else None),
                 max_support=op.max_support, dish_diameter_m=op.dish_diameter_m, ellipticity=op.ellipticity,
-                cf_dtype=cf_dtype, separable=separable)
+                cf_dtype=cf_dtype, separable=separable, use_pol=op.use_pol, squint_rad=op.squint_rad,
+                leakage=complex(op.leakage), mueller_threshold=op.mueller_threshold)
 
 
 def rel_rms(a, b) -> float:

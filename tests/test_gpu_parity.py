@@ -205,6 +205,43 @@ def test_awproj_parity(awg, separable):
     assert np.all(res["vis"][~orc["idx"].valid] == 0)
 
 
+def test_mueller_full_polarisation_parity(awg):
+    """Sparse Mueller matrix of A-term CFs (feed squint and complex leakage, 12 of 16 elements kept):
+    CF tables, gridding (pol q from conj(CF_pq) w_p V_p), weight sums and degridding against the
+    oracle."""
+    wl = synth.make_workload("awproj", n_int=10, n_chan=8, grid_n=512, n_pa=3, n_sb=2, n_wplanes=4, max_support=32,
+                             oversampling=8)
+    op = oracle_params(wl, use_pol=True, squint_rad=3e-4, leakage=0.04 * np.exp(0.9j), mueller_threshold=0.01)
+    cf = awg.cf_set_create(**library_params(op))
+    assert cf.mueller() == ocf.mueller_elements(op) and len(cf.mueller()) == 12
+    assert cf.separable and cf.rank >= 1
+    # a diagonal and a leakage element table
+    for e in (0, 1):
+        ci = e * op.n_base + op.cf_index(1, 1, op.n_signed - 1)
+        ref = ocf.cf_table(op, 1, 1, op.n_signed - 1, ocf.mueller_elements(op)[e])
+        assert np.abs(cf.copy_table(ci) - ref).max() <= 1.5e-6 * np.abs(ref).max() + 1e-9
+    R, C, N = wl.n_rows, wl.n_chan, wl.grid_n
+    vis = wl.vis.reshape(-1, 4)
+    wt = wl.weight.reshape(-1, 4)
+    plan = awg.plan_create(cf, _dev(wl.uvw_m), _dev(wl.freq_hz), _dev(wl.pa_bin, torch.int32),
+                           _dev(wl.chan_subband, torch.int32))
+    g = torch.zeros((N, N, 4), dtype=torch.complex64, device="cuda")
+    sw = torch.zeros(4, dtype=torch.float64, device="cuda")
+    awg.grid_visibilities(cf, plan, _dev(vis.reshape(R, C, 4), torch.complex64), _dev(wt.reshape(R, C, 4), torch.float32),
+                          g, sw)
+    out = torch.full((R, C, 4), complex(5.0, 1.0), dtype=torch.complex64, device="cuda")
+    awg.degrid_visibilities(cf, plan, g, out)
+    idx = oindex.sample_index(op, wl.uvw_m, wl.freq_hz, wl.pa_bin, wl.chan_subband)
+    buf, off, _ = ocf.flatten_cf_set(op, ocf.cf_set(op))
+    g_o, sw_o = oops.grid_mueller(op, idx, buf, off, op.oversampling, N, vis.astype(np.complex128),
+                                  wt.astype(np.float64))
+    assert rel_rms(g.cpu().numpy(), g_o) < 1e-5
+    assert np.allclose(sw.cpu().numpy(), sw_o, rtol=1e-12)
+    d_o = oops.degrid_mueller(op, idx, buf, off, op.oversampling, g.cpu().numpy().astype(np.complex128))
+    assert rel_rms(out.cpu().numpy().reshape(-1, 4), d_o) < 1e-5
+    assert np.all(out.cpu().numpy().reshape(-1, 4)[~idx.valid] == 0)
+
+
 def _random_tables_case(awg, P, rank1, config=0):
     sups = [1, 3, 7, 8, 9, 15, 16, 17, 24, 25, 31, 32, 33, 40, 48, 49, 56, 63, 64]
     wl = synth.make_workload("standard", n_int=16, n_chan=3, f_lo=2.8e9, f_hi=3.2e9, with_vis=False)

@@ -515,3 +515,79 @@ def test_gcal_lowers_chi2_with_noise():
         assert chi(gs) < 0.1 * chi(np.ones(27))
         gt = g[idx] * np.conj(g[idx][0]) / abs(g[idx][0])
         assert np.abs(gs - gt).max() < 0.05
+
+
+# ------------------------------------------------------------- full polarisation (Mueller CFs)
+
+def _pol_params(**over):
+    kw = dict(grid_n=256, cell_rad=2e-5, oversampling=6, max_support=24, use_w=True, n_wplanes=3,
+              w_max_lambda=3e4, use_a=True, n_pa_bins=2, pa_bin_centers=[0.3, -0.9], n_subbands=1,
+              subband_freq_hz=[3.0e9], use_pol=True, squint_rad=2.5e-4, leakage=0.05 * np.exp(0.7j),
+              mueller_threshold=0.01)
+    kw.update(over)
+    return cf.CFParams(**kw)
+
+
+def test_mueller_element_list():
+    assert len(cf.mueller_elements(_pol_params())) == 12          # 4 diagonal + 8 with one leakage factor
+    assert len(cf.mueller_elements(_pol_params(mueller_threshold=0.002))) == 16
+    assert cf.mueller_elements(_pol_params(leakage=0.0)) == [(0, 0), (1, 1), (2, 2), (3, 3)]
+
+
+def test_mueller_without_squint_or_leakage_is_the_pol_shared_aterm():
+    """J = diag(A, A): every diagonal element's screen is A^2, the Airy power pattern of the
+    pol-shared A-term, and the element tables equal that CF."""
+    p = _pol_params(squint_rad=0.0, leakage=0.0)
+    p0 = _pol_params(use_pol=False)
+    for e in range(4):
+        for ks in range(p.n_signed):
+            t = cf.cf_table(p, 1, 0, ks, cf.mueller_elements(p)[e])
+            t0 = cf.cf_table(p0, 1, 0, ks)
+            assert np.abs(t - t0).max() <= 1e-13 * np.abs(t0).max()
+
+
+def test_mueller_screens_are_the_jones_kronecker_product():
+    """Element (p, q) of the screen is entry (p, q) of kron(J, conj(J)) in the RR, RL, LR, LL
+    order (numpy's Kronecker product, not the element formula)."""
+    p = _pol_params(mueller_threshold=0.0)
+    M = 32
+    i = np.arange(M, dtype=np.float64)
+    lm = (i - M / 2) * p.grid_n / M * p.cell_rad
+    chi = p.pa_bin_centers[0]
+    L, Mm = lm[None, :], lm[:, None]
+    lr = L * math.cos(chi) + Mm * math.sin(chi)
+    mr = -L * math.sin(chi) + Mm * math.cos(chi)
+    eps = p.ellipticity
+    rr = np.sqrt(((lr - p.squint_rad) / (1 + eps)) ** 2 + (mr / (1 - eps)) ** 2)
+    rl = np.sqrt(((lr + p.squint_rad) / (1 + eps)) ** 2 + (mr / (1 - eps)) ** 2)
+    ar = cf.airy_voltage(rr, 3.0e9, 25.0)
+    al = cf.airy_voltage(rl, 3.0e9, 25.0)
+    base = cf.screen(cf.CFParams(grid_n=p.grid_n, cell_rad=p.cell_rad, use_w=True, n_wplanes=3, w_max_lambda=3e4),
+                     0, 0, 4, M)
+    d = p.leakage
+    for y, x in [(3, 5), (16, 16), (20, 9), (31, 0)]:
+        J = np.array([[ar[y, x], d * ar[y, x]], [d * al[y, x], al[y, x]]])
+        K = np.kron(J, J.conj())
+        for e, (pp, qq) in enumerate(cf.mueller_elements(p)):
+            s = cf.screen(p, 0, 0, 4, M, (pp, qq))
+            assert abs(s[y, x] - base[y, x] * K[pp, qq]) <= 1e-14 * max(1.0, abs(s[y, x]))
+
+
+def test_mueller_gridding_is_the_adjoint_of_degridding():
+    """<G_M V, X> = <V, D_M X> with unit weights for the full Mueller operators."""
+    p = _pol_params(grid_n=128, cell_rad=4e-5, max_support=16, oversampling=4)
+    wl = synth.make_workload("standard", n_int=3, with_vis=False)
+    rng = np.random.default_rng(12)
+    uvw = wl.uvw_m * 0.02
+    freq = np.array([3.0e9])
+    pa = rng.integers(0, 2, uvw.shape[0]).astype(np.int32)
+    idx = index.sample_index(p, uvw, freq, pa_bin=pa)
+    assert idx.valid.mean() > 0.5
+    buf, off, _ = cf.flatten_cf_set(p, cf.cf_set(p))
+    n = idx.valid.shape[0]
+    V = rng.standard_normal((n, 4)) + 1j * rng.standard_normal((n, 4))
+    X = rng.standard_normal((p.grid_n, p.grid_n, 4)) + 1j * rng.standard_normal((p.grid_n, p.grid_n, 4))
+    g, _ = ops.grid_mueller(p, idx, buf, off, p.oversampling, p.grid_n, V, np.ones((n, 4)))
+    d = ops.degrid_mueller(p, idx, buf, off, p.oversampling, X)
+    a, b = np.vdot(g, X), np.vdot(V, d)
+    assert abs(a - b) <= 1e-12 * abs(a)
