@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--config", choices=["wproj", "awproj"], default="wproj",
                     help="wproj: the W-projection workload (default); awproj: the batched AW-projection workload "
                          "(20 PA bins x 32 w-planes x 16 sub-bands, CFs as sums of outer products)")
+    ap.add_argument("--mosaic", action="store_true",
+                    help="give every row its own phase centre (a two-field mosaic with pointing offsets)")
+    ap.add_argument("--full-pol", action="store_true",
+                    help="with --config awproj: full-polarisation A-terms (sparse Mueller CFs; 4 PA bins x 4 "
+                         "sub-bands so that the 12-element CF set builds in seconds)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel configuration of every support instead of timing both")
     ap.add_argument("--minor-cycle", action="store_true",
@@ -73,9 +78,12 @@ def dist_env():
     return world, rank, local
 
 
+WORKLOAD_OVERRIDES = {}
+
+
 def rank_workload(world: int, rank: int, n_int: int, device: str, with_vis=True):
     """Rank `rank`'s slice of a track of world * n_int integrations (time-major rows)."""
-    full = synth.make_workload(CONFIG, with_vis=False, n_int=n_int * world)
+    full = synth.make_workload(CONFIG, with_vis=False, n_int=n_int * world, **WORKLOAD_OVERRIDES)
     r0, r1 = rank * n_int * full.n_bl, (rank + 1) * n_int * full.n_bl
     wl = dataclasses.replace(full, uvw_m=full.uvw_m[r0:r1].copy(), pa_rad=full.pa_rad[r0:r1].copy(),
                              pa_bin=full.pa_bin[r0:r1].copy(), n_int=n_int)
@@ -529,20 +537,38 @@ WORKLOADS = {
 }
 
 
-def cf_kwargs(wl) -> dict:
-    """cf_set_create arguments of a workload."""
+def cf_kwargs(wl, full_pol=False) -> dict:
+    """cf_set_create arguments of a workload (full_pol: squinted feeds, leakage 0.04, 12 Mueller
+    elements)."""
     kw = dict(grid_n=wl.grid_n, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support,
               use_w=wl.use_w, n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda, max_support=wl.max_support)
     if wl.use_a:
         kw.update(use_a=True, n_pa_bins=wl.n_pa_bins, pa_bin_centers_rad=np.asarray(wl.pa_bin_centers),
                   n_subbands=wl.n_subbands, subband_freq_hz=np.asarray(wl.subband_freq_hz))
+    if full_pol:
+        kw.update(use_pol=True, squint_rad=2e-4, leakage=0.04 * np.exp(0.9j), mueller_threshold=0.01)
     return kw
+
+
+def mosaic_row_phase(wl) -> np.ndarray:
+    """Per-row (dl, dm) of a two-field mosaic: pointings on alternating integrations 30 / 20 cells
+    from the image centre, plus a per-row pointing offset of up to 2 cells."""
+    rng = np.random.default_rng(4)
+    field = (np.arange(wl.n_rows) // wl.n_bl) % 2
+    dl = np.where(field == 0, 30.0, -30.0) * wl.cell_rad
+    dm = np.where(field == 0, -20.0, 20.0) * wl.cell_rad
+    jit = rng.uniform(-2.0, 2.0, (wl.n_rows, 2)) * wl.cell_rad
+    return np.stack([dl + jit[:, 0], dm + jit[:, 1]], -1)
 
 
 def main():
     global CONFIG
     args = parse()
     CONFIG = args.config
+    if args.full_pol:
+        if CONFIG != "awproj":
+            raise SystemExit("--full-pol needs --config awproj")
+        WORKLOAD_OVERRIDES.update(n_pa=4, n_sb=4)
     if args.impl == "reference":
         return reference_arm(args)
     if args.precision_sweep:
@@ -569,7 +595,7 @@ def main():
     lib = _lib.load()
 
     t_cf = time.perf_counter()
-    cf = awg.cf_set_create(**cf_kwargs(wl))
+    cf = awg.cf_set_create(**cf_kwargs(wl, args.full_pol))
     t_cf = time.perf_counter() - t_cf
     uvw = torch.as_tensor(wl.uvw_m, device=dev)
     freq = torch.as_tensor(wl.freq_hz, device=dev)
@@ -582,6 +608,8 @@ def main():
         tuned, _ = cf.autotune(uvw, freq, pa_bin, chan_sb, n_pol=wl.n_pol)
         t_tune = time.perf_counter() - t_tune
     plan = awg.plan_create(cf, uvw, freq, pa_bin, chan_sb)
+    if args.mosaic:
+        plan.set_row_phase(torch.as_tensor(mosaic_row_phase(wl), device=dev), uvw, freq)
     kept, dropped, sum_taps = plan.stats()
     grid = torch.zeros((N, N, P), dtype=torch.complex64, device=dev)
     sumwt = torch.zeros(P, dtype=torch.float64, device=dev)
@@ -745,7 +773,9 @@ def main():
     fma = measure_fma_peak(lib, sms, dev)
     # the kernels run inside a long step: the sustained probe rate is their ceiling
     peak_tf = fma["sustained_tflops"]
-    flop = 8.0 * P * sum_taps          # one complex MAC = 4 FP32 FMA = 8 FLOP, per pol and tap
+    # one complex MAC = 4 FP32 FMA = 8 FLOP per tap and pol product; a full-polarisation set applies
+    # one CF per kept Mueller element instead of one per pol
+    flop = 8.0 * (len(cf.mueller()) or P) * sum_taps
     g_ms = statistics.mean(op_ms["grid"])
     d_ms = statistics.mean(op_ms["degrid"])
     dom, dom_ms = ("grid", g_ms) if g_ms >= d_ms else ("degrid", d_ms)
@@ -760,7 +790,10 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic VLA A-array-like uvw, 200 point sources + 1 mJy noise, natural weights",
-        "config": {"workload": WORKLOADS[CONFIG], "cf_terms": max(cf.rank, 1), "cf_storage":
+        "config": {"workload": WORKLOADS[CONFIG] + (" (full polarisation: 4 PA bins x 4 sub-bands, "
+                                                     f"{len(cf.mueller())} Mueller elements)" if args.full_pol else "")
+                   + (" (two-field mosaic: per-row phase centres)" if args.mosaic else ""),
+                   "cf_terms": max(cf.rank, 1), "cf_storage":
                    "separable factors" if cf.separable else "full tables", "cf_build_s": t_cf,
                    "kernel_config_per_support": tuned, "autotune_s": t_tune,
                    "visibilities_per_step": vis_per_step, "kept_samples": kept, "dropped_samples": dropped,

@@ -190,8 +190,9 @@ awg_status cf_set_copy_table(awg_cf_set cf, int32_t cf_index, float* table_out);
  * n_pa_bins > 1, else may be NULL); chan_subband: device int32 [C] (needed when n_subbands > 1);
  * phase_shift: host f64 [2] (dl, dm) of the image centre from the phase centre, or NULL for none:
  * G multiplies w V by exp(+2 pi i (u dl + v dm + w dn)), dn = sqrt(1 - dl^2 - dm^2) - 1, D by its
- * conjugate (the phase term of Eq. CIJ).  The plan allocates device memory (about 44 bytes per
- * sample) and keeps pointers to no caller buffer.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * conjugate (the phase term of Eq. CIJ); the plan forms every sample's phasor once per build and
+ * the kernels read it.  The plan allocates device memory (about 44 bytes per sample and CF term,
+ * 8 more per sample with a phase term) and keeps pointers to no caller buffer.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
  */
 awg_status plan_create(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const double* freq_hz,
                        int32_t n_chan, const int32_t* pa_bin, const int32_t* chan_subband,

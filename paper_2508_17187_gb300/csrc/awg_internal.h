@@ -156,6 +156,7 @@ struct PlanImpl {
   double* d_uvw = nullptr;        // plan-owned copies of uvw / freq (only with a phase shift,
   double* d_freq = nullptr;       // whose phasor the compute kernels form per sample)
   double* d_row_dlm = nullptr;    // per-row phase centres [R][2] (plan_set_row_phase) or NULL
+  float2* d_phasor = nullptr;     // per-sample phasor [n] of the phase term (when has_phase)
   int global_phase = 0;           // a plan-wide phase shift was given to plan_create
   cudaStream_t last_stream = nullptr;
 };
@@ -211,6 +212,9 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
                              const int32_t* pa_bin, const int32_t* chan_sb, int P, cudaStream_t st, int32_t* choice,
                              float* ms_out);
 void fill_slots(CfSetImpl* cf);
+// Forms every sample's phasor exp(+2 pi i (u dl + v dm + w dn)) of the plan's phase term (plan-wide
+// shift or per-row centres) from the plan's uvw / freq copies into d_phasor.
+awg_status compute_phasors(PlanImpl* pl, cudaStream_t st);
 awg_status launch_normalize(CfSetImpl* cf, void* image, int P, const double* sumwt, int direction,
                             cudaStream_t st);
 

@@ -590,6 +590,7 @@ static awg_status plan_free(PlanImpl* pl) {
   cudaFree(pl->d_uvw);
   cudaFree(pl->d_freq);
   cudaFree(pl->d_row_dlm);
+  cudaFree(pl->d_phasor);
   delete pl;
   return AWG_OK;
 }
@@ -656,6 +657,7 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
   if (pl->has_phase) {
     A((void**)&pl->d_uvw, (size_t)std::max<int64_t>(pl->R, 1) * 3 * sizeof(double));
     A((void**)&pl->d_freq, (size_t)pl->C * sizeof(double));
+    A((void**)&pl->d_phasor, n * sizeof(float2));
   }
   if (e != cudaSuccess) {
     plan_free(pl);
@@ -683,20 +685,21 @@ awg_status plan_set_row_phase(awg_plan h, const double* row_dlm, const double* u
       pl->d_row_dlm = nullptr;
     }
     pl->has_phase = pl->global_phase;
-    return AWG_OK;
+    return pl->has_phase ? compute_phasors(pl, st) : AWG_OK;
   }
   if (pl->R > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
   const size_t R = (size_t)std::max<int64_t>(pl->R, 1);
   if (!pl->d_row_dlm) AWG_CUDA_TRY(cudaMalloc(&pl->d_row_dlm, R * 2 * sizeof(double)));
   if (!pl->d_uvw) AWG_CUDA_TRY(cudaMalloc(&pl->d_uvw, R * 3 * sizeof(double)));
   if (!pl->d_freq) AWG_CUDA_TRY(cudaMalloc(&pl->d_freq, (size_t)pl->C * sizeof(double)));
+  if (!pl->d_phasor) AWG_CUDA_TRY(cudaMalloc(&pl->d_phasor, (size_t)std::max<int64_t>(pl->n, 1) * sizeof(float2)));
   if (pl->R > 0) {
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_row_dlm, row_dlm, R * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_uvw, uvw_m, R * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_freq, freq_hz, (size_t)pl->C * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   pl->has_phase = 1;
-  return AWG_OK;
+  return compute_phasors(pl, st);
 }
 
 awg_status plan_update(awg_plan h, const double* uvw_m, const double* freq_hz, const int32_t* pa_bin,

@@ -165,6 +165,7 @@ static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* v
   a.uvw = pl->d_uvw;
   a.freq = pl->d_freq;
   a.row_dlm = pl->d_row_dlm;
+  a.phasor = pl->has_phase ? pl->d_phasor : nullptr;
   a.vis = (const float*)vis;
   a.weight = weight;
   a.grid = (float*)grid;
@@ -198,6 +199,7 @@ static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const voi
   a.uvw = pl->d_uvw;
   a.freq = pl->d_freq;
   a.row_dlm = pl->d_row_dlm;
+  a.phasor = pl->has_phase ? pl->d_phasor : nullptr;
   a.grid = (const float*)grid;
   // with several terms per CF every record writes its own row of the per-term buffer, summed later
   a.vis_out = pl->rank > 1 ? (float*)pl->d_part : (float*)vis_out;

@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "awg_internal.h"
+#include "resample.cuh"
 
 namespace awg {
 namespace {
@@ -320,7 +321,32 @@ __global__ void __launch_bounds__(kItemChunk) k_sort_items(const int32_t* __rest
   }
 }
 
+struct PhaseArgs {
+  const double* uvw;
+  const double* freq;
+  const double* row_dlm;
+  int C;
+  double dl, dm, dn;
+};
+
+__global__ void k_phasors(PhaseArgs a, int64_t n, float2* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride) out[s] = phasor_of(a, (int)s);
+}
+
 }  // namespace
+
+awg_status compute_phasors(PlanImpl* pl, cudaStream_t st) {
+  if (pl->n == 0) return AWG_OK;
+  PhaseArgs a{pl->d_uvw, pl->d_freq, pl->d_row_dlm, pl->C, pl->dl, pl->dm, pl->dn};
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
+  const int blocks = (int)std::min<int64_t>((pl->n + 255) / 256, (int64_t)std::max(sms, 1) * 8);
+  k_phasors<<<blocks, 256, 0, st>>>(a, pl->n, pl->d_phasor);
+  AWG_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return AWG_OK;
+}
 
 // class_of_support is also used in device code above.
 awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const int32_t* pa_bin,
@@ -331,6 +357,8 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
   if (pl->has_phase && pl->n > 0) {
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_uvw, uvw, sizeof(double) * 3 * pl->R, cudaMemcpyDeviceToDevice, st));
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_freq, freq, sizeof(double) * pl->C, cudaMemcpyDeviceToDevice, st));
+    awg_status ps = compute_phasors(pl, st);
+    if (ps != AWG_OK) return ps;
   }
   const int nb = pl->n_buckets;
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_bcount, 0, sizeof(int32_t) * (nb + 1), st));

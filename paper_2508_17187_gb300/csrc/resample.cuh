@@ -39,6 +39,7 @@ struct GridArgs {
   const double* uvw;
   const double* freq;
   const double* row_dlm; // per-row (dl, dm) [R][2] or NULL (then dl, dm, dn apply to every row)
+  const float2* phasor;  // per-sample phasor [n] formed by the plan, or NULL (no phase term)
   const float* vis;      // interleaved c64 [n][P]
   const float* weight;   // [n][P]
   float* grid;           // c64 [N][N][P] (or complex128 with AWG_GRID_FP64)
@@ -66,6 +67,7 @@ struct DegridArgs {
   const double* uvw;
   const double* freq;
   const double* row_dlm; // per-row (dl, dm) [R][2] or NULL
+  const float2* phasor;  // per-sample phasor [n] formed by the plan, or NULL
   const float* grid;     // c64 [N][N][P]
   float* vis_out;        // c64 [n][P]; with rank > 1 the per-term values [n][rank][P]
   const float* sep;      // separable CF factors (c64), or NULL
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(NT) k_grid(const GridArgs a, const int cls) {
           wt[0] = __ldg(wp);
         }
         float2 ph = make_float2(1.f, 0.f);
-        if (a.has_phase) ph = phasor_of(a, rc.src);
+        if (a.phasor) ph = a.phasor[rc.src];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           wsum[p] += (double)wt[p];
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(NT) k_degrid(const DegridArgs a, const int cls
         s_pack[tid] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
         s_src[tid] = rc.src;
         float2 ph = make_float2(1.f, 0.f);
-        if (a.has_phase) ph = phasor_of(a, rc.src);
+        if (a.phasor) ph = a.phasor[rc.src];
         s_ph[tid] = ph;
       }
       __syncthreads();

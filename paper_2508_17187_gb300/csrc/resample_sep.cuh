@@ -131,7 +131,7 @@ __device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, in
       sl.src()[j] = a.rank > 1 ? rc.src * a.rank + rc.cf % a.rank : rc.src;
     else   // the visibility / weight row
       sl.src()[j] = rc.src;
-    sl.ph()[j] = a.has_phase ? phasor_of(a, rc.src) : make_float2(1.f, 0.f);
+    sl.ph()[j] = a.phasor ? a.phasor[rc.src] : make_float2(1.f, 0.f);
   }
 }
 
