@@ -299,7 +299,10 @@ __global__ void __launch_bounds__(kItemChunk) k_sort_items(const int32_t* __rest
     }
     s_idx[t] = (unsigned short)t;
     __syncthreads();
-    for (int k = 2; k <= kItemChunk; k <<= 1) {
+    // the network of the item's own power of two (the padding keys sort last either way)
+    int n2 = 2;
+    while (n2 < wi.count) n2 <<= 1;
+    for (int k = 2; k <= n2; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
         const int ixj = t ^ j;
         if (ixj > t) {
