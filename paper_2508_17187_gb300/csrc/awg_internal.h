@@ -119,6 +119,7 @@ struct CfSetImpl {
   int8_t cand[kMaxSupport + 1] = {};   // exact-kernel candidate per support (cf_set_autotune)
   int slots_version = 0;               // bumped whenever the slot table (tiles) changes
   int rank = 1;                      // outer-product terms per CF when separable
+  int fused = 0;                     // rank of the fused kernels (2..4) when every support has them, else 0
   std::vector<int64_t> sep_offsets;  // [n_cf * rank]: element offset of term k of CF c at c * rank + k
   void* d_sep = nullptr;
   int64_t* d_sep_off = nullptr;

@@ -187,6 +187,11 @@ static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<
     rank = std::max(rank, (int)(fx[i].size() / (2 * (size_t)(OS + 1) * cf->supports[i])));
   cf->separable = 1;
   cf->rank = rank;
+  // fused kernels (one plan record per sample) for 2..4 terms on the exact supports, single Mueller
+  // element; otherwise the plan holds one record per sample and term
+  cf->fused = rank >= 2 && rank <= 4 && cf->n_elem == 1 ? rank : 0;
+  for (int i = 0; i < cf->n_cf && cf->fused; ++i)
+    if (!has_exact(cf->supports[i])) cf->fused = 0;
   cf->sep_offsets.assign((size_t)cf->n_cf * rank, 0);
   int64_t off = 2 * (int64_t)(OS + 1) * kMaxSupport;   // the zero block (fx and fy of the largest support)
   for (int i = 0; i < cf->n_cf; ++i) {
@@ -499,6 +504,7 @@ awg_status cf_set_choose(awg_cf_set h, int32_t support, int32_t config) {
   if (support < 1 || support > kMaxSupport || !has_exact(support))
     return set_error(AWG_ERR_INVALID_ARG, "support " + std::to_string(support) + " has no kernel configurations");
   if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0 or 1");
+  if (cf->fused && config != 0) return set_error(AWG_ERR_UNSUPPORTED, "fused kernels have one configuration");
   cf->cand[support] = (int8_t)config;
   fill_slots(cf);
   return AWG_OK;
@@ -615,7 +621,7 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
   pl->R = n_rows;
   pl->C = n_chan;
   pl->n = n_rows * n_chan;
-  pl->rank = cf->separable ? cf->rank : 1;
+  pl->rank = cf->separable && !cf->fused ? cf->rank : 1;
   pl->slots_version = cf->slots_version;
   pl->n_rec = pl->n * pl->rank;
   if (pl->n_rec > ((int64_t)1 << 31) - 1) {

@@ -18,6 +18,12 @@ AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 0)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 0)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 1)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 1)
+AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 2)
+AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 3)
+AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 4)
+AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 2)
+AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 3)
+AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 4)
 
 namespace {
 
@@ -59,6 +65,27 @@ awg_status grid_slot_sep(int S, int cand, int slot, int P, const GridArgs& a, in
   AWG_FOR_SEP_CLASSES_AND_POLS(AWG_CASE)
 #undef AWG_CASE
   return set_error(AWG_ERR_UNSUPPORTED, "no separable gridding kernel for this support / pol count");
+}
+
+// Fused kernels: one record per sample of a CF set of rk outer-product terms.
+awg_status grid_slot_fused(int S, int rk, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
+#define AWG_CASE(SS, PP, RR) \
+  if (S == SS && P == PP && rk == RR) return run_grid_fused<SS, PP, RR>(a, slot, sms, st);
+  AWG_FOR_FUSED(AWG_CASE, 2)
+  AWG_FOR_FUSED(AWG_CASE, 3)
+  AWG_FOR_FUSED(AWG_CASE, 4)
+#undef AWG_CASE
+  return set_error(AWG_ERR_UNSUPPORTED, "no fused gridding kernel for this support / pol count / rank");
+}
+
+awg_status degrid_slot_fused(int S, int rk, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+#define AWG_CASE(SS, PP, RR) \
+  if (S == SS && P == PP && rk == RR) return run_degrid_fused<SS, PP, RR>(a, slot, sms, st);
+  AWG_FOR_FUSED(AWG_CASE, 2)
+  AWG_FOR_FUSED(AWG_CASE, 3)
+  AWG_FOR_FUSED(AWG_CASE, 4)
+#undef AWG_CASE
+  return set_error(AWG_ERR_UNSUPPORTED, "no fused degridding kernel for this support / pol count / rank");
 }
 
 awg_status degrid_slot_sep(int S, int cand, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
@@ -248,7 +275,8 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   if (cf->separable) {
     for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
-      s = grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
+      s = cf->fused ? grid_slot_fused(cf->slots.S[i], cf->fused, i, P, a, sms, st)
+                    : grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
       if (s != AWG_OK) return s;
     }
     return AWG_OK;
@@ -325,7 +353,8 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
   if (cf->separable) {
     for (int i = cf->slots.n - 1; i >= 0; --i) {
-      s = degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
+      s = cf->fused ? degrid_slot_fused(cf->slots.S[i], cf->fused, i, P, a, sms, st)
+                    : degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
       if (s != AWG_OK) return s;
     }
   } else {
@@ -353,7 +382,7 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
   for (int S = 0; S <= kMaxSupport; ++S) choice[S] = -1;
   if (ms_out)
     for (int i = 0; i < kNumCand * (kMaxSupport + 1); ++i) ms_out[i] = 0.f;
-  if (!cf->separable) return AWG_OK;   // full-table sets have one kernel per class
+  if (!cf->separable || cf->fused) return AWG_OK;   // full tables and fused kernels: one configuration
   const int N = cf->p.grid_n;
   const int64_t n = n_rows * (int64_t)n_chan;
   // unit visibilities and weights (a value-independent timing; zeros would skip the flushes)

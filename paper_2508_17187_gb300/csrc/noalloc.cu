@@ -70,7 +70,7 @@ extern "C" awg_status grid_visibilities_noalloc(awg_cf_set hc, const double* uvw
   if (n_rows < 0 || n_chan < 1) return set_error(AWG_ERR_INVALID_ARG, "n_rows must be >= 0 and n_chan >= 1");
   if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
   const int64_t n = n_rows * (int64_t)n_chan;
-  const int rank = cf->separable ? cf->rank : 1;   // records per sample
+  const int rank = cf->separable && !cf->fused ? cf->rank : 1;   // records per sample
   if (n * rank > kNoAllocMaxSamples)
     return set_error(AWG_ERR_INVALID_ARG, "grid_visibilities_noalloc takes at most " +
                                               std::to_string(kNoAllocMaxSamples) +

@@ -48,43 +48,46 @@ __host__ __device__ constexpr int sep_rows(int smin, int smax, int nt) {
 // memory, twice (the chunk being computed and the one being fetched).
 __host__ __device__ constexpr int sep_stage(int smax) { return smax >= 56 ? 8 : 16; }
 
-// Shared-memory layout: the U x U window, then two slots of staged samples.
-template <int SMAX, int TILE, int P, int ST>
+// Shared-memory layout: the U x U window, then two slots of staged samples.  RK > 1 (fused
+// kernels for CF sets of RK outer-product terms): a sample stages RK pairs of factor rows.
+template <int SMAX, int TILE, int P, int ST, int RK = 1>
 struct SepLayout {
   static constexpr int UMAX = TILE + SMAX - 1;
   // rounded up so that each slot starts 128-byte aligned (16-byte cp.async destinations)
   static constexpr size_t tile_bytes = ((size_t)UMAX * UMAX * P * sizeof(float2) + 127) & ~(size_t)127;
   // per slot
-  static constexpr size_t f_off = 0;                                             // float2 [ST][2][SMAX]
-  static constexpr size_t v_off = f_off + (size_t)ST * 2 * SMAX * sizeof(float2);  // float2 [ST][P]
+  static constexpr size_t f_off = 0;                                             // float2 [ST][2 RK][SMAX]
+  static constexpr size_t v_off = f_off + (size_t)ST * 2 * RK * SMAX * sizeof(float2);  // float2 [ST][P]
   static constexpr size_t a_off = v_off + (size_t)ST * P * sizeof(float2);        // float2 [ST][P]
   static constexpr size_t w_off = a_off + (size_t)ST * P * sizeof(float2);        // float [ST][P] (padded)
   static constexpr size_t r_off = w_off + (((size_t)ST * P * sizeof(float) + 15) & ~(size_t)15);  // SampleRec [ST]
-  static constexpr size_t x_off = r_off + (size_t)ST * sizeof(SampleRec);          // long long [ST] fx offsets
-  static constexpr size_t y_off = x_off + (size_t)ST * sizeof(long long);          // long long [ST] fy offsets
-  static constexpr size_t ph_off = y_off + (size_t)ST * sizeof(long long);         // float2 [ST]
+  static constexpr size_t x_off = r_off + (size_t)ST * sizeof(SampleRec);          // long long [ST][RK] fx offsets
+  static constexpr size_t y_off = x_off + (size_t)ST * RK * sizeof(long long);     // long long [ST][RK] fy offsets
+  static constexpr size_t ph_off = y_off + (size_t)ST * RK * sizeof(long long);    // float2 [ST]
   static constexpr size_t k_off = ph_off + (size_t)ST * sizeof(float2);            // int [ST] packed offsets
   static constexpr size_t s_off = k_off + (size_t)ST * sizeof(int);                // int [ST] sample index
   static constexpr size_t slot_bytes = (s_off + (size_t)ST * sizeof(int) + 127) & ~(size_t)127;
   // per-chunk table by column residue: gridding alpha[j][rx][p] = conj(fx[j][tx]) w V_p,
-  // degridding beta[j][rx] = fx[j][tx], tx = (rx - p0x) mod S
+  // degridding beta[j][rx] = fx[j][tx], tx = (rx - p0x) mod S; with RK > 1 both hold the terms
+  // beta[j][rx][t] = fx_t[j][tx] (conjugated for gridding)
   static constexpr size_t al_off = tile_bytes + 2 * slot_bytes;
-  static constexpr size_t al_bytes = (size_t)ST * SMAX * P * sizeof(float2);
+  static constexpr size_t al_bytes = (size_t)ST * SMAX * (RK > 1 ? RK : P) * sizeof(float2);
   static constexpr size_t bytes = al_off + al_bytes;
 };
 
 // CTAs per SM that the shared-memory window allows (228 KB per SM, 1 KB reserved per CTA),
-// capped so that each thread keeps at least 96 registers: the min-blocks hint of the kernels.
-__host__ __device__ constexpr int sep_min_blocks(size_t smem_bytes, int nt) {
+// capped so that each thread keeps at least min_regs registers (96; 128 for the fused kernels,
+// which also hold the CF terms and w V): the min-blocks hint of the kernels.
+__host__ __device__ constexpr int sep_min_blocks(size_t smem_bytes, int nt, int min_regs = 96) {
   const int by_smem = (int)(233472 / (smem_bytes + 1024));
-  const int by_regs = 65536 / (nt * 96);
+  const int by_regs = 65536 / (nt * min_regs);
   const int b = by_smem < by_regs ? by_smem : by_regs;
   return b < 1 ? 1 : b;
 }
 
-template <int SMAX, int TILE, int P, int ST>
+template <int SMAX, int TILE, int P, int ST, int RK = 1>
 struct SepSlot {
-  using L = SepLayout<SMAX, TILE, P, ST>;
+  using L = SepLayout<SMAX, TILE, P, ST, RK>;
   unsigned char* base;
   __device__ SepSlot(unsigned char* smem, int slot) : base(smem + L::tile_bytes + slot * L::slot_bytes) {}
   __device__ float2* f() const { return reinterpret_cast<float2*>(base + L::f_off); }
@@ -112,20 +115,26 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Records of chunk c into a slot (threads < nst, one 16-byte copy each).
-template <int SMAX, int TILE, int P, int ST>
-__device__ __forceinline__ void stage_recs(const SampleRec* rec, int start, int nst, const SepSlot<SMAX, TILE, P, ST>& sl) {
+template <int SMAX, int TILE, int P, int ST, int RK>
+__device__ __forceinline__ void stage_recs(const SampleRec* rec, int start, int nst,
+                                           const SepSlot<SMAX, TILE, P, ST, RK>& sl) {
   if ((int)threadIdx.x < nst) cp_async(sl.rec() + threadIdx.x, rec + start + threadIdx.x, 16);
 }
 
 // From staged records: packed window offsets, factor-row offsets, sample index, phasor.
-template <int SMAX, int TILE, int P, int ST, class Args>
-__device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, int Y0, const SepSlot<SMAX, TILE, P, ST>& sl) {
+template <int SMAX, int TILE, int P, int ST, int RK, class Args>
+__device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, int Y0,
+                                       const SepSlot<SMAX, TILE, P, ST, RK>& sl) {
   const int j = threadIdx.x;
   if (j < nst) {
     const SampleRec rc = sl.rec()[j];
-    const long long base = a.sep_off[a.cf_shift + rc.cf];
-    sl.fxo()[j] = base + (long long)rc.ox * S;
-    sl.fyo()[j] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
+    // RK == 1: the record's own term; RK > 1: the CF's RK terms at sep_off[cf RK + t]
+#pragma unroll
+    for (int t = 0; t < RK; ++t) {
+      const long long base = a.sep_off[a.cf_shift + (RK == 1 ? rc.cf : rc.cf * RK + t)];
+      sl.fxo()[j * RK + t] = base + (long long)rc.ox * S;
+      sl.fyo()[j * RK + t] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
+    }
     sl.pack()[j] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | ((rc.p0x % S) << 16) | ((rc.p0y % S) << 24);
     if constexpr (std::is_same<Args, DegridArgs>::value)   // the output row of this record
       sl.src()[j] = a.rank > 1 ? rc.src * a.rank + rc.cf % a.rank : rc.src;
@@ -137,18 +146,20 @@ __device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, in
 
 // Asynchronous copies of a chunk's factor rows (all threads) and, when vis != NULL, its
 // visibilities and weights (threads < nst).
-template <int SMAX, int TILE, int P, int ST, int NT>
+template <int SMAX, int TILE, int P, int ST, int NT, int RK>
 __device__ __forceinline__ void stage_payload(const float* sep, const float* vis, const float* weight, int nst, int S,
-                                              const SepSlot<SMAX, TILE, P, ST>& sl, int vstride = P, int voff = 0) {
+                                              const SepSlot<SMAX, TILE, P, ST, RK>& sl, int vstride = P,
+                                              int voff = 0) {
   const float2* sep2 = reinterpret_cast<const float2*>(sep);
   const long long* fxo = sl.fxo();
   const long long* fyo = sl.fyo();
   float2* f = sl.f();
-  for (int i = threadIdx.x; i < nst * 2 * S; i += NT) {
-    const int j = i / (2 * S), r = i - j * 2 * S;
+  // row 2 t of sample j holds fx of term t, row 2 t + 1 its fy
+  for (int i = threadIdx.x; i < nst * 2 * RK * S; i += NT) {
+    const int jt = i / (2 * S), r = i - jt * 2 * S;   // jt = j RK + t
     const bool isx = r < S;
-    const long long srcidx = isx ? fxo[j] + r : fyo[j] + (r - S);
-    cp_async(f + (j * 2 + (isx ? 0 : 1)) * SMAX + (isx ? r : r - S), sep2 + srcidx, 8);
+    const long long srcidx = isx ? fxo[jt] + r : fyo[jt] + (r - S);
+    cp_async(f + (jt * 2 + (isx ? 0 : 1)) * SMAX + (isx ? r : r - S), sep2 + srcidx, 8);
   }
   if (vis != nullptr && (int)threadIdx.x < nst) {
     const int j = threadIdx.x;
@@ -232,12 +243,38 @@ struct RowState {
 // alpha[j][rx][p] = conj(fx[j][(rx - mx_j) mod S]) * w_jp V_jp (* phasor): formed once per
 // chunk for every (sample, column residue) instead of by each of the G threads of a column.  The
 // threads below nst also add the chunk's weights to the sum of weights (term 0 of each sample).
-template <int SMAX, int TILE, int P, int ST, int NT>
-__device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P, ST>& sl, float2* alpha, int nst, int S,
+template <int SMAX, int TILE, int P, int ST, int NT, int RK>
+__device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P, ST, RK>& sl, float2* alpha, int nst, int S,
                                            int rank, double (&wsum)[P]) {
   if ((int)threadIdx.x < nst && (rank == 1 || sl.rec()[threadIdx.x].cf % rank == 0)) {
 #pragma unroll
     for (int p = 0; p < P; ++p) wsum[p] += (double)sl.w()[threadIdx.x * P + p];
+  }
+  if constexpr (RK > 1) {
+    // fused terms: w V (* phasor) per sample into the slot's a(), conj(fx_t) per column residue
+    if ((int)threadIdx.x < nst) {
+      const int j = threadIdx.x;
+      const float2 ph = sl.ph()[j];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float wv = sl.w()[j * P + p];
+        const float2 v = sl.v()[j * P + p];
+        const float xr = wv * v.x, xi = wv * v.y;
+        sl.a()[j * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
+      }
+    }
+    for (int i = threadIdx.x; i < nst * S; i += NT) {
+      const int j = i / S, rx = i - j * S;
+      const int mx = (sl.pack()[j] >> 16) & 0xff;
+      int tx = rx - mx;
+      tx += (tx < 0) ? S : 0;
+#pragma unroll
+      for (int t = 0; t < RK; ++t) {
+        const float2 fxv = sl.f()[(j * 2 * RK + 2 * t) * SMAX + tx];
+        alpha[(j * SMAX + rx) * RK + t] = make_float2(fxv.x, -fxv.y);
+      }
+    }
+    return;
   }
   for (int i = threadIdx.x; i < nst * S; i += NT) {
     const int j = i / S, rx = i - j * S;
@@ -258,25 +295,26 @@ __device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P, ST>& sl,
 }
 
 // beta[j][rx] = fx[j][(rx - mx_j) mod S] for the degridding kernel.
-template <int SMAX, int TILE, int P, int ST, int NT>
-__device__ __forceinline__ void form_beta(const SepSlot<SMAX, TILE, P, ST>& sl, float2* beta, int nst, int S) {
+template <int SMAX, int TILE, int P, int ST, int NT, int RK>
+__device__ __forceinline__ void form_beta(const SepSlot<SMAX, TILE, P, ST, RK>& sl, float2* beta, int nst, int S) {
   for (int i = threadIdx.x; i < nst * S; i += NT) {
     const int j = i / S, rx = i - j * S;
     const int mx = (sl.pack()[j] >> 16) & 0xff;
     int tx = rx - mx;
     tx += (tx < 0) ? S : 0;
-    beta[j * SMAX + rx] = sl.f()[(j * 2) * SMAX + tx];
+#pragma unroll
+    for (int t = 0; t < RK; ++t) beta[(j * SMAX + rx) * RK + t] = sl.f()[(j * 2 * RK + 2 * t) * SMAX + tx];
   }
 }
 
-template <int SMIN, int SMAX, int NT, int TILE, int P, int ST>
-__global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST>::bytes, NT))
+template <int SMIN, int SMAX, int NT, int TILE, int P, int ST, int RK = 1>
+__global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST, RK>::bytes, NT, RK > 1 ? 128 : 96))
     k_grid_sep(const GridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
-  using Slot = SepSlot<SMAX, TILE, P, ST>;
+  using Slot = SepSlot<SMAX, TILE, P, ST, RK>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
-  float2* alpha = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST>::al_off);
+  float2* alpha = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST, RK>::al_off);
   __shared__ int s_item;
   __shared__ double s_wsum[NT / 32][P];
   static_assert(NT % 32 == 0, "the warp reductions need whole warps");
@@ -320,11 +358,11 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       derive(a, nst_of(0), S, X0, Y0, s0);
       if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
       __syncthreads();
-      stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(0), S, s0, a.vstride, a.voff);
+      stage_payload<SMAX, TILE, P, ST, NT, RK>(a.sep, a.vis, a.weight, nst_of(0), S, s0, a.vstride, a.voff);
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      form_alpha<SMAX, TILE, P, ST, NT>(s0, alpha, nst_of(0), S, a.rank, wsum);
+      form_alpha<SMAX, TILE, P, ST, NT, RK>(s0, alpha, nst_of(0), S, a.rank, wsum);
       __syncthreads();
     }
 
@@ -343,15 +381,22 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     }
     for (int c = 0; c < nch; ++c) {
       const Slot A(smem, c & 1), B(smem, (c & 1) ^ 1);
-      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT>(a.sep, a.vis, a.weight, nst_of(c + 1), S, B, a.vstride, a.voff);
+      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT, RK>(a.sep, a.vis, a.weight, nst_of(c + 1), S, B, a.vstride, a.voff);
       if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
       cp_async_commit();
       const int nst = nst_of(c);
       if (active) {
         for (int j = 0; j < nst; ++j) {
           const int pk = A.pack()[j];
-          float2 al[P];
-          load_pols<P>(alpha + (j * SMAX + rx) * P, al);
+          // RK == 1: al = alpha_p = conj(fx) w V_p; RK > 1: bt_t = conj(fx_t), wv_p = w V_p
+          float2 al[RK > 1 ? RK : P];
+          float2 wv[P];
+          if constexpr (RK == 1) {
+            load_pols<P>(alpha + (j * SMAX + rx) * P, al);
+          } else {
+            load_pols<RK>(alpha + (j * SMAX + rx) * RK, al);
+            load_pols<P>(A.a() + j * P, wv);
+          }
           if (pk != prev_pk) {   // the first tap moved (the same test in every thread of the CTA)
             prev_pk = pk;
             const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
@@ -385,15 +430,37 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
               curX = X;
             }
           }
-          const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
+          if constexpr (RK == 1) {
+            const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
 #pragma unroll
-          for (int k = 0; k < R; ++k) {
-            if (vmask & (1u << k)) {
-              const float2 f = fyrow[rs.ty[k]];
+            for (int k = 0; k < R; ++k) {
+              if (vmask & (1u << k)) {
+                const float2 f = fyrow[rs.ty[k]];
 #pragma unroll
-              for (int p = 0; p < P; ++p) {   // acc += conj(fy) alpha
-                acc[k][p].x = fmaf(f.x, al[p].x, fmaf(f.y, al[p].y, acc[k][p].x));
-                acc[k][p].y = fmaf(f.x, al[p].y, fmaf(-f.y, al[p].x, acc[k][p].y));
+                for (int p = 0; p < P; ++p) {   // acc += conj(fy) alpha
+                  acc[k][p].x = fmaf(f.x, al[p].x, fmaf(f.y, al[p].y, acc[k][p].x));
+                  acc[k][p].y = fmaf(f.x, al[p].y, fmaf(-f.y, al[p].x, acc[k][p].y));
+                }
+              }
+            }
+          } else {
+            const float2* frows = A.f() + (j * 2 * RK + 1) * SMAX;   // fy of term t at 2 t SMAX further
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+              if (vmask & (1u << k)) {
+                // c = conj(CF) at this tap = sum_t conj(fy_t) conj(fx_t)
+                float2 c = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < RK; ++t) {
+                  const float2 f = frows[2 * t * SMAX + rs.ty[k]];
+                  c.x = fmaf(f.x, al[t].x, fmaf(f.y, al[t].y, c.x));
+                  c.y = fmaf(f.x, al[t].y, fmaf(-f.y, al[t].x, c.y));
+                }
+#pragma unroll
+                for (int p = 0; p < P; ++p) {   // acc += c w V_p
+                  acc[k][p].x = fmaf(c.x, wv[p].x, fmaf(-c.y, wv[p].y, acc[k][p].x));
+                  acc[k][p].y = fmaf(c.x, wv[p].y, fmaf(c.y, wv[p].x, acc[k][p].y));
+                }
               }
             }
           }
@@ -403,7 +470,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       __syncthreads();
       // slot A is free: derive chunk c+2 into it; chunk c+1's payload has landed in B: form w V
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
-      if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT>(B, alpha, nst_of(c + 1), S, a.rank, wsum);
+      if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT, RK>(B, alpha, nst_of(c + 1), S, a.rank, wsum);
       __syncthreads();
     }
 #pragma unroll
@@ -454,8 +521,8 @@ struct DegridCache {
   static constexpr bool enabled = R * P * 2 <= 48;
 };
 
-template <int SMIN, int SMAX, int NT, int TILE, int P, int ST>
-__global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST>::bytes, NT))
+template <int SMIN, int SMAX, int NT, int TILE, int P, int ST, int RK = 1>
+__global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST, RK>::bytes, NT, RK > 1 ? 128 : 96))
     k_degrid_sep(const DegridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
   constexpr int NW = NT / 32;
@@ -463,10 +530,10 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
   constexpr int B = 32 / (2 * P);
   constexpr bool CACHE = DegridCache<R, P>::enabled;
   constexpr int RC = CACHE ? R : 1;
-  using Slot = SepSlot<SMAX, TILE, P, ST>;
+  using Slot = SepSlot<SMAX, TILE, P, ST, RK>;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
-  float2* beta = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST>::al_off);
+  float2* beta = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST, RK>::al_off);
   // per-warp butterfly results of every batch of the chunk; combined once per chunk
   constexpr int NB = (ST + B - 1) / B;          // batches per chunk
   constexpr int NBW = (NB + NW - 1) / NW;       // batches combined by one warp
@@ -515,11 +582,11 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       derive(a, nst_of(0), S, X0, Y0, s0);
       if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
       __syncthreads();
-      stage_payload<SMAX, TILE, P, ST, NT>(a.sep, nullptr, nullptr, nst_of(0), S, s0);
+      stage_payload<SMAX, TILE, P, ST, NT, RK>(a.sep, nullptr, nullptr, nst_of(0), S, s0);
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      form_beta<SMAX, TILE, P, ST, NT>(s0, beta, nst_of(0), S);
+      form_beta<SMAX, TILE, P, ST, NT, RK>(s0, beta, nst_of(0), S);
       __syncthreads();
     }
     RowState<R> rs;
@@ -536,7 +603,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
     for (int k = 0; k < RC; ++k) curY[k] = -1;
     for (int c = 0; c < nch; ++c) {
       const Slot A(smem, c & 1), Bs(smem, (c & 1) ^ 1);
-      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT>(a.sep, nullptr, nullptr, nst_of(c + 1), S, Bs);
+      if (c + 1 < nch) stage_payload<SMAX, TILE, P, ST, NT, RK>(a.sep, nullptr, nullptr, nst_of(c + 1), S, Bs);
       if (c + 2 < nch) stage_recs(a.rec, wi.start + (c + 2) * ST, nst_of(c + 2), A);
       cp_async_commit();
       const int nst = nst_of(c);
@@ -553,7 +620,11 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
           const int j = j0 + b;
           if (active && j < nst) {
             const int pk = A.pack()[j];
-            const float2 fxv = beta[j * SMAX + rx];
+            // RK == 1: fxv = fx[tx] applied after the rows; RK > 1: bt_t = fx_t[tx] inside each row
+            float2 bt[RK];
+            if constexpr (RK == 1) bt[0] = beta[j * SMAX + rx];
+            else load_pols<RK>(beta + (j * SMAX + rx) * RK, bt);
+            const float2 fxv = RK == 1 ? bt[0] : make_float2(1.f, 0.f);
             if (pk != prev_pk) {   // the first tap moved (the same test in every thread of the CTA)
               prev_pk = pk;
               const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
@@ -582,14 +653,25 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
                 }
               }
             }
-            const float2* fyrow = A.f() + (j * 2 + 1) * SMAX;
+            const float2* fyrow = A.f() + (j * 2 * RK + 1) * SMAX;   // fy of term t at 2 t SMAX further
             float2 part[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) part[p] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
               if (vmask & (1u << k)) {
-                const float2 f = fyrow[rs.ty[k]];
+                float2 f;
+                if constexpr (RK == 1) {
+                  f = fyrow[rs.ty[k]];
+                } else {   // the CF at this tap: sum_t fy_t fx_t
+                  f = make_float2(0.f, 0.f);
+#pragma unroll
+                  for (int t = 0; t < RK; ++t) {
+                    const float2 y = fyrow[2 * t * SMAX + rs.ty[k]];
+                    f.x = fmaf(y.x, bt[t].x, fmaf(-y.y, bt[t].y, f.x));
+                    f.y = fmaf(y.x, bt[t].y, fmaf(y.y, bt[t].x, f.y));
+                  }
+                }
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                   float2 gv;
@@ -602,8 +684,13 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-              vals[b * 2 * P + 2 * p] = fxv.x * part[p].x - fxv.y * part[p].y;
-              vals[b * 2 * P + 2 * p + 1] = fxv.x * part[p].y + fxv.y * part[p].x;
+              if constexpr (RK == 1) {
+                vals[b * 2 * P + 2 * p] = fxv.x * part[p].x - fxv.y * part[p].y;
+                vals[b * 2 * P + 2 * p + 1] = fxv.x * part[p].y + fxv.y * part[p].x;
+              } else {
+                vals[b * 2 * P + 2 * p] = part[p].x;
+                vals[b * 2 * P + 2 * p + 1] = part[p].y;
+              }
             }
           }
         }
@@ -660,7 +747,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
         }
       }
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
-      if (c + 1 < nch) form_beta<SMAX, TILE, P, ST, NT>(Bs, beta, nst_of(c + 1), S);
+      if (c + 1 < nch) form_beta<SMAX, TILE, P, ST, NT, RK>(Bs, beta, nst_of(c + 1), S);
       __syncthreads();
     }
   }
@@ -753,6 +840,67 @@ awg_status run_degrid_exact(const DegridArgs& a, int slot, int sms, cudaStream_t
   count_launches(1);
   return AWG_OK;
 }
+
+// Fused kernels for CF sets of RK = 2..4 outer-product terms on the exact supports (configuration
+// 0): the staging depth is halved until the layout fits shared memory.
+template <int S, int T, int P, int RK, int ST0>
+constexpr int fused_stage() {
+  if constexpr (SepLayout<S, T, P, ST0, RK>::bytes <= 227 * 1024 || ST0 <= 2) return ST0;
+  else return fused_stage<S, T, P, RK, ST0 / 2>();
+}
+
+template <int S, int P, int RK>
+awg_status run_grid_fused(const GridArgs& a, int slot, int sms, cudaStream_t st) {
+  constexpr ExactCfg e = exact_cfg(S, 0);
+  constexpr int nt = S * e.g_grid;
+  constexpr int stage = fused_stage<S, e.tile, P, RK, e.stage>();
+  using L = SepLayout<S, e.tile, P, stage, RK>;
+  static_assert(L::bytes <= 227 * 1024, "fused gridding window does not fit in shared memory");
+  auto kern = k_grid_sep<S - 1, S, nt, e.tile, P, stage, RK>;
+  static int bps = 0;
+  if (bps == 0) {
+    AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+    AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, nt, L::bytes));
+    if (bps < 1) return set_error(AWG_ERR_CUDA, "fused gridding kernel does not fit on an SM");
+  }
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, slot);
+  AWG_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return AWG_OK;
+}
+
+template <int S, int P, int RK>
+awg_status run_degrid_fused(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
+  constexpr ExactCfg e = exact_cfg(S, 0);
+  constexpr int nt = S * e.g_degrid;
+  constexpr int stage = fused_stage<S, e.tile, P, RK, e.stage>();
+  using L = SepLayout<S, e.tile, P, stage, RK>;
+  static_assert(L::bytes <= 227 * 1024, "fused degridding window does not fit in shared memory");
+  auto kern = k_degrid_sep<S - 1, S, nt, e.tile, P, stage, RK>;
+  static int bps = 0;
+  if (bps == 0) {
+    AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+    AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, nt, L::bytes));
+    if (bps < 1) return set_error(AWG_ERR_CUDA, "fused degridding kernel does not fit on an SM");
+  }
+  kern<<<sms * bps, nt, L::bytes, st>>>(a, slot);
+  AWG_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return AWG_OK;
+}
+
+#define AWG_FOR_FUSED(M, RK)                                                                                \
+  M(8, 1, RK) M(8, 2, RK) M(8, 4, RK) M(16, 1, RK) M(16, 2, RK) M(16, 4, RK) M(24, 1, RK) M(24, 2, RK)     \
+  M(24, 4, RK) M(32, 1, RK) M(32, 2, RK) M(32, 4, RK) M(40, 1, RK) M(40, 2, RK) M(40, 4, RK) M(48, 1, RK) \
+  M(48, 2, RK) M(48, 4, RK) M(56, 1, RK) M(56, 2, RK) M(56, 4, RK) M(64, 1, RK) M(64, 2, RK) M(64, 4, RK)
+#define AWG_DECLARE_GRID_FUSED(S, P, RK) \
+  extern template awg_status run_grid_fused<S, P, RK>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_DECLARE_DEGRID_FUSED(S, P, RK) \
+  extern template awg_status run_degrid_fused<S, P, RK>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_FUSED(S, P, RK) \
+  template awg_status run_grid_fused<S, P, RK>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_DEGRID_FUSED(S, P, RK) \
+  template awg_status run_degrid_fused<S, P, RK>(const DegridArgs&, int, int, cudaStream_t);
 
 #define AWG_FOR_EXACT_AND_POLS(M, C)                                                                        \
   M(8, 1, C) M(8, 2, C) M(8, 4, C) M(16, 1, C) M(16, 2, C) M(16, 4, C) M(24, 1, C) M(24, 2, C) M(24, 4, C)      \

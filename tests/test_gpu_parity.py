@@ -242,8 +242,8 @@ def test_mueller_full_polarisation_parity(awg):
     assert np.all(out.cpu().numpy().reshape(-1, 4)[~idx.valid] == 0)
 
 
-def _random_tables_case(awg, P, rank1, config=0):
-    sups = [1, 3, 7, 8, 9, 15, 16, 17, 24, 25, 31, 32, 33, 40, 48, 49, 56, 63, 64]
+def _random_tables_case(awg, P, rank1, config=0, terms=1, sups=None):
+    sups = sups or [1, 3, 7, 8, 9, 15, 16, 17, 24, 25, 31, 32, 33, 40, 48, 49, 56, 63, 64]
     wl = synth.make_workload("standard", n_int=16, n_chan=3, f_lo=2.8e9, f_hi=3.2e9, with_vis=False)
     N = 384
     OS = 3
@@ -257,8 +257,10 @@ def _random_tables_case(awg, P, rank1, config=0):
     flat = []
     for S in sups:
         if rank1:
-            # an outer product fy[oy][ty] fx[ox][tx]: stored as factors by the library
-            t = cplx(OS + 1, S)[:, None, :, None] * cplx(OS + 1, S)[None, :, None, :]
+            # a sum of `terms` outer products fy[oy][ty] fx[ox][tx]: stored as factors by the library
+            # (term k scaled by 0.3^k, so that the library's term-by-term fit separates them)
+            t = sum(0.3 ** k * cplx(OS + 1, S)[:, None, :, None] * cplx(OS + 1, S)[None, :, None, :]
+                    for k in range(terms))
         else:
             t = cplx(OS + 1, OS + 1, S, S)
         flat.append(t.astype(np.complex64).astype(np.complex128).reshape(-1))
@@ -276,6 +278,8 @@ def _random_tables_case(awg, P, rank1, config=0):
     cfset = awg.cf_set_create_from_table(sups, buf.astype(np.complex64), grid_n=N, cell_rad=op.cell_rad,
                                          oversampling=OS, n_pa_bins=len(sups), separable=True)
     assert cfset.separable == rank1
+    if rank1:
+        assert cfset.rank == terms
     if config:
         for S in sups:
             if S % 8 == 0:
@@ -308,6 +312,14 @@ def test_every_support_class_random_tables(awg, P):
     """Random (non-symmetric, full-rank) tables with supports 1..64 spread over all kernel classes;
     CF chosen per row through the PA-bin index.  Also checks <G V, X> = <V, D X> on the GPU."""
     _random_tables_case(awg, P, rank1=False)
+
+
+@pytest.mark.parametrize("terms", [2, 3, 4])
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_fused_kernels_random_low_rank_tables(awg, P, terms):
+    """Random tables of 2, 3 and 4 outer-product terms on the exact supports: the fused kernels
+    (one record per sample, the CF formed per tap from its terms) against the oracle."""
+    _random_tables_case(awg, P, rank1=True, terms=terms, sups=[8, 16, 24, 32, 40, 48, 56, 64])
 
 
 @pytest.mark.parametrize("config", [0, 1])
