@@ -168,9 +168,12 @@ def csrc_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(op: str):
+def measured_traffic(op: str, variant: bool = False):
     """DRAM bytes per full-size launch of `op` from the committed ncu summary, or None when the
-    kernels have changed since the counters were taken."""
+    kernels have changed since the counters were taken or the step is a variant of the workload
+    (mosaic phases, full polarisation) that the counters were not taken on."""
+    if variant:
+        return None
     try:
         with open(os.path.join(ROOT, "profiles", f"dram_traffic_{CONFIG}.json")) as f:
             rec = json.load(f)
@@ -806,7 +809,7 @@ def main():
         "ops": ops,
         "roofline": {"bound": "alu", "kernel": f"{dom}_visibilities (all supports)", "achieved": achieved,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
-                     "traffic": measured_traffic(dom),
+                     "traffic": measured_traffic(dom, args.mosaic or args.full_pol),
                      "peak_basis": "measured: sustained FP32 FMA rate of awg_fp32_fma_probe "
                                    f"({fma['launches']} launches of {fma['launch_ms']:.0f} ms)",
                      "peak_burst": fma["burst_tflops"],
@@ -817,8 +820,12 @@ def main():
         "e2e": e2e,
     }
     if cf.separable and cf.rank > 1:
-        # the kernels run one rank-1 record per (sample, term): rank x the method's arithmetic
-        line["executed_tflops"] = {k: max(cf.rank, 1) * ops[k]["tflops"] for k in ops}
+        # fused kernels form each tap's CF value from its terms (4 FMA per term) and apply it to the
+        # P pols (4 FMA per pol): (terms + P) / P x the method's arithmetic; otherwise one rank-1
+        # record runs per (sample, term): terms x
+        pp = 1 if args.full_pol else P
+        mult = (cf.fused_terms + pp) / pp if cf.fused_terms else cf.rank
+        line["executed_tflops"] = {k: mult * ops[k]["tflops"] for k in ops}
     if not args.no_cpu_baseline and CONFIG == "wproj":
         host_wl = dataclasses.replace(wl, vis=vis.cpu().numpy(), weight=wt.cpu().numpy())
         cb = run_cpu_baseline(host_wl, args.cpu_sample_every or 40)

@@ -139,6 +139,13 @@ awg_status cf_set_destroy(awg_cf_set cf);
  * outer-product terms per CF, or 0 for full tables. */
 awg_status cf_set_info(awg_cf_set cf, int32_t* n_cf, int64_t* n_values, int32_t* separable);
 
+/* Outer-product terms that the gridding and degridding kernels combine per tap: RK in [2, 4] when
+ * every CF of a factored single-pol set has RK terms and every support has a compiled kernel, so
+ * that a plan holds one record per sample and each tap's CF value is formed from the RK terms in
+ * registers; 0 otherwise (rank 1, full tables, full polarisation, or a set whose plans hold one
+ * record per sample and term).  terms: host. */
+awg_status cf_set_fused_terms(awg_cf_set cf, int32_t* terms);
+
 /*
  * Per-support autotuner of the separable kernels (a project addition; the paper fixes no kernel
  * shapes).  Every support of the W-projection schedule (8, 16, ..., 64) has two compiled kernel

@@ -107,8 +107,8 @@ def supports(p: CFParams) -> np.ndarray:
 def mueller_elements(p: CFParams):
     """Kept Mueller elements (p, q), row-major: the element of output product p = (a, b) and sky
     product q = (c, d) carries |d|^n with n = [a != c] + [b != d] leakage factors; it is kept when
-    that is at least the threshold (reading: the 'terms significant compared to the telescope
-    sensitivity' of the sparse Mueller matrix of CFs, Sec. 6)."""
+    that is at least the threshold (reading of Sec. 6, where the sparse Mueller matrix of CFs keeps
+    only the elements that matter at the instrument's sensitivity)."""
     dmag = abs(complex(p.leakage))
     out = []
     for pp in range(4):

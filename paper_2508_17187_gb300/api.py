@@ -58,6 +58,9 @@ class CFSet:
         self.n_values = int(n_val.value)
         self.rank = int(sep.value)            # outer-product terms per CF; 0 for full tables
         self.separable = self.rank > 0
+        fused = ctypes.c_int32()
+        check(_lib.load().cf_set_fused_terms(self._h, ctypes.byref(fused)), "cf_set_fused_terms")
+        self.fused_terms = int(fused.value)   # terms combined per tap by the kernels; 0 if not fused
 
     @property
     def handle(self):

@@ -530,6 +530,13 @@ awg_status cf_set_info(awg_cf_set h, int32_t* n_cf, int64_t* n_values, int32_t* 
   return AWG_OK;
 }
 
+awg_status cf_set_fused_terms(awg_cf_set h, int32_t* terms) {
+  if (!h || !terms) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  *terms = cf->fused;
+  return AWG_OK;
+}
+
 awg_status cf_set_get_supports(awg_cf_set h, int32_t* out) {
   if (!h || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
   CfSetImpl* cf = (CfSetImpl*)h;

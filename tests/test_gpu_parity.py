@@ -280,6 +280,7 @@ def _random_tables_case(awg, P, rank1, config=0, terms=1, sups=None):
     assert cfset.separable == rank1
     if rank1:
         assert cfset.rank == terms
+        assert cfset.fused_terms == (terms if terms > 1 and sups is not None else 0)
     if config:
         for S in sups:
             if S % 8 == 0:
