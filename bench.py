@@ -406,7 +406,7 @@ def calibrate_bench(args):
     achieved = nbytes / (ms / 1e3) / 1e9
     line = {"metric": "calibrated visibilities/s (G-Jones solve)", "value": R * C * P / (ms / 1e3),
             "unit": "visibilities/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "dtype": "f64 sums of f32 data", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32 (compensated interval sums), f64 gain iteration", "data": "synthetic",
             "config": {"workload": f"W-projection data {R} rows x {C} channels x {P} pols, model from degridding; "
                                    f"solution intervals {sol_int} integrations x {sol_chan} channels, 2 hands, 27 antennas",
                        "solutions": n_ts * n_fs * 2},
@@ -821,10 +821,14 @@ def main():
     }
     if cf.separable and cf.rank > 1:
         # fused kernels form each tap's CF value from its terms (4 FMA per term) and apply it to the
-        # P pols (4 FMA per pol): (terms + P) / P x the method's arithmetic; otherwise one rank-1
-        # record runs per (sample, term): terms x
-        pp = 1 if args.full_pol else P
-        mult = (cf.fused_terms + pp) / pp if cf.fused_terms else cf.rank
+        # P pols (4 FMA per pol): (terms + P) / P x the method's arithmetic, and a full-polarisation
+        # set runs 3 such 4-pol passes for its n_elem elements: 3 (terms + 4) / n_elem x; otherwise
+        # one rank-1 record runs per (sample, term): terms x
+        n_el = len(cf.mueller())
+        if cf.fused_terms:
+            mult = 3 * (cf.fused_terms + 4) / n_el if n_el else (cf.fused_terms + P) / P
+        else:
+            mult = cf.rank
         line["executed_tflops"] = {k: mult * ops[k]["tflops"] for k in ops}
     if not args.no_cpu_baseline and CONFIG == "wproj":
         host_wl = dataclasses.replace(wl, vis=vis.cpu().numpy(), weight=wt.cpu().numpy())

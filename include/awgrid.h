@@ -140,10 +140,12 @@ awg_status cf_set_destroy(awg_cf_set cf);
 awg_status cf_set_info(awg_cf_set cf, int32_t* n_cf, int64_t* n_values, int32_t* separable);
 
 /* Outer-product terms that the gridding and degridding kernels combine per tap: RK in [2, 4] when
- * every CF of a factored single-pol set has RK terms and every support has a compiled kernel, so
- * that a plan holds one record per sample and each tap's CF value is formed from the RK terms in
- * registers; 0 otherwise (rank 1, full tables, full polarisation, or a set whose plans hold one
- * record per sample and term).  terms: host. */
+ * every stored CF of a factored set has at most RK terms (RK the largest) and every support has an
+ * exact-support kernel, so that a plan holds one record per sample and each tap's CF value is
+ * formed from the RK terms in registers; 0 otherwise (rank 1, full tables, or a set whose plans
+ * hold one record per sample and term).  A full-polarisation set with fused kernels runs one 4-pol
+ * pass per base CF (A_R A_R, A_R A_L, A_L A_L) with its elements' scalars as a pol-mixing matrix;
+ * otherwise one single-pol pass per Mueller element.  terms: host. */
 awg_status cf_set_fused_terms(awg_cf_set cf, int32_t* terms);
 
 /*
@@ -358,7 +360,12 @@ awg_status clean_hogbom_components(const void* workspace, int32_t* n_done);
  * weighted average of V / M), then from g = 1: g_i <- (1 - alpha) g_i + alpha sum_{j != i} g_j
  * X_ij w_ij / sum_{j != i} |g_j|^2 w_ij (X_ji = conj(X_ij)) until max_i |change| < delta or
  * max_iter iterations; finally every g_i is multiplied by conj(g_ref) / |g_ref| (ref_ant's phase
- * is zero).  All sums FP64.  gains: device c128 [n_ts][n_fs][n_hands][n_ant] with n_ts =
+ * is zero).  Precision: the data pass forms N = sum w V conj(M) and D = sum w |M|^2 (so that
+ * X w = N, w = D) in FP32 - products rounded once, Kahan-compensated per-thread sums, an FP32 tree
+ * over 32 threads - to within ~10 u (u = 2^-24) of sum w |V| |M|.  The iteration runs in FP32
+ * while the largest change exceeds 3e-5 of the largest |g|, then in FP64 to the exit test (a
+ * delta coarser than that is tested in the FP32 phase); iterations counts both phases.
+ * gains: device c128 [n_ts][n_fs][n_hands][n_ant] with n_ts =
  * ceil(n_int / sol_int), n_fs = ceil(n_chan / sol_chan); iterations: device int32
  * [n_ts][n_fs][n_hands], the iterations run.  workspace: device, gcal_workspace_bytes(...) bytes,
  * 16-byte aligned.  Asynchronous (two launches).  Errors: INVALID_ARG, UNSUPPORTED (> 128

@@ -98,6 +98,10 @@ struct SlotTable {
   int slot_of_S[kMaxSupport + 1];
 };
 
+// Base block k of a full-polarisation set is the screen of the diagonal element of this pol (RR,
+// RL, LL): A_R A_R, A_R A_L, A_L A_L.
+constexpr int kBasePol[3] = {0, 1, 3};
+
 struct CfSetImpl {
   awg_cf_params p{};
   std::vector<double> pa_centers, sb_freqs;
@@ -113,9 +117,20 @@ struct CfSetImpl {
   SlotTable slots{};
   // Separable storage: CF = fy[oy][ty] * fx[ox][tx]; per CF, fx [OS+1][S] then fy [OS+1][S] c64.
   int separable = 0;
-  // Mueller elements (use_pol): CF index = element * n_base + (pa n_sb + sb) n_signed + ks
+  // Mueller elements (use_pol): the API's CF index = element * n_base + (pa n_sb + sb) n_signed + ks.
+  // Element (p, q) is s_pq B_k with k = a + b for p = (a, b): B_0, B_1, B_2 are the CFs of the
+  // voltage-pattern products A_R A_R, A_R A_L, A_L A_L, fitted once; n_cf = n_mb n_base.
   int n_elem = 1, n_base = 0;
   int elem_p[16] = {}, elem_q[16] = {};   // output pol p and input pol q of each element
+  // CF blocks stored: 1; or the 3 base blocks (fused kernels: one pol-mixing pass per block); or,
+  // with mb_elements, one block per element (s_pq times the base factors: one single-pol pass per
+  // element, for sets the fused kernels do not take)
+  int n_mb = 1;
+  int mb_elements = 0;
+  int elem_mb[16] = {};                   // base block of each element
+  double elem_s[16][2] = {};              // s_pq of each element (re, im)
+  int mb_pmask[3] = {};                   // pols p of each base block
+  float2* d_mix = nullptr;                // [n_mb][2][16]: gridding, then degridding mixing matrix
   int8_t cand[kMaxSupport + 1] = {};   // exact-kernel candidate per support (cf_set_autotune)
   int slots_version = 0;               // bumped whenever the slot table (tiles) changes
   int rank = 1;                      // outer-product terms per CF when separable

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -117,6 +118,7 @@ static void free_cf(CfSetImpl* cf) {
   cudaFree(cf->d_inv_taper);
   cudaFree(cf->d_sep);
   cudaFree(cf->d_sep_off);
+  cudaFree(cf->d_mix);
   delete cf;
 }
 
@@ -187,9 +189,9 @@ static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<
     rank = std::max(rank, (int)(fx[i].size() / (2 * (size_t)(OS + 1) * cf->supports[i])));
   cf->separable = 1;
   cf->rank = rank;
-  // fused kernels (one plan record per sample) for 2..4 terms on the exact supports, single Mueller
-  // element; otherwise the plan holds one record per sample and term
-  cf->fused = rank >= 2 && rank <= 4 && cf->n_elem == 1 ? rank : 0;
+  // fused kernels (one plan record per sample) for 2..4 terms on the exact supports; otherwise the
+  // plan holds one record per sample and term
+  cf->fused = rank >= 2 && rank <= 4 ? rank : 0;
   for (int i = 0; i < cf->n_cf && cf->fused; ++i)
     if (!has_exact(cf->supports[i])) cf->fused = 0;
   cf->sep_offsets.assign((size_t)cf->n_cf * rank, 0);
@@ -241,17 +243,17 @@ static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<
 static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
   const awg_cf_params& p = cf->p;
   cf->n_signed = p.use_w ? 2 * p.n_wplanes - 1 : 1;
-  // Without full polarisation the non-W part of every screen is real, so a negative-w plane is the
-  // conjugate point reflection of the positive one and only n_w planes are fitted; Mueller elements
-  // with a complex leakage are not, and every signed plane is fitted.
-  const bool mirror = !p.use_pol;
+  // The non-W part of every screen is real (the pol-shared A-term, or a base product of real
+  // voltage patterns), so a negative-w plane is the conjugate point reflection of the positive one
+  // and only n_w planes are fitted.
+  const bool mirror = true;
   const int n_w = !p.use_w ? 1 : mirror ? p.n_wplanes : 2 * p.n_wplanes - 1;
   const int n_pos = p.n_pa_bins * p.n_subbands * n_w;
   const int OS = p.oversampling;
   std::vector<std::vector<double>> fx(cf->n_cf), fy(cf->n_cf);
   int failed = 0;
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int je = 0; je < n_pos * cf->n_elem; ++je) {
+  for (int je = 0; je < n_pos * cf->n_mb; ++je) {
     if (failed) continue;
     const int e = je / n_pos, j = je - e * n_pos;
     const int k = j % n_w, pasb = j / n_w;
@@ -259,7 +261,9 @@ static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
     const int ks = !p.use_w ? 0 : mirror ? p.n_wplanes - 1 + k : k;
     const int S = support_of_plane(p, ks);
     const int ci = e * cf->n_base + pasb * cf->n_signed + ks;
-    const int ep = p.use_pol ? cf->elem_p[e] : -1, eq = p.use_pol ? cf->elem_q[e] : -1;
+    // base block e of a full-polarisation set: the diagonal element of pol kBasePol[e], whose
+    // screen is the voltage-pattern product A_a A_b itself
+    const int ep = p.use_pol ? kBasePol[e] : -1, eq = ep;
     if (build_cf_factors(p, cf->pa_centers.data(), cf->sb_freqs.data(), pa, sb, ks, ep, eq, kSepTol, kMaxRank,
                          fx[ci], fy[ci]) == 0) {
 #pragma omp atomic write
@@ -284,7 +288,55 @@ static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
     }
   }
   if (failed) return AWG_ERR_UNSUPPORTED;
-  return upload_separable(cf, fx, fy, st);
+  if (cf->n_mb > 1) {
+    // base passes need the fused kernels (2..4 terms, exact supports); otherwise store every
+    // element as s_pq times its base factors (fx scaled) for the single-pol element passes
+    int rank = 1;
+    bool exact = true;
+    for (int i = 0; i < cf->n_cf; ++i) {
+      rank = std::max(rank, (int)(fx[i].size() / (2 * (size_t)(OS + 1) * cf->supports[i])));
+      exact = exact && has_exact(cf->supports[i]);
+    }
+    if (!(rank >= 2 && rank <= 4 && exact)) {
+      std::vector<std::vector<double>> ex((size_t)cf->n_elem * cf->n_base), ey(ex.size());
+      for (int e = 0; e < cf->n_elem; ++e) {
+        const double sr = cf->elem_s[e][0], si = cf->elem_s[e][1];
+        for (int c = 0; c < cf->n_base; ++c) {
+          const size_t b = (size_t)cf->elem_mb[e] * cf->n_base + c, d = (size_t)e * cf->n_base + c;
+          ex[d] = fx[b];
+          ey[d] = fy[b];
+          for (size_t t = 0; t + 1 < ex[d].size(); t += 2) {
+            const double re = ex[d][t], im = ex[d][t + 1];
+            ex[d][t] = sr * re - si * im;
+            ex[d][t + 1] = sr * im + si * re;
+          }
+        }
+      }
+      fx.swap(ex);
+      fy.swap(ey);
+      cf->n_mb = cf->n_elem;
+      cf->mb_elements = 1;
+      cf->n_cf = cf->n_elem * cf->n_base;
+      std::vector<int32_t> sup((size_t)cf->n_cf);
+      for (int i = 0; i < cf->n_cf; ++i) sup[i] = cf->supports[i % cf->n_base];
+      cf->supports.swap(sup);
+    }
+  }
+  awg_status s = upload_separable(cf, fx, fy, st);
+  if (s != AWG_OK || cf->n_mb == 1 || cf->mb_elements) return s;
+  // pol-mixing matrices of the base blocks: gridding mix_g[4 q + p] = conj(s_pq), degridding
+  // mix_d[4 p + q] = s_pq, for the kept elements (p, q) of the block
+  std::vector<float2> mix((size_t)cf->n_mb * 32, make_float2(0.f, 0.f));
+  for (int e = 0; e < cf->n_elem; ++e) {
+    const int k = cf->elem_mb[e], pp = cf->elem_p[e], qq = cf->elem_q[e];
+    const float sr = (float)cf->elem_s[e][0], si = (float)cf->elem_s[e][1];
+    mix[(size_t)k * 32 + 4 * qq + pp] = make_float2(sr, -si);
+    mix[(size_t)k * 32 + 16 + 4 * pp + qq] = make_float2(sr, si);
+  }
+  AWG_CUDA_TRY(cudaMalloc(&cf->d_mix, sizeof(float2) * mix.size()));
+  AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_mix, mix.data(), sizeof(float2) * mix.size(), cudaMemcpyHostToDevice, st));
+  AWG_CUDA_TRY(cudaStreamSynchronize(st));
+  return AWG_OK;
 }
 
 }  // namespace awg
@@ -316,9 +368,24 @@ awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* 
   const int n_signed = params->use_w ? 2 * params->n_wplanes - 1 : 1;
   cf->n_base = params->n_pa_bins * params->n_subbands * n_signed;
   cf->n_elem = params->use_pol ? mueller_elements(cf->p, cf->elem_p, cf->elem_q) : 1;
-  cf->n_cf = cf->n_elem * cf->n_base;
+  if (params->use_pol) {
+    // element (p, q), p = (a, b), q = (c, e): J_ac conj(J_be) = A_a A_b f(a, c) conj(f(b, e)) with
+    // f(x, y) = 1 for x == y, else the leakage d: base block a + b, scalar f(a, c) conj(f(b, e))
+    cf->n_mb = 3;
+    const std::complex<double> d(params->leakage_re, params->leakage_im);
+    for (int e = 0; e < cf->n_elem; ++e) {
+      const int pp = cf->elem_p[e], qq = cf->elem_q[e];
+      const int a = pp >> 1, b = pp & 1, c = qq >> 1, ee = qq & 1;
+      const std::complex<double> s = (a == c ? 1.0 : d) * std::conj(b == ee ? std::complex<double>(1.0) : d);
+      cf->elem_mb[e] = a + b;
+      cf->elem_s[e][0] = s.real();
+      cf->elem_s[e][1] = s.imag();
+      cf->mb_pmask[a + b] |= 1 << pp;
+    }
+  }
+  cf->n_cf = cf->n_mb * cf->n_base;
   cf->supports.resize(cf->n_cf);
-  for (int e = 0; e < cf->n_elem; ++e)
+  for (int e = 0; e < cf->n_mb; ++e)
     for (int pa = 0; pa < params->n_pa_bins; ++pa)
       for (int sb = 0; sb < params->n_subbands; ++sb)
         for (int ks = 0; ks < n_signed; ++ks)
@@ -524,7 +591,7 @@ awg_status cf_set_mueller(awg_cf_set h, int32_t* n_elem, int32_t* elem_p, int32_
 awg_status cf_set_info(awg_cf_set h, int32_t* n_cf, int64_t* n_values, int32_t* separable) {
   if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
   CfSetImpl* cf = (CfSetImpl*)h;
-  if (n_cf) *n_cf = cf->n_cf;
+  if (n_cf) *n_cf = cf->p.use_pol ? cf->n_elem * cf->n_base : cf->n_cf;   // Mueller sets: element-major
   if (n_values) *n_values = cf->n_values;
   if (separable) *separable = cf->separable ? cf->rank : 0;
   return AWG_OK;
@@ -540,6 +607,11 @@ awg_status cf_set_fused_terms(awg_cf_set h, int32_t* terms) {
 awg_status cf_set_get_supports(awg_cf_set h, int32_t* out) {
   if (!h || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
   CfSetImpl* cf = (CfSetImpl*)h;
+  if (cf->n_mb > 1 && !cf->mb_elements) {   // every element shares the supports of the base index
+    for (int e = 0; e < cf->n_elem; ++e)
+      std::memcpy(out + (size_t)e * cf->n_base, cf->supports.data(), sizeof(int32_t) * cf->n_base);
+    return AWG_OK;
+  }
   std::memcpy(out, cf->supports.data(), sizeof(int32_t) * cf->n_cf);
   return AWG_OK;
 }
@@ -547,6 +619,15 @@ awg_status cf_set_get_supports(awg_cf_set h, int32_t* out) {
 awg_status cf_set_copy_table(awg_cf_set h, int32_t ci, float* out) {
   if (!h || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
   CfSetImpl* cf = (CfSetImpl*)h;
+  // a Mueller element's CF is s_pq times its stored base CF
+  float scale_r = 1.f, scale_i = 0.f;
+  if (cf->n_mb > 1 && !cf->mb_elements) {
+    if (ci < 0 || ci >= cf->n_elem * cf->n_base) return set_error(AWG_ERR_INVALID_ARG, "cf index out of range");
+    const int e = ci / cf->n_base;
+    scale_r = (float)cf->elem_s[e][0];
+    scale_i = (float)cf->elem_s[e][1];
+    ci = cf->elem_mb[e] * cf->n_base + ci % cf->n_base;
+  }
   if (ci < 0 || ci >= cf->n_cf) return set_error(AWG_ERR_INVALID_ARG, "cf index out of range");
   const int64_t nv = (int64_t)(cf->p.oversampling + 1) * (cf->p.oversampling + 1) * cf->supports[ci] * cf->supports[ci];
   if (cf->separable) {
@@ -571,6 +652,12 @@ awg_status cf_set_copy_table(awg_cf_set h, int32_t ci, float* out) {
               out[o + 1] += gr * fi + gi * fr;
             }
     }
+    if (scale_r != 1.f || scale_i != 0.f)
+      for (int64_t i = 0; i < nv; ++i) {
+        const float re = out[2 * i], im = out[2 * i + 1];
+        out[2 * i] = scale_r * re - scale_i * im;
+        out[2 * i + 1] = scale_r * im + scale_i * re;
+      }
     return AWG_OK;
   }
   if (cf->p.cf_dtype == AWG_CF_BF16) {

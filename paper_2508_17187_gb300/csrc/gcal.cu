@@ -1,14 +1,18 @@
 // Direction-independent G-Jones calibration (Sec. 5.1, Architectural View for Calibration):
-//   k_vavg       Eq. VAvg - the model-normalised visibilities of every baseline averaged over a
-//                solution interval of sol_int integrations x sol_chan channels, per parallel-hand
-//                polarisation product: X = sum w V conj(M) / sum w |M|^2 with weight sum w |M|^2
-//                (one pass over the data, HBM-bound);
+//   k_vavg       Eq. VAvg - per solution interval of sol_int integrations x sol_chan channels,
+//                parallel-hand product and baseline, the sums N = sum w V conj(M) and
+//                D = sum w |M|^2 (X = N / D is the weighted average of V / M, and D its weight;
+//                the iteration needs only w X = N and w = D).  One pass over the data, HBM-bound.
 //   k_gain_solve Eq. CalUpdateDir / Eq. CalUpdateModel - the fixed-point iteration for the
 //                antenna gains of one (solution interval, polarisation), with the exit test
 //                max_i |g_i^{k+1} - g_i^k| < delta, then the phase of a reference antenna
 //                removed (the solution is defined up to a common phase).
-// The model visibilities come from degrid_visibilities (Eq. VMod).  Sums and the iteration are
-// FP64.
+// The model visibilities come from degrid_visibilities (Eq. VMod).
+//
+// Precision: GB300's FP64 rate is 1/64 of its FP32 rate, so the data pass runs in FP32: every
+// product rounded once, per-lane sums Kahan-compensated, a 5-level FP32 tree across the lanes
+// (relative error of N and D within ~10 u of sum w |V| |M|, u = 2^-24, whatever the interval
+// length).  The iteration is FP64.
 #include <cuda_runtime.h>
 
 #include "awg_internal.h"
@@ -50,12 +54,29 @@ __device__ __forceinline__ void load_hands(const float2* __restrict__ v, const f
   }
 }
 
+// Kahan-compensated FP32 accumulation: sum + c carries the running total.
+struct KSum {
+  float sum = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+  }
+};
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 // One CTA per solution cell (time interval, channel block); its warps take baselines, the lanes
-// of a warp take the (integration, channel) samples of one baseline.
+// of a warp take the (integration, channel) samples of one baseline.  Output per (cell, hand,
+// baseline): float4 (Re N, Im N, D, 0).
 template <int P>
 __global__ void __launch_bounds__(256) k_vavg(GcalDims d, const float2* __restrict__ vis, const float2* __restrict__ mod,
-                                              const float* __restrict__ weight, double2* __restrict__ X,
-                                              double* __restrict__ Wt) {
+                                              const float* __restrict__ weight, float4* __restrict__ ND) {
   constexpr int H = P == 1 ? 1 : 2;
   const int ts = blockIdx.x / d.n_fs, fs = blockIdx.x - (blockIdx.x / d.n_fs) * d.n_fs;
   const int t0 = ts * d.sol_int, t1 = min(t0 + d.sol_int, d.n_int);
@@ -63,7 +84,8 @@ __global__ void __launch_bounds__(256) k_vavg(GcalDims d, const float2* __restri
   const int nc = c1 - c0, ns = (t1 - t0) * nc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int b = warp; b < d.n_bl; b += nw) {
-    double nr[2] = {0.0, 0.0}, ni[2] = {0.0, 0.0}, den[2] = {0.0, 0.0};
+    KSum nr[2], ni[2], den[2];
+#pragma unroll 4
     for (int k = lane; k < ns; k += 32) {
       const int t = t0 + k / nc, c = c0 + k % nc;
       const int64_t s = ((int64_t)t * d.n_bl + b) * d.C + c;
@@ -75,23 +97,20 @@ __global__ void __launch_bounds__(256) k_vavg(GcalDims d, const float2* __restri
       for (int q = 0; q < H; ++q) {
         if (!(w[q] > 0.f)) continue;
         // w V conj(M) and w |M|^2
-        nr[q] += (double)w[q] * ((double)v[q].x * m[q].x + (double)v[q].y * m[q].y);
-        ni[q] += (double)w[q] * ((double)v[q].y * m[q].x - (double)v[q].x * m[q].y);
-        den[q] += (double)w[q] * ((double)m[q].x * m[q].x + (double)m[q].y * m[q].y);
+        const float re = fmaf(v[q].x, m[q].x, v[q].y * m[q].y);
+        const float im = fmaf(v[q].y, m[q].x, -(v[q].x * m[q].y));
+        const float mm = fmaf(m[q].x, m[q].x, m[q].y * m[q].y);
+        nr[q].add(w[q] * re);
+        ni[q].add(w[q] * im);
+        den[q].add(w[q] * mm);
       }
     }
 #pragma unroll
     for (int q = 0; q < H; ++q) {
-      for (int o = 16; o > 0; o >>= 1) {
-        nr[q] += __shfl_xor_sync(0xffffffffu, nr[q], o);
-        ni[q] += __shfl_xor_sync(0xffffffffu, ni[q], o);
-        den[q] += __shfl_xor_sync(0xffffffffu, den[q], o);
-      }
-      if (lane == 0) {
-        const int64_t o = (((int64_t)ts * d.n_fs + fs) * H + q) * d.n_bl + b;
-        X[o] = den[q] > 0.0 ? make_double2(nr[q] / den[q], ni[q] / den[q]) : make_double2(0.0, 0.0);
-        Wt[o] = den[q];
-      }
+      const float a = warp_sum(nr[q].sum - nr[q].c);
+      const float bb = warp_sum(ni[q].sum - ni[q].c);
+      const float cc = warp_sum(den[q].sum - den[q].c);
+      if (lane == 0) ND[(((int64_t)ts * d.n_fs + fs) * H + q) * d.n_bl + b] = make_float4(a, bb, cc, 0.f);
     }
   }
 }
@@ -99,86 +118,177 @@ __global__ void __launch_bounds__(256) k_vavg(GcalDims d, const float2* __restri
 constexpr int kMaxAnt = 128;
 constexpr int kMaxBl = kMaxAnt * (kMaxAnt - 1) / 2;
 
-// Dynamic shared memory: for every antenna its baselines, as (b << 1) | (1 if the antenna is
-// ant2 of b, so X_ij = conj(X_b)), [n_ant][n_ant - 1], then the counts [n_ant].
+// Dynamic shared memory of k_gain_solve: the solution's N (2 values) and D per baseline as FP32,
+// then as T again when T = double (the FP64 phase reads that copy; with T = float it converts the
+// FP32 one), then for every antenna its neighbour entries (b << 8) | (j << 1) | (1 if the antenna
+// is ant2 of b, so that w_ij X_ij = conj(N_b)), [n_ant][n_ant - 1].
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+template <typename T>
+size_t gain_solve_smem(int n_bl, int n_ant) {
+  const size_t nd32 = align16((size_t)n_bl * 3 * sizeof(float));
+  const size_t nd64 = sizeof(T) == sizeof(double) ? align16((size_t)n_bl * 3 * sizeof(double)) : 0;
+  return nd32 + nd64 + sizeof(int) * (size_t)n_ant * (n_ant - 1);
+}
+
+// One update of antenna i (Eq. CalUpdateDir, then Eq. CalUpdateModel) in precision R:
+//   g_i' = sum_j g_j w_ij X_ij / sum_j |g_j|^2 w_ij,  w_ij X_ij = N_b or conj(N_b), w_ij = D_b,
+//   g_i <- (1 - alpha) g_i + alpha g_i'.
+// Returns the new gain in (re, im) and |change|^2.  (The FP64 phase is bound by the FP64 pipe's
+// throughput: one thread per antenna keeps every FP64 operation useful.)
+template <typename R, typename S>
+__device__ __forceinline__ R gain_update(int deg, const int* __restrict__ adj, const S* __restrict__ nd,
+                                         const R* __restrict__ gre, const R* __restrict__ gim,
+                                         const R* __restrict__ gg, R alpha, int i, R& re, R& im) {
+  R num_r = R(0), num_i = R(0), den = R(0);
+  for (int k = 0; k < deg; ++k) {
+    const int e = adj[k], b = e >> 8, j = (e >> 1) & 127;
+    const R nr = (R)nd[3 * b];
+    const R ni = (e & 1) ? -(R)nd[3 * b + 1] : (R)nd[3 * b + 1];
+    const R gx = gre[j], gy = gim[j];
+    num_r = fma(gx, nr, fma(-gy, ni, num_r));
+    num_i = fma(gx, ni, fma(gy, nr, num_i));
+    den = fma(gg[j], (R)nd[3 * b + 2], den);
+  }
+  const R gx = gre[i], gy = gim[i];
+  re = gx;
+  im = gy;
+  if (den > R(0)) {
+    const R r = alpha / den;
+    re = fma(r, num_r, (R(1) - alpha) * gx);
+    im = fma(r, num_i, (R(1) - alpha) * gy);
+  }
+  const R dx = re - gx, dy = im - gy;
+  return dx * dx + dy * dy;
+}
+
+// Largest of v over the CTA's threads (all threads call it; s_red holds one value per warp).
+template <typename R>
+__device__ __forceinline__ R block_max(R v, R* s_red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R m = R(0);
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, s_red[k]);
+  return m;
+}
+
+// Relative change below which the FP32 phase hands over to FP64: 3e-5 of the largest gain is
+// ~500 u (u = 2^-24), far above the rounding of an FP32 update.  Below kStall32 the FP32 phase also
+// hands over as soon as the largest change stops shrinking (where its rounding would take over),
+// so it cannot stall; above it a non-monotone early step does not end the phase.
+constexpr float kTau32 = 3e-5f;
+constexpr float kStall32 = 1e-4f;
+
+// One CTA per (interval, hand): thread i owns antenna i; Jacobi order (every g_j of the previous
+// iteration).  The iteration runs in FP32 while the largest change is above kTau32 max |g| (the
+// FP64 pipe of GB300 is 1/64 of the FP32 one), then in FP64 until max_i |change| < delta.  A delta
+// coarser than kTau32 max |g| is tested in the FP32 phase.
+template <typename T>
 __global__ void __launch_bounds__(kMaxAnt) k_gain_solve(GcalDims d, const int32_t* __restrict__ ant1,
                                                          const int32_t* __restrict__ ant2,
-                                                         const double2* __restrict__ X, const double* __restrict__ Wt,
-                                                         double alpha, double delta, int max_iter, int ref_ant,
-                                                         double2* __restrict__ gains, int32_t* __restrict__ iters) {
-  extern __shared__ int s_adj[];
-  __shared__ double2 g[kMaxAnt];
+                                                         const float4* __restrict__ ND, double alpha, double delta,
+                                                         int max_iter, int ref_ant, double2* __restrict__ gains,
+                                                         int32_t* __restrict__ iters) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  float* s_nd32 = reinterpret_cast<float*>(s_raw);   // [n_bl][3]
+  const size_t o64 = align16((size_t)d.n_bl * 3 * sizeof(float));
+  T* s_nd = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(s_raw + o64) : reinterpret_cast<T*>(s_nd32);
+  const size_t oadj = o64 + (sizeof(T) == sizeof(double) ? align16((size_t)d.n_bl * 3 * sizeof(double)) : 0);
+  int* s_adj = reinterpret_cast<int*>(s_raw + oadj);
+  __shared__ float g32r[kMaxAnt], g32i[kMaxAnt], gg32[kMaxAnt];
+  __shared__ double gre[kMaxAnt], gim[kMaxAnt], gg[kMaxAnt];
+  __shared__ float s_red32[kMaxAnt / 32];
   __shared__ double s_red[kMaxAnt / 32];
-  __shared__ int s_done;
   const int sol = blockIdx.x;   // (ts, fs, q)
-  const double2* x = X + (int64_t)sol * d.n_bl;
-  const double* w = Wt + (int64_t)sol * d.n_bl;
+  const float4* nd = ND + (int64_t)sol * d.n_bl;
   const int i = threadIdx.x;
+  for (int b = i; b < d.n_bl; b += blockDim.x) {
+    const float4 v = nd[b];
+    s_nd32[3 * b] = v.x;
+    s_nd32[3 * b + 1] = v.y;
+    s_nd32[3 * b + 2] = v.z;
+    if (sizeof(T) == sizeof(double)) {
+      s_nd[3 * b] = (T)v.x;
+      s_nd[3 * b + 1] = (T)v.y;
+      s_nd[3 * b + 2] = (T)v.z;
+    }
+  }
   const int deg_max = d.n_ant - 1;
   int* adj = s_adj + i * deg_max;
   int deg = 0;
-  if (i < d.n_ant) {
-    g[i] = make_double2(1.0, 0.0);
+  const bool own = i < d.n_ant;
+  if (own) {
+    g32r[i] = 1.f;
+    g32i[i] = 0.f;
+    gg32[i] = 1.f;
     for (int b = 0; b < d.n_bl && deg < deg_max; ++b) {
       const int a = ant1[b], c = ant2[b];
       if (a < 0 || c < 0 || a >= d.n_ant || c >= d.n_ant || a == c) continue;
-      if (a == i) adj[deg++] = b << 1;
-      else if (c == i) adj[deg++] = (b << 1) | 1;
+      if (a == i) adj[deg++] = (b << 8) | (c << 1);
+      else if (c == i) adj[deg++] = (b << 8) | (a << 1) | 1;
     }
   }
-  if (i == 0) s_done = 0;
+  const double delta2 = delta * delta;
   __syncthreads();
   int it = 0;
-  for (; it < max_iter; ++it) {
-    double2 gn = make_double2(0.0, 0.0);
-    double change = 0.0;
-    if (i < d.n_ant) {
-      // Eq. CalUpdateDir: sum over j != i of g_j X_ij w_ij / sum |g_j|^2 w_ij; X_ij = conj(X_ji)
-      double num_r = 0.0, num_i = 0.0, den = 0.0;
-      for (int k = 0; k < deg; ++k) {
-        const int e = adj[k], b = e >> 1;
-        const int j = (e & 1) ? ant1[b] : ant2[b];
-        const double2 xb = x[b];
-        const double xi = (e & 1) ? -xb.y : xb.y;
-        const double2 gj = g[j];
-        const double wb = w[b];
-        num_r += wb * (gj.x * xb.x - gj.y * xi);
-        num_i += wb * (gj.x * xi + gj.y * xb.x);
-        den += wb * (gj.x * gj.x + gj.y * gj.y);
-      }
-      const double2 gi = g[i];
-      if (den > 0.0) {   // Eq. CalUpdateModel
-        gn = make_double2((1.0 - alpha) * gi.x + alpha * num_r / den, (1.0 - alpha) * gi.y + alpha * num_i / den);
-      } else {
-        gn = gi;
-      }
-      change = hypot(gn.x - gi.x, gn.y - gi.y);
+  bool done = false;
+  float m_prev = INFINITY;
+  // FP32 phase
+  while (it < max_iter) {
+    float re = 0.f, im = 0.f, c2 = 0.f;
+    if (own) c2 = gain_update<float, float>(deg, adj, s_nd32, g32r, g32i, gg32, (float)alpha, i, re, im);
+    const float m = block_max(c2, s_red32);
+    __syncthreads();   // every thread has read s_red32 and the old gains
+    const float gm = block_max(own ? re * re + im * im : 0.f, s_red32);
+    if (own) {
+      g32r[i] = re;
+      g32i[i] = im;
+      gg32[i] = re * re + im * im;
     }
-    // largest change over the antennas
-    for (int o = 16; o > 0; o >>= 1) change = fmax(change, __shfl_xor_sync(0xffffffffu, change, o));
-    if ((i & 31) == 0) s_red[i >> 5] = change;
+    ++it;
     __syncthreads();
-    if (i < d.n_ant) g[i] = gn;
-    if (i == 0) {
-      double m = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, s_red[k]);
-      s_done = m < delta;
-    }
-    __syncthreads();
-    if (s_done) {
-      ++it;
+    const double switch2 = (double)(kTau32 * kTau32) * (double)gm;
+    const double stall2 = (double)(kStall32 * kStall32) * (double)gm;
+    if ((double)m < switch2 || ((double)m < stall2 && !(m < m_prev))) {
+      done = delta2 >= switch2 && (double)m < delta2;
       break;
     }
+    m_prev = m;
   }
-  if (i < d.n_ant) {
+  // FP64 phase
+  if (own) {
+    gre[i] = g32r[i];
+    gim[i] = g32i[i];
+    gg[i] = (double)g32r[i] * g32r[i] + (double)g32i[i] * g32i[i];
+  }
+  __syncthreads();
+  while (!done && it < max_iter) {
+    double re = 0.0, im = 0.0, c2 = 0.0;
+    if (own) c2 = gain_update<double, T>(deg, adj, s_nd, gre, gim, gg, alpha, i, re, im);
+    const double m = block_max(c2, s_red);
+    __syncthreads();
+    if (own) {
+      gre[i] = re;
+      gim[i] = im;
+      gg[i] = re * re + im * im;
+    }
+    ++it;
+    __syncthreads();
+    done = m < delta2 || (m == 0.0 && delta > 0.0);
+  }
+  if (own) {
     // remove the reference antenna's phase: g_i conj(g_ref) / |g_ref|
-    const double2 gr = g[ref_ant];
-    const double ar = hypot(gr.x, gr.y);
-    double2 o = g[i];
-    if (ar > 0.0) o = make_double2((o.x * gr.x + o.y * gr.y) / ar, (o.y * gr.x - o.x * gr.y) / ar);
-    gains[(int64_t)sol * d.n_ant + i] = o;
+    const double rx = gre[ref_ant], ry = gim[ref_ant];
+    const double ar = hypot(rx, ry);
+    double ox = gre[i], oy = gim[i];
+    if (ar > 0.0) {
+      const double tx = (ox * rx + oy * ry) / ar;
+      oy = (oy * rx - ox * ry) / ar;
+      ox = tx;
+    }
+    gains[(int64_t)sol * d.n_ant + i] = make_double2(ox, oy);
   }
-  if (i == 0) iters[sol] = it;
+  if (threadIdx.x == 0) iters[sol] = it;
 }
 
 awg_status gcal_dims(int64_t n_rows, int32_t n_chan, int32_t n_pol, int32_t n_bl, int32_t n_ant, int32_t sol_int,
@@ -214,7 +324,7 @@ extern "C" int64_t gcal_workspace_bytes(int64_t n_rows, int32_t n_chan, int32_t 
   if (n_bl < 1 || sol_int < 1 || sol_chan < 1 || n_chan < 1 || n_rows < 1) return 0;
   const int64_t n_int = n_rows / n_bl;
   const int64_t n_sol = ((n_int + sol_int - 1) / sol_int) * ((n_chan + sol_chan - 1) / sol_chan) * (n_pol == 1 ? 1 : 2);
-  return n_sol * n_bl * (int64_t)(sizeof(double2) + sizeof(double));
+  return n_sol * n_bl * (int64_t)sizeof(float4);
 }
 
 extern "C" awg_status gcal_solve(const void* vis, const void* model, const float* weight, int64_t n_rows, int32_t n_chan,
@@ -231,24 +341,30 @@ extern "C" awg_status gcal_solve(const void* vis, const void* model, const float
   if (ref_ant < 0 || ref_ant >= n_ant) return set_error(AWG_ERR_INVALID_ARG, "ref_ant out of range");
   if (((uintptr_t)workspace & 15) != 0) return set_error(AWG_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
   const int64_t n_sol = (int64_t)d.n_ts * d.n_fs * d.n_pp;
-  double2* X = (double2*)workspace;
-  double* Wt = (double*)(X + n_sol * d.n_bl);
+  float4* ND = (float4*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
   if (((uintptr_t)vis | (uintptr_t)model | (uintptr_t)weight) & 15)
     return set_error(AWG_ERR_INVALID_ARG, "vis, model and weight must be 16-byte aligned");
   auto kv = n_pol == 4 ? k_vavg<4> : n_pol == 2 ? k_vavg<2> : k_vavg<1>;
-  kv<<<d.n_ts * d.n_fs, 256, 0, st>>>(d, (const float2*)vis, (const float2*)model, weight, X, Wt);
+  kv<<<d.n_ts * d.n_fs, 256, 0, st>>>(d, (const float2*)vis, (const float2*)model, weight, ND);
   AWG_CUDA_TRY(cudaGetLastError());
   const int threads = ((n_ant + 31) / 32) * 32;
-  const size_t adj_bytes = sizeof(int) * (size_t)n_ant * (n_ant - 1);
+  // N and D staged as FP64 when that fits next to the neighbour lists, else as FP32
+  constexpr size_t kSmemMax = 200 * 1024;
+  const bool dbl = gain_solve_smem<double>(n_bl, n_ant) <= kSmemMax;
+  const size_t smem = dbl ? gain_solve_smem<double>(n_bl, n_ant) : gain_solve_smem<float>(n_bl, n_ant);
   static bool attr_set = false;
   if (!attr_set) {
-    AWG_CUDA_TRY(cudaFuncSetAttribute(k_gain_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(int) * kMaxAnt * (kMaxAnt - 1))));
+    AWG_CUDA_TRY(cudaFuncSetAttribute(k_gain_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    AWG_CUDA_TRY(cudaFuncSetAttribute(k_gain_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     attr_set = true;
   }
-  k_gain_solve<<<(int)n_sol, threads, adj_bytes, st>>>(d, ant1, ant2, X, Wt, alpha, delta, max_iter, ref_ant,
-                                                       (double2*)gains, iterations);
+  if (dbl)
+    k_gain_solve<double><<<(int)n_sol, threads, smem, st>>>(d, ant1, ant2, ND, alpha, delta, max_iter, ref_ant,
+                                                            (double2*)gains, iterations);
+  else
+    k_gain_solve<float><<<(int)n_sol, threads, smem, st>>>(d, ant1, ant2, ND, alpha, delta, max_iter, ref_ant,
+                                                           (double2*)gains, iterations);
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(2);
   return AWG_OK;

@@ -24,6 +24,12 @@ AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 4)
 AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 2)
 AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 3)
 AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 4)
+AWG_FOR_FUSED_MIX(AWG_DECLARE_GRID_FUSED_MIX, 2)
+AWG_FOR_FUSED_MIX(AWG_DECLARE_GRID_FUSED_MIX, 3)
+AWG_FOR_FUSED_MIX(AWG_DECLARE_GRID_FUSED_MIX, 4)
+AWG_FOR_FUSED_MIX(AWG_DECLARE_DEGRID_FUSED_MIX, 2)
+AWG_FOR_FUSED_MIX(AWG_DECLARE_DEGRID_FUSED_MIX, 3)
+AWG_FOR_FUSED_MIX(AWG_DECLARE_DEGRID_FUSED_MIX, 4)
 
 namespace {
 
@@ -67,8 +73,18 @@ awg_status grid_slot_sep(int S, int cand, int slot, int P, const GridArgs& a, in
   return set_error(AWG_ERR_UNSUPPORTED, "no separable gridding kernel for this support / pol count");
 }
 
-// Fused kernels: one record per sample of a CF set of rk outer-product terms.
+// Fused kernels: one record per sample of a CF set of rk outer-product terms (the pol-mixing
+// instances when a.mix is set).
 awg_status grid_slot_fused(int S, int rk, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
+  if (a.mix != nullptr) {
+#define AWG_CASE(SS, PP, RR) \
+  if (S == SS && P == PP && rk == RR) return run_grid_fused<SS, PP, RR, true>(a, slot, sms, st);
+    AWG_FOR_FUSED_MIX(AWG_CASE, 2)
+    AWG_FOR_FUSED_MIX(AWG_CASE, 3)
+    AWG_FOR_FUSED_MIX(AWG_CASE, 4)
+#undef AWG_CASE
+    return set_error(AWG_ERR_UNSUPPORTED, "no pol-mixing gridding kernel for this support / pol count / rank");
+  }
 #define AWG_CASE(SS, PP, RR) \
   if (S == SS && P == PP && rk == RR) return run_grid_fused<SS, PP, RR>(a, slot, sms, st);
   AWG_FOR_FUSED(AWG_CASE, 2)
@@ -79,6 +95,15 @@ awg_status grid_slot_fused(int S, int rk, int slot, int P, const GridArgs& a, in
 }
 
 awg_status degrid_slot_fused(int S, int rk, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+  if (a.mix != nullptr) {
+#define AWG_CASE(SS, PP, RR) \
+  if (S == SS && P == PP && rk == RR) return run_degrid_fused<SS, PP, RR, true>(a, slot, sms, st);
+    AWG_FOR_FUSED_MIX(AWG_CASE, 2)
+    AWG_FOR_FUSED_MIX(AWG_CASE, 3)
+    AWG_FOR_FUSED_MIX(AWG_CASE, 4)
+#undef AWG_CASE
+    return set_error(AWG_ERR_UNSUPPORTED, "no pol-mixing degridding kernel for this support / pol count / rank");
+  }
 #define AWG_CASE(SS, PP, RR) \
   if (S == SS && P == PP && rk == RR) return run_degrid_fused<SS, PP, RR>(a, slot, sms, st);
   AWG_FOR_FUSED(AWG_CASE, 2)
@@ -201,6 +226,8 @@ static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* v
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
   a.rank = pl->rank;
+  a.mix = nullptr;
+  a.pmask = (1 << P) - 1;
   return a;
 }
 
@@ -234,6 +261,8 @@ static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const voi
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
   a.rank = pl->rank;
+  a.mix = nullptr;
+  a.pmask = (1 << P) - 1;
   return a;
 }
 
@@ -253,9 +282,9 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   const GridArgs a = grid_args(cf, pl, vis, weight, grid, grid_lo, sumwt, flags, P);
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
-  if (cf->n_elem > 1) {
-    // Mueller set: one single-pol pass per element (p, q): grid pol q += conj(CF_pq) w_p V_p, and
-    // the diagonal elements add their weights to sumwt[q]
+  if (cf->n_mb > 1 && cf->mb_elements) {
+    // full-polarisation set stored per element (p, q): one single-pol pass per element, grid pol q
+    // += conj(CF_pq) w_p V_p; the diagonal elements add their weights to sumwt[q]
     if (P != 4) return set_error(AWG_ERR_INVALID_ARG, "a full-polarisation CF set needs 4 pols");
     for (int e = 0; e < cf->n_elem; ++e) {
       GridArgs ae = a;
@@ -272,19 +301,32 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
     }
     return AWG_OK;
   }
-  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
-  if (cf->separable) {
-    for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
-      s = cf->fused ? grid_slot_fused(cf->slots.S[i], cf->fused, i, P, a, sms, st)
-                    : grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
+  // A full-polarisation set with fused kernels runs one 4-pol pass per base CF block k: grid pol q
+  // gets conj(B_k) sum_p conj(s_pq) w_p V_p over the pols p of block k (mixing matrix mix_g[k]);
+  // the weights of those pols go to sumwt.
+  const int n_pass = cf->n_mb;
+  if (n_pass > 1 && P != 4) return set_error(AWG_ERR_INVALID_ARG, "a full-polarisation CF set needs 4 pols");
+  for (int k = 0; k < n_pass; ++k) {
+    GridArgs ak = a;
+    if (n_pass > 1) {
+      ak.cf_shift = (int64_t)k * cf->n_base * cf->rank;   // factor offsets stride: the set's terms
+      ak.mix = cf->d_mix + 32 * k;
+      ak.pmask = cf->mb_pmask[k];
+    }
+    AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+    if (cf->separable) {
+      for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
+        s = cf->fused ? grid_slot_fused(cf->slots.S[i], cf->fused, i, P, ak, sms, st)
+                      : grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, st);
+        if (s != AWG_OK) return s;
+      }
+      continue;
+    }
+    for (int c = kNumClasses - 1; c >= 0; --c) {   // largest supports first
+      if (!class_present(cf, c)) continue;
+      s = bf16 ? grid_class<true>(c, P, ak, sms, st) : grid_class<false>(c, P, ak, sms, st);
       if (s != AWG_OK) return s;
     }
-    return AWG_OK;
-  }
-  for (int c = kNumClasses - 1; c >= 0; --c) {   // largest supports first
-    if (!class_present(cf, c)) continue;
-    s = bf16 ? grid_class<true>(c, P, a, sms, st) : grid_class<false>(c, P, a, sms, st);
-    if (s != AWG_OK) return s;
   }
   return AWG_OK;
 }
@@ -311,9 +353,9 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   const DegridArgs a = degrid_args(cf, pl, grid, vis_out, P);
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
-  if (cf->n_elem > 1) {
-    // Mueller set: vis pol p = sum over elements (p, q) of CF_pq applied to grid pol q; dropped
-    // samples keep the zeros written first
+  if (cf->n_mb > 1 && cf->mb_elements) {
+    // full-polarisation set stored per element: vis pol p = sum over elements (p, q) of CF_pq
+    // applied to grid pol q; dropped samples keep the zeros written first
     if (P != 4) return set_error(AWG_ERR_INVALID_ARG, "a full-polarisation CF set needs 4 pols");
     AWG_CUDA_TRY(cudaMemsetAsync(vis_out, 0, sizeof(float2) * 4 * (size_t)pl->n, st));
     for (int e = 0; e < cf->n_elem; ++e) {
@@ -350,18 +392,31 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
     count_launches(1);
     return AWG_OK;
   }
-  AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
-  if (cf->separable) {
-    for (int i = cf->slots.n - 1; i >= 0; --i) {
-      s = cf->fused ? degrid_slot_fused(cf->slots.S[i], cf->fused, i, P, a, sms, st)
-                    : degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, a, sms, st);
-      if (s != AWG_OK) return s;
+  // A full-polarisation set with fused kernels runs one 4-pol pass per base CF block k, which
+  // writes the output pols p of block k: V_p = sum_q s_pq (B_k applied to grid pol q) (mixing
+  // matrix mix_d[k]); its plans hold one record per sample.
+  const int n_pass = cf->n_mb;
+  if (n_pass > 1 && P != 4) return set_error(AWG_ERR_INVALID_ARG, "a full-polarisation CF set needs 4 pols");
+  for (int k = 0; k < n_pass; ++k) {
+    DegridArgs ak = a;
+    if (n_pass > 1) {
+      ak.cf_shift = (int64_t)k * cf->n_base * cf->rank;   // factor offsets stride: the set's terms
+      ak.mix = cf->d_mix + 32 * k + 16;
+      ak.pmask = cf->mb_pmask[k];
     }
-  } else {
-    for (int c = kNumClasses - 1; c >= 0; --c) {
-      if (!class_present(cf, c)) continue;
-      s = bf16 ? degrid_class<true>(c, P, a, sms, st) : degrid_class<false>(c, P, a, sms, st);
-      if (s != AWG_OK) return s;
+    AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+    if (cf->separable) {
+      for (int i = cf->slots.n - 1; i >= 0; --i) {
+        s = cf->fused ? degrid_slot_fused(cf->slots.S[i], cf->fused, i, P, ak, sms, st)
+                      : degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, st);
+        if (s != AWG_OK) return s;
+      }
+    } else {
+      for (int c = kNumClasses - 1; c >= 0; --c) {
+        if (!class_present(cf, c)) continue;
+        s = bf16 ? degrid_class<true>(c, P, ak, sms, st) : degrid_class<false>(c, P, ak, sms, st);
+        if (s != AWG_OK) return s;
+      }
     }
   }
   return degrid_finish(pl, vis_out, P, sms, st);

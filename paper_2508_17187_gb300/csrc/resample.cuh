@@ -53,6 +53,11 @@ struct GridArgs {
   // (P pols from there); otherwise cf_shift = 0, vstride = gstride = P, voff = goff = 0.
   int64_t cf_shift;
   int vstride, voff, gstride, goff;
+  // Full-polarisation base passes (fused separable kernels, P = 4): when mix != NULL the kernel
+  // grids u_q = sum_p mix[4 q + p] w_p V_p as pol q instead of w_q V_q; only the pols set in pmask
+  // add their weights to sumwt.  Otherwise mix = NULL and pmask has all P bits set.
+  const float2* mix;
+  int pmask;
 };
 
 struct DegridArgs {
@@ -76,6 +81,11 @@ struct DegridArgs {
   int64_t cf_shift;      // as in GridArgs; the output row r goes to vis_out at r vstride + voff,
   int vstride, voff, gstride, goff;
   int accumulate;        // 1: add to vis_out instead of writing it
+  // Full-polarisation base passes (fused separable kernels, P = 4): with Y_q the CF applied to
+  // grid pol q, output pol p = sum_q mix[4 p + q] Y_q when mix != NULL (else Y_p); only the pols
+  // set in pmask are written.
+  const float2* mix;
+  int pmask;
 };
 
 template <bool BF16>

@@ -240,27 +240,59 @@ struct RowState {
   }
 };
 
+// u_q = sum_p mix[4 q + p] w_p V_p for the 4 pols of one staged sample (full-polarisation base
+// launches).
+__device__ __forceinline__ void mix_pols(const float2* __restrict__ mix, const float2* v, const float* w,
+                                         float2 (&u)[4]) {
+  float2 wv[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) wv[p] = make_float2(w[p] * v[p].x, w[p] * v[p].y);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float2 m = __ldg(mix + 4 * q + p);
+      acc.x = fmaf(m.x, wv[p].x, fmaf(-m.y, wv[p].y, acc.x));
+      acc.y = fmaf(m.x, wv[p].y, fmaf(m.y, wv[p].x, acc.y));
+    }
+    u[q] = acc;
+  }
+}
+
 // alpha[j][rx][p] = conj(fx[j][(rx - mx_j) mod S]) * w_jp V_jp (* phasor): formed once per
 // chunk for every (sample, column residue) instead of by each of the G threads of a column.  The
 // threads below nst also add the chunk's weights to the sum of weights (term 0 of each sample).
-template <int SMAX, int TILE, int P, int ST, int NT, int RK>
+// The MIX instances of the fused kernels (P = 4) serve the base passes of full-polarisation sets:
+// only the pols in pmask add weights, and the mixed u_q of mix_pols take the place of w V.
+template <int SMAX, int TILE, int P, int ST, int NT, int RK, bool MIX>
 __device__ __forceinline__ void form_alpha(const SepSlot<SMAX, TILE, P, ST, RK>& sl, float2* alpha, int nst, int S,
-                                           int rank, double (&wsum)[P]) {
+                                           int rank, double (&wsum)[P], const float2* mix, int pmask) {
+  static_assert(!MIX || (P == 4 && RK > 1), "pol mixing is compiled into the 4-pol fused kernels only");
   if ((int)threadIdx.x < nst && (rank == 1 || sl.rec()[threadIdx.x].cf % rank == 0)) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) wsum[p] += (double)sl.w()[threadIdx.x * P + p];
+    for (int p = 0; p < P; ++p)
+      if (!MIX || ((pmask >> p) & 1)) wsum[p] += (double)sl.w()[threadIdx.x * P + p];
   }
   if constexpr (RK > 1) {
     // fused terms: w V (* phasor) per sample into the slot's a(), conj(fx_t) per column residue
     if ((int)threadIdx.x < nst) {
       const int j = threadIdx.x;
       const float2 ph = sl.ph()[j];
+      if constexpr (MIX) {
+        float2 u[4];
+        mix_pols(mix, sl.v() + j * 4, sl.w() + j * 4, u);
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const float wv = sl.w()[j * P + p];
-        const float2 v = sl.v()[j * P + p];
-        const float xr = wv * v.x, xi = wv * v.y;
-        sl.a()[j * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
+        for (int q = 0; q < 4; ++q)
+          sl.a()[j * 4 + q] = make_float2(u[q].x * ph.x - u[q].y * ph.y, u[q].x * ph.y + u[q].y * ph.x);
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const float wv = sl.w()[j * P + p];
+          const float2 v = sl.v()[j * P + p];
+          const float xr = wv * v.x, xi = wv * v.y;
+          sl.a()[j * P + p] = make_float2(xr * ph.x - xi * ph.y, xr * ph.y + xi * ph.x);
+        }
       }
     }
     for (int i = threadIdx.x; i < nst * S; i += NT) {
@@ -307,7 +339,7 @@ __device__ __forceinline__ void form_beta(const SepSlot<SMAX, TILE, P, ST, RK>& 
   }
 }
 
-template <int SMIN, int SMAX, int NT, int TILE, int P, int ST, int RK = 1>
+template <int SMIN, int SMAX, int NT, int TILE, int P, int ST, int RK = 1, bool MIX = false>
 __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST, RK>::bytes, NT, RK > 1 ? 128 : 96))
     k_grid_sep(const GridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
@@ -362,7 +394,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      form_alpha<SMAX, TILE, P, ST, NT, RK>(s0, alpha, nst_of(0), S, a.rank, wsum);
+      form_alpha<SMAX, TILE, P, ST, NT, RK, MIX>(s0, alpha, nst_of(0), S, a.rank, wsum, a.mix, a.pmask);
       __syncthreads();
     }
 
@@ -470,7 +502,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       __syncthreads();
       // slot A is free: derive chunk c+2 into it; chunk c+1's payload has landed in B: form w V
       if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
-      if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT, RK>(B, alpha, nst_of(c + 1), S, a.rank, wsum);
+      if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT, RK, MIX>(B, alpha, nst_of(c + 1), S, a.rank, wsum, a.mix, a.pmask);
       __syncthreads();
     }
 #pragma unroll
@@ -521,7 +553,7 @@ struct DegridCache {
   static constexpr bool enabled = R * P * 2 <= 48;
 };
 
-template <int SMIN, int SMAX, int NT, int TILE, int P, int ST, int RK = 1>
+template <int SMIN, int SMAX, int NT, int TILE, int P, int ST, int RK = 1, bool MIX = false>
 __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST, RK>::bytes, NT, RK > 1 ? 128 : 96))
     k_degrid_sep(const DegridArgs a, const int cls) {
   constexpr int R = sep_rows(SMIN, SMAX, NT);
@@ -737,11 +769,37 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
 #pragma unroll
             for (int w = 0; w < NW; ++w) v += s_red[bi][w][lane];
             const float partner = __shfl_xor_sync(0xffffffffu, v, 1);
-            if (cap_src[q] >= 0) {
+            if constexpr (!MIX) {
+              if (cap_src[q] >= 0) {
+                const float2 ph = cap_ph[q];
+                const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
+                float* o = a.vis_out + ((size_t)cap_src[q] * a.vstride + a.voff) * 2 + comp;
+                *o = a.accumulate ? *o + out : out;
+              }
+            } else {
               const float2 ph = cap_ph[q];
-              const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
-              float* o = a.vis_out + ((size_t)cap_src[q] * a.vstride + a.voff) * 2 + comp;
-              *o = a.accumulate ? *o + out : out;
+              float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
+              static_assert(!MIX || (P == 4 && RK > 1), "pol mixing is compiled into the 4-pol fused kernels only");
+              {
+                // the sample's 8 lanes hold Y_0..Y_3 (re, im): output pol p = sum_q mix[4 p + q] Y_q
+                const float other = __shfl_xor_sync(0xffffffffu, out, 1);
+                const float yr = (comp & 1) ? other : out, yi = (comp & 1) ? out : other;
+                const int base = lane & ~7, p = comp >> 1;
+                float ar = 0.f, ai = 0.f;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                  const float2 m = __ldg(a.mix + 4 * p + qq);
+                  const float zr = __shfl_sync(0xffffffffu, yr, base + 2 * qq);
+                  const float zi = __shfl_sync(0xffffffffu, yi, base + 2 * qq);
+                  ar = fmaf(m.x, zr, fmaf(-m.y, zi, ar));
+                  ai = fmaf(m.x, zi, fmaf(m.y, zr, ai));
+                }
+                out = (comp & 1) ? ai : ar;
+              }
+              if (cap_src[q] >= 0 && ((a.pmask >> (comp >> 1)) & 1)) {
+                float* o = a.vis_out + ((size_t)cap_src[q] * a.vstride + a.voff) * 2 + comp;
+                *o = a.accumulate ? *o + out : out;
+              }
             }
           }
         }
@@ -849,14 +907,14 @@ constexpr int fused_stage() {
   else return fused_stage<S, T, P, RK, ST0 / 2>();
 }
 
-template <int S, int P, int RK>
+template <int S, int P, int RK, bool MIX = false>
 awg_status run_grid_fused(const GridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr ExactCfg e = exact_cfg(S, 0);
   constexpr int nt = S * e.g_grid;
   constexpr int stage = fused_stage<S, e.tile, P, RK, e.stage>();
   using L = SepLayout<S, e.tile, P, stage, RK>;
   static_assert(L::bytes <= 227 * 1024, "fused gridding window does not fit in shared memory");
-  auto kern = k_grid_sep<S - 1, S, nt, e.tile, P, stage, RK>;
+  auto kern = k_grid_sep<S - 1, S, nt, e.tile, P, stage, RK, MIX>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
@@ -869,14 +927,14 @@ awg_status run_grid_fused(const GridArgs& a, int slot, int sms, cudaStream_t st)
   return AWG_OK;
 }
 
-template <int S, int P, int RK>
+template <int S, int P, int RK, bool MIX = false>
 awg_status run_degrid_fused(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr ExactCfg e = exact_cfg(S, 0);
   constexpr int nt = S * e.g_degrid;
   constexpr int stage = fused_stage<S, e.tile, P, RK, e.stage>();
   using L = SepLayout<S, e.tile, P, stage, RK>;
   static_assert(L::bytes <= 227 * 1024, "fused degridding window does not fit in shared memory");
-  auto kern = k_degrid_sep<S - 1, S, nt, e.tile, P, stage, RK>;
+  auto kern = k_degrid_sep<S - 1, S, nt, e.tile, P, stage, RK, MIX>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
@@ -901,6 +959,16 @@ awg_status run_degrid_fused(const DegridArgs& a, int slot, int sms, cudaStream_t
   template awg_status run_grid_fused<S, P, RK>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_INSTANTIATE_DEGRID_FUSED(S, P, RK) \
   template awg_status run_degrid_fused<S, P, RK>(const DegridArgs&, int, int, cudaStream_t);
+// The pol-mixing instances (full-polarisation base passes): 4 pols, every exact support.
+#define AWG_FOR_FUSED_MIX(M, RK) M(8, 4, RK) M(16, 4, RK) M(24, 4, RK) M(32, 4, RK) M(40, 4, RK) M(48, 4, RK) M(56, 4, RK) M(64, 4, RK)
+#define AWG_DECLARE_GRID_FUSED_MIX(S, P, RK) \
+  extern template awg_status run_grid_fused<S, P, RK, true>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_DECLARE_DEGRID_FUSED_MIX(S, P, RK) \
+  extern template awg_status run_degrid_fused<S, P, RK, true>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_FUSED_MIX(S, P, RK) \
+  template awg_status run_grid_fused<S, P, RK, true>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_DEGRID_FUSED_MIX(S, P, RK) \
+  template awg_status run_degrid_fused<S, P, RK, true>(const DegridArgs&, int, int, cudaStream_t);
 
 #define AWG_FOR_EXACT_AND_POLS(M, C)                                                                        \
   M(8, 1, C) M(8, 2, C) M(8, 4, C) M(16, 1, C) M(16, 2, C) M(16, 4, C) M(24, 1, C) M(24, 2, C) M(24, 4, C)      \

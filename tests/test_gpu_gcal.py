@@ -1,6 +1,13 @@
 """G-Jones calibration on the GPU (gcal_solve: Eq. VAvg, Eq. CalUpdateDir, Eq. CalUpdateModel)
 against the FP64 oracle on the same FP32 inputs, and end to end with model visibilities from the
-library's degridding (Eq. VMod)."""
+library's degridding (Eq. VMod).
+
+Tolerance: the library forms the interval sums N = sum w V conj(M) and D = sum w |M|^2 in FP32
+(each product rounded once, compensated per-thread sums, a 5-level tree), within about 10 u =
+6e-7 of sum w |V| |M| (u = 2^-24); with |V| ~ |g|^2 |M| and |g| in [0.8, 1.2] that is a relative
+error of X = N / D below ~1e-6, and the gains - weighted averages of g_j X_ij over 26 baselines
+- move by less than that.  GAIN_TOL = 2e-6 leaves a factor 2 over that bound."""
+GAIN_TOL = 2e-6
 import numpy as np
 import pytest
 
@@ -41,7 +48,7 @@ def test_gcal_matches_oracle(P):
                             torch.as_tensor(a1).cuda(), torch.as_tensor(a2).cuda(), n_ant, sol_int, sol_chan,
                             alpha=0.5, delta=1e-12, max_iter=400)
     Go, itso = gcal.gcal(V32, M32, W32, a1, a2, n_ant, sol_int, sol_chan, 0.5, 1e-12, 400)
-    assert np.abs(G.cpu().numpy() - Go).max() < 1e-9
+    assert np.abs(G.cpu().numpy() - Go).max() < GAIN_TOL
     assert np.abs(its.cpu().numpy() - itso).max() <= 1
     gt = g * np.conj(g[..., :1]) / np.abs(g[..., :1])
     assert np.abs(Go - gt).max() < 0.05
@@ -80,7 +87,7 @@ def test_gcal_end_to_end_with_degridded_model():
     G, its = awg.gcal_solve(torch.as_tensor(V32).cuda(), M, torch.as_tensor(W32).cuda(), torch.as_tensor(a1).cuda(),
                             torch.as_tensor(a2).cuda(), 27, sol_int, sol_chan, alpha=0.5, delta=1e-12, max_iter=400)
     Go, _ = gcal.gcal(V32, Mh, W32, a1, a2, 27, sol_int, sol_chan, 0.5, 1e-12, 400)
-    assert np.abs(G.cpu().numpy() - Go).max() < 1e-9
+    assert np.abs(G.cpu().numpy() - Go).max() < GAIN_TOL
     gt = g * np.conj(g[..., :1]) / np.abs(g[..., :1])
     assert np.abs(Go - gt).max() < 0.02
 

@@ -8,6 +8,7 @@ whole grids, images and visibility vectors is the 1e-5 relative RMS accuracy tar
 (8-bit mantissa, 2^-9 relative) get their own, looser gate.  Integer-valued inputs make FP32 sums
 exact, and there the comparison is bit for bit.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -205,16 +206,26 @@ def test_awproj_parity(awg, separable):
     assert np.all(res["vis"][~orc["idx"].valid] == 0)
 
 
-def test_mueller_full_polarisation_parity(awg):
+@pytest.mark.parametrize("fused", [True, False])
+def test_mueller_full_polarisation_parity(awg, fused):
     """Sparse Mueller matrix of A-term CFs (feed squint and complex leakage, 12 of 16 elements kept):
     CF tables, gridding (pol q from conj(CF_pq) w_p V_p), weight sums and degridding against the
-    oracle."""
-    wl = synth.make_workload("awproj", n_int=10, n_chan=8, grid_n=512, n_pa=3, n_sb=2, n_wplanes=4, max_support=32,
-                             oversampling=8)
-    op = oracle_params(wl, use_pol=True, squint_rad=3e-4, leakage=0.04 * np.exp(0.9j), mueller_threshold=0.01)
+    oracle.  fused: W-projection supports 8..32 (the 4-pol base passes with pol mixing); not fused:
+    no W term and support 20, which has no exact-support kernel (one single-pol pass per element)."""
+    if fused:
+        wl = synth.make_workload("awproj", n_int=10, n_chan=8, grid_n=512, n_pa=3, n_sb=2, n_wplanes=4,
+                                 max_support=32, oversampling=8)
+        op = oracle_params(wl, use_pol=True, squint_rad=3e-4, leakage=0.04 * np.exp(0.9j), mueller_threshold=0.01)
+    else:
+        wl = synth.make_workload("awproj", n_int=10, n_chan=8, grid_n=512, n_pa=3, n_sb=2, n_wplanes=4,
+                                 max_support=20, oversampling=8)
+        op = oracle_params(wl, use_pol=True, squint_rad=3e-4, leakage=0.04 * np.exp(0.9j), mueller_threshold=0.01)
+        op = dataclasses.replace(op, use_w=False)
     cf = awg.cf_set_create(**library_params(op))
     assert cf.mueller() == ocf.mueller_elements(op) and len(cf.mueller()) == 12
     assert cf.separable and cf.rank >= 1
+    assert (cf.fused_terms > 0) == fused
+    assert cf.n_cf == op.n_cf
     # a diagonal and a leakage element table
     for e in (0, 1):
         ci = e * op.n_base + op.cf_index(1, 1, op.n_signed - 1)
