@@ -181,6 +181,25 @@ awg_status cf_set_choose(awg_cf_set cf, int32_t support, int32_t config);
  * pol q.  Both need n_pol = 4. */
 awg_status cf_set_mueller(awg_cf_set cf, int32_t* n_elem, int32_t* elem_p, int32_t* elem_q);
 
+/* The parameters a CF set was made with (pointers NULL in *out); when not NULL,
+ * pa_bin_centers_rad host [n_pa_bins] and subband_freq_hz host [n_subbands] receive the A-term
+ * bins (left untouched without use_a). */
+awg_status cf_set_get_params(awg_cf_set cf, awg_cf_params* out, double* pa_bin_centers_rad, double* subband_freq_hz);
+
+/*
+ * Persistent CF cache (the CFCache of Sec. 6, which the paper keeps in memory and on disk): save a
+ * CF set to a file and load it back without rebuilding it.  The file holds the parameters, the
+ * storage mode, the support and autotuned kernel choice of every support, and the stored CF data
+ * (FP32 factors, or the FP32 / BF16 tables) exactly, so that a loaded set computes bit-identical
+ * results; it is read on hosts of the same byte order and awg_cf_params layout.  cf_set_save
+ * copies the device data first (blocking) and writes nothing when that fails; cf_set_load checks
+ * the magic, version, parameter layout, the parameters (as cf_set_create does), the storage mode
+ * against the parameters and the end marker.  Errors: INVALID_ARG (NULL, unreadable / unwritable
+ * path, a file that is not a CF cache, truncated or inconsistent), OOM, CUDA.
+ */
+awg_status cf_set_save(awg_cf_set cf, const char* path);
+awg_status cf_set_load(const char* path, void* stream, awg_cf_set* out);
+
 /* Host copy of the support of every CF: supports_out host [n_cf]. */
 awg_status cf_set_get_supports(awg_cf_set cf, int32_t* supports_out);
 

@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "AWG_OK", 1: "AWG_ERR_INVALID_ARG", 2: "AWG_ERR_UNSUPPORTED",
 AWG_CF_FP32, AWG_CF_BF16 = 0, 1
 AWG_GRID_KAHAN, AWG_GRID_FP64 = 1, 2
 
-EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_fused_terms",
+EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_fused_terms", "cf_set_get_params", "cf_set_save", "cf_set_load",
             "cf_set_get_supports",
             "cf_set_copy_table", "plan_create", "plan_update", "plan_destroy", "plan_stats", "grid_visibilities",
             "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
@@ -81,6 +81,9 @@ def load():
             "cf_set_destroy": ([vp], st),
             "cf_set_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)], st),
             "cf_set_fused_terms": ([vp, ctypes.POINTER(i32)], st),
+            "cf_set_get_params": ([vp, ctypes.POINTER(CfParams), vp, vp], st),
+            "cf_set_save": ([vp, ctypes.c_char_p], st),
+            "cf_set_load": ([ctypes.c_char_p, vp, ctypes.POINTER(vp)], st),
             "cf_set_get_supports": ([vp, vp], st),
             "cf_set_copy_table": ([vp, i32, vp], st),
             "plan_create": ([vp, vp, i64, vp, i32, vp, vp, vp, vp, ctypes.POINTER(vp)], st),

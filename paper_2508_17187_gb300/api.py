@@ -62,6 +62,19 @@ class CFSet:
         check(_lib.load().cf_set_fused_terms(self._h, ctypes.byref(fused)), "cf_set_fused_terms")
         self.fused_terms = int(fused.value)   # terms combined per tap by the kernels; 0 if not fused
 
+    def params(self) -> dict:
+        """The parameters the set was made with (cf_set_get_params), A-term bins as arrays."""
+        p = CfParams()
+        pa = np.zeros(max(self.n_pa_bins, 1), dtype=np.float64)
+        sb = np.zeros(max(self.n_subbands, 1), dtype=np.float64)
+        check(_lib.load().cf_set_get_params(self.handle, ctypes.byref(p), pa.ctypes.data_as(ctypes.c_void_p),
+                                            sb.ctypes.data_as(ctypes.c_void_p)), "cf_set_get_params")
+        out = {name: getattr(p, name) for name, _ in CfParams._fields_
+               if name not in ("pa_bin_centers_rad", "subband_freq_hz")}
+        if p.use_a:
+            out["pa_bin_centers_rad"], out["subband_freq_hz"] = pa[:p.n_pa_bins], sb[:p.n_subbands]
+        return out
+
     @property
     def handle(self):
         if self._h is None:
@@ -183,6 +196,20 @@ def cf_set_create_from_table(supports: Sequence[int], table: np.ndarray, stream=
                                                tab.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream),
                                                ctypes.byref(h)), "cf_set_create_from_table")
     del keep
+    return CFSet(h, p.grid_n, p.oversampling, p.n_pa_bins, p.n_subbands)
+
+
+def cf_set_save(cf: CFSet, path) -> None:
+    """Write the CF set to a CF cache file (see cf_set_save in awgrid.h); blocking."""
+    check(_lib.load().cf_set_save(cf.handle, str(path).encode()), "cf_set_save")
+
+
+def cf_set_load(path, stream=None) -> CFSet:
+    """Load a CF set from a CF cache file written by cf_set_save, without rebuilding it."""
+    h = ctypes.c_void_p()
+    check(_lib.load().cf_set_load(str(path).encode(), _stream_ptr(stream), ctypes.byref(h)), "cf_set_load")
+    p = CfParams()
+    check(_lib.load().cf_set_get_params(h, ctypes.byref(p), None, None), "cf_set_get_params")
     return CFSet(h, p.grid_n, p.oversampling, p.n_pa_bins, p.n_subbands)
 
 

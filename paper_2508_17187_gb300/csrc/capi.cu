@@ -240,6 +240,8 @@ static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<
 // fy fx (from its image-plane screen, without forming the 2-D table), mirror the fit for the
 // negative planes, upload only the factors.  Returns AWG_ERR_UNSUPPORTED (nothing allocated on
 // the device) when some CF needs more terms than that to come within kSepTol of its peak.
+static awg_status upload_mix(CfSetImpl* cf, cudaStream_t st);
+
 static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
   const awg_cf_params& p = cf->p;
   cf->n_signed = p.use_w ? 2 * p.n_wplanes - 1 : 1;
@@ -324,8 +326,13 @@ static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
   }
   awg_status s = upload_separable(cf, fx, fy, st);
   if (s != AWG_OK || cf->n_mb == 1 || cf->mb_elements) return s;
-  // pol-mixing matrices of the base blocks: gridding mix_g[4 q + p] = conj(s_pq), degridding
-  // mix_d[4 p + q] = s_pq, for the kept elements (p, q) of the block
+  return upload_mix(cf, st);
+}
+
+// The pol-mixing matrices of the base blocks of a full-polarisation set: gridding
+// mix_g[4 q + p] = conj(s_pq), degridding mix_d[4 p + q] = s_pq, for the kept elements (p, q) of
+// the block.
+static awg_status upload_mix(CfSetImpl* cf, cudaStream_t st) {
   std::vector<float2> mix((size_t)cf->n_mb * 32, make_float2(0.f, 0.f));
   for (int e = 0; e < cf->n_elem; ++e) {
     const int k = cf->elem_mb[e], pp = cf->elem_p[e], qq = cf->elem_q[e];
@@ -339,24 +346,12 @@ static awg_status build_separable(CfSetImpl* cf, cudaStream_t st) {
   return AWG_OK;
 }
 
-}  // namespace awg
-
-using namespace awg;
-
-extern "C" {
-
-const char* awg_last_error(void) { return g_last_error.c_str(); }
-
-int64_t awg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
-
-awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* out) {
-  if (!out) return set_error(AWG_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  awg_status s = check_params(params, false);
-  if (s != AWG_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
+// A CF set's host state from checked params: the A-term bin centres and frequencies, the Mueller
+// elements with their base blocks and scalars, and the support of every stored CF (no device
+// memory yet).  NULL when the host allocation fails.
+static CfSetImpl* new_cf_set(const awg_cf_params* params) {
   CfSetImpl* cf = new (std::nothrow) CfSetImpl();
-  if (!cf) return set_error(AWG_ERR_OOM, "host allocation failed");
+  if (!cf) return nullptr;
   cf->p = *params;
   if (params->use_a) {
     cf->pa_centers.assign(params->pa_bin_centers_rad, params->pa_bin_centers_rad + params->n_pa_bins);
@@ -366,6 +361,7 @@ awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* 
   cf->p.subband_freq_hz = nullptr;
   cudaGetDevice(&cf->device);
   const int n_signed = params->use_w ? 2 * params->n_wplanes - 1 : 1;
+  cf->n_signed = n_signed;
   cf->n_base = params->n_pa_bins * params->n_subbands * n_signed;
   cf->n_elem = params->use_pol ? mueller_elements(cf->p, cf->elem_p, cf->elem_q) : 1;
   if (params->use_pol) {
@@ -390,6 +386,28 @@ awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* 
       for (int sb = 0; sb < params->n_subbands; ++sb)
         for (int ks = 0; ks < n_signed; ++ks)
           cf->supports[e * cf->n_base + (pa * params->n_subbands + sb) * n_signed + ks] = support_of_plane(cf->p, ks);
+  return cf;
+}
+
+}  // namespace awg
+
+using namespace awg;
+
+extern "C" {
+
+const char* awg_last_error(void) { return g_last_error.c_str(); }
+
+int64_t awg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* out) {
+  if (!out) return set_error(AWG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  awg_status s = check_params(params, false);
+  if (s != AWG_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  CfSetImpl* cf = new_cf_set(params);
+  if (!cf) return set_error(AWG_ERR_OOM, "host allocation failed");
+  const int n_signed = cf->n_signed;
   if (params->separable && params->cf_dtype == AWG_CF_FP32) {
     s = build_separable(cf, st);
     if (s == AWG_OK) {
@@ -601,6 +619,195 @@ awg_status cf_set_fused_terms(awg_cf_set h, int32_t* terms) {
   if (!h || !terms) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
   CfSetImpl* cf = (CfSetImpl*)h;
   *terms = cf->fused;
+  return AWG_OK;
+}
+
+awg_status cf_set_get_params(awg_cf_set h, awg_cf_params* out, double* pa_bin_centers_rad, double* subband_freq_hz) {
+  if (!h || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  const CfSetImpl* cf = (const CfSetImpl*)h;
+  *out = cf->p;
+  out->pa_bin_centers_rad = nullptr;
+  out->subband_freq_hz = nullptr;
+  if (pa_bin_centers_rad && !cf->pa_centers.empty())
+    std::memcpy(pa_bin_centers_rad, cf->pa_centers.data(), sizeof(double) * cf->pa_centers.size());
+  if (subband_freq_hz && !cf->sb_freqs.empty())
+    std::memcpy(subband_freq_hz, cf->sb_freqs.data(), sizeof(double) * cf->sb_freqs.size());
+  return AWG_OK;
+}
+
+// CF cache file (same-endian hosts): magic, format version, sizeof(awg_cf_params), the params
+// (pointers zeroed), the A-term bin centres and frequencies, the storage mode (separable, blocks,
+// element blocks, stored CFs), the support of every stored CF, the autotuned kernel choice per
+// support, then either every stored CF's terms (count, then fx and fy of each term as FP32
+// [OS+1][S] complex) or the raw table data, and an end marker.
+static const char kCacheMagic[8] = {'A', 'W', 'G', 'C', 'F', 'S', 'E', 'T'};
+static const char kCacheEnd[8] = {'A', 'W', 'G', 'C', 'F', 'E', 'N', 'D'};
+static const int32_t kCacheVersion = 1;
+
+awg_status cf_set_save(awg_cf_set h, const char* path) {
+  if (!h || !path) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  if (cudaSetDevice(cf->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
+  // the device data first, so that a CUDA error leaves no partial file behind
+  std::vector<float> sep;
+  std::vector<unsigned char> raw;
+  if (cf->separable) {
+    sep.resize((size_t)2 * cf->n_values);
+    AWG_CUDA_TRY(cudaMemcpy(sep.data(), cf->d_sep, sizeof(float) * sep.size(), cudaMemcpyDeviceToHost));
+  } else {
+    raw.resize((size_t)cf->n_values * (cf->p.cf_dtype == AWG_CF_BF16 ? 4 : 8));
+    AWG_CUDA_TRY(cudaMemcpy(raw.data(), cf->d_data, raw.size(), cudaMemcpyDeviceToHost));
+  }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_error(AWG_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+  bool ok = true;
+  auto put = [&](const void* p, size_t n) { ok = ok && (n == 0 || std::fwrite(p, 1, n, f) == n); };
+  awg_cf_params pp = cf->p;
+  pp.pa_bin_centers_rad = nullptr;
+  pp.subband_freq_hz = nullptr;
+  const int32_t psize = (int32_t)sizeof(awg_cf_params);
+  put(kCacheMagic, 8);
+  put(&kCacheVersion, 4);
+  put(&psize, 4);
+  put(&pp, sizeof(pp));
+  const int64_t n_pa = (int64_t)cf->pa_centers.size(), n_sb = (int64_t)cf->sb_freqs.size();
+  put(&n_pa, 8);
+  put(cf->pa_centers.data(), sizeof(double) * n_pa);
+  put(&n_sb, 8);
+  put(cf->sb_freqs.data(), sizeof(double) * n_sb);
+  const int32_t mode[4] = {cf->separable, cf->n_mb, cf->mb_elements, cf->n_cf};
+  put(mode, sizeof(mode));
+  put(cf->supports.data(), sizeof(int32_t) * cf->n_cf);
+  put(cf->cand, sizeof(cf->cand));
+  if (cf->separable) {
+    const int OS = cf->p.oversampling;
+    for (int i = 0; i < cf->n_cf && ok; ++i) {
+      const int64_t q = (int64_t)(OS + 1) * cf->supports[i];
+      int32_t terms = 0;
+      for (int k = 0; k < cf->rank; ++k) terms += cf->sep_offsets[(size_t)i * cf->rank + k] != 0;
+      put(&terms, 4);
+      for (int k = 0; k < cf->rank; ++k) {
+        const int64_t o = cf->sep_offsets[(size_t)i * cf->rank + k];
+        if (o != 0) put(sep.data() + 2 * o, sizeof(float) * 4 * q);   // fx then fy
+      }
+    }
+  } else {
+    put(raw.data(), raw.size());
+  }
+  put(kCacheEnd, 8);
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return set_error(AWG_ERR_INVALID_ARG, std::string("writing ") + path + " failed");
+  return AWG_OK;
+}
+
+awg_status cf_set_load(const char* path, void* stream, awg_cf_set* out) {
+  if (!path || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(AWG_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  bool ok = true;
+  auto get = [&](void* p, size_t n) { ok = ok && (n == 0 || std::fread(p, 1, n, f) == n); return ok; };
+  auto fail = [&](const std::string& why) {
+    std::fclose(f);
+    return set_error(AWG_ERR_INVALID_ARG, std::string(path) + ": " + why);
+  };
+  char magic[8];
+  int32_t version = 0, psize = 0;
+  if (!get(magic, 8) || std::memcmp(magic, kCacheMagic, 8) != 0) return fail("not a CF cache file");
+  if (!get(&version, 4) || version != kCacheVersion) return fail("unsupported CF cache version");
+  if (!get(&psize, 4) || psize != (int32_t)sizeof(awg_cf_params)) return fail("CF parameter layout differs");
+  awg_cf_params p;
+  int64_t n_pa = 0, n_sb = 0;
+  if (!get(&p, sizeof(p)) || !get(&n_pa, 8) || n_pa < 0 || n_pa > (1 << 20)) return fail("truncated or corrupt header");
+  std::vector<double> pa((size_t)n_pa), sb;
+  if (!get(pa.data(), sizeof(double) * n_pa) || !get(&n_sb, 8) || n_sb < 0 || n_sb > (1 << 20))
+    return fail("truncated or corrupt header");
+  sb.resize((size_t)n_sb);
+  if (!get(sb.data(), sizeof(double) * n_sb)) return fail("truncated header");
+  p.pa_bin_centers_rad = p.use_a ? pa.data() : nullptr;
+  p.subband_freq_hz = p.use_a ? sb.data() : nullptr;
+  if (p.use_a && (n_pa != p.n_pa_bins || n_sb != p.n_subbands)) return fail("A-term bins do not match the params");
+  const bool from_table = !p.use_ps && !p.use_a;   // a caller-table set keeps its own supports
+  if (check_params(&p, from_table) != AWG_OK) {
+    const std::string why = g_last_error;
+    return fail("invalid params: " + why);
+  }
+  int32_t mode[4];
+  if (!get(mode, sizeof(mode))) return fail("truncated header");
+  CfSetImpl* cf = new_cf_set(&p);
+  if (!cf) {
+    std::fclose(f);
+    return set_error(AWG_ERR_OOM, "host allocation failed");
+  }
+  auto fail_cf = [&](const std::string& why) {
+    free_cf(cf);
+    return fail(why);
+  };
+  // the stored blocks: as built, or one block per Mueller element
+  const bool elements = mode[2] != 0;
+  if (elements) {
+    if (!p.use_pol || mode[1] != cf->n_elem) return fail_cf("inconsistent storage mode");
+    cf->n_mb = cf->n_elem;
+    cf->mb_elements = 1;
+    cf->n_cf = cf->n_elem * cf->n_base;
+  } else if (mode[1] != cf->n_mb) {
+    return fail_cf("inconsistent storage mode");
+  }
+  if (mode[3] != cf->n_cf || (mode[0] && !(p.separable && p.cf_dtype == AWG_CF_FP32)) || (p.use_pol && !mode[0]))
+    return fail_cf("inconsistent storage mode");
+  cf->supports.resize(cf->n_cf);
+  if (!get(cf->supports.data(), sizeof(int32_t) * cf->n_cf) || !get(cf->cand, sizeof(cf->cand)))
+    return fail_cf("truncated header");
+  for (int i = 0; i < cf->n_cf; ++i)
+    if (cf->supports[i] < 1 || cf->supports[i] > kMaxSupport) return fail_cf("corrupt supports");
+  for (int S = 0; S <= kMaxSupport; ++S)
+    if (cf->cand[S] < 0 || cf->cand[S] >= kNumCand || (cf->cand[S] && !has_exact(S))) return fail_cf("corrupt kernel choices");
+  cudaStream_t st = (cudaStream_t)stream;
+  awg_status s = AWG_OK;
+  if (mode[0]) {
+    const int OS = p.oversampling;
+    std::vector<std::vector<double>> fx(cf->n_cf), fy(cf->n_cf);
+    std::vector<float> buf;
+    for (int i = 0; i < cf->n_cf; ++i) {
+      const size_t q = (size_t)(OS + 1) * cf->supports[i];
+      int32_t terms = 0;
+      if (!get(&terms, 4) || terms < 1 || terms > kMaxRank) return fail_cf("corrupt factors");
+      fx[i].resize(2 * q * terms);
+      fy[i].resize(2 * q * terms);
+      buf.resize(4 * q);
+      for (int k = 0; k < terms; ++k) {
+        if (!get(buf.data(), sizeof(float) * 4 * q)) return fail_cf("truncated factors");
+        for (size_t t = 0; t < 2 * q; ++t) {
+          fx[i][2 * q * k + t] = buf[t];
+          fy[i][2 * q * k + t] = buf[2 * q + t];
+        }
+      }
+    }
+    char end[8];
+    if (!get(end, 8) || std::memcmp(end, kCacheEnd, 8) != 0) return fail_cf("missing end marker");
+    std::fclose(f);
+    s = upload_separable(cf, fx, fy, st);
+    if (s == AWG_OK && cf->n_mb > 1 && !cf->mb_elements) s = upload_mix(cf, st);
+  } else {
+    s = alloc_cf(cf, st);
+    if (s != AWG_OK) {
+      std::fclose(f);
+      free_cf(cf);
+      return s;
+    }
+    std::vector<unsigned char> raw((size_t)cf->n_values * (p.cf_dtype == AWG_CF_BF16 ? 4 : 8));
+    char end[8];
+    if (!get(raw.data(), raw.size()) || !get(end, 8) || std::memcmp(end, kCacheEnd, 8) != 0)
+      return fail_cf("truncated tables");
+    std::fclose(f);
+    if (cudaMemcpy(cf->d_data, raw.data(), raw.size(), cudaMemcpyHostToDevice) != cudaSuccess) s = AWG_ERR_CUDA;
+    if (s != AWG_OK) set_error(s, "uploading the tables failed");
+  }
+  if (s != AWG_OK) {   // the uploads above fill the slot table from the loaded kernel choices
+    free_cf(cf);
+    return s;
+  }
+  *out = (awg_cf_set)cf;
   return AWG_OK;
 }
 

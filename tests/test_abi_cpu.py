@@ -70,3 +70,32 @@ def test_python_binding_refuses_cpu_tensors():
     from paper_2508_17187_gb300 import api
     with pytest.raises(ValueError, match="CUDA"):
         api._need(torch.zeros(3), "x", torch.float32)
+
+
+def test_cf_cache_load_rejects_bad_files_before_the_device(lib, tmp_path):
+    """cf_set_load checks the file (existence, magic, version, parameter layout, a complete header)
+    before it touches the device; every failure is INVALID_ARG with a message naming the file."""
+    from paper_2508_17187_gb300._lib import CfParams
+    out = ctypes.c_void_p()
+    lib.awg_last_error.restype = ctypes.c_char_p
+
+    def load(path):
+        return lib.cf_set_load(str(path).encode(), None, ctypes.byref(out))
+
+    assert load(tmp_path / "missing.awgcf") == 1 and out.value is None
+    assert b"cannot open" in lib.awg_last_error()
+    junk = tmp_path / "junk.awgcf"
+    junk.write_bytes(b"not a cache file at all")
+    assert load(junk) == 1 and b"not a CF cache file" in lib.awg_last_error()
+    magic = b"AWGCFSET"
+    bad_version = tmp_path / "v.awgcf"
+    bad_version.write_bytes(magic + (99).to_bytes(4, "little") + ctypes.sizeof(CfParams).to_bytes(4, "little"))
+    assert load(bad_version) == 1 and b"version" in lib.awg_last_error()
+    bad_layout = tmp_path / "l.awgcf"
+    bad_layout.write_bytes(magic + (1).to_bytes(4, "little") + (ctypes.sizeof(CfParams) + 8).to_bytes(4, "little"))
+    assert load(bad_layout) == 1 and b"layout" in lib.awg_last_error()
+    truncated = tmp_path / "t.awgcf"
+    truncated.write_bytes(magic + (1).to_bytes(4, "little") + ctypes.sizeof(CfParams).to_bytes(4, "little") + b"\0" * 16)
+    assert load(truncated) == 1 and b"truncated" in lib.awg_last_error()
+    assert lib.cf_set_save(None, str(junk).encode()) == 1
+    assert lib.cf_set_load(None, None, ctypes.byref(out)) == 1
