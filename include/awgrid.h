@@ -397,6 +397,17 @@ awg_status gcal_solve(const void* vis, const void* model, const float* weight, i
                       int32_t sol_int, int32_t sol_chan, double alpha, double delta, int32_t max_iter, int32_t ref_ant,
                       void* gains, int32_t* iterations, void* workspace, void* stream);
 
+/*
+ * Failure injection for tests (host side; no device fault).  After awg_debug_fail_allocations(n)
+ * the next n device allocations of this library succeed and the one after fails as out of memory
+ * (without reaching the driver), and so does every later one until the hook is reset with -1.  A
+ * call that meets the failure returns AWG_ERR_OOM and frees what it had allocated:
+ * awg_debug_live_allocations() (the library's live device allocations) is then what it was
+ * before the call.  Errors: INVALID_ARG (n < -1).
+ */
+awg_status awg_debug_fail_allocations(int64_t after);
+int64_t awg_debug_live_allocations(void);
+
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* awg_last_error(void);
 

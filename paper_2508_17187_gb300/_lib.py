@@ -22,7 +22,7 @@ EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_s
             "grid_visibilities_noalloc", "grid_visibilities_plain_fp64", "degrid_visibilities_plain_fp64",
             "awg_fp32_fma_probe", "cf_set_autotune", "cf_set_choose", "clean_hogbom_workspace_bytes",
             "clean_hogbom", "clean_hogbom_components", "plan_set_row_phase", "gcal_workspace_bytes", "gcal_solve",
-            "cf_set_mueller"]
+            "cf_set_mueller", "awg_debug_fail_allocations", "awg_debug_live_allocations"]
 
 
 class AwgError(RuntimeError):
@@ -107,6 +107,8 @@ def load():
             "plan_set_row_phase": ([vp, vp, vp, vp, vp], st),
             "gcal_workspace_bytes": ([i64, i32, i32, i32, i32, i32], ctypes.c_int64),
             "cf_set_mueller": ([vp, vp, vp, vp], st),
+            "awg_debug_fail_allocations": ([ctypes.c_int64], st),
+            "awg_debug_live_allocations": ([], ctypes.c_int64),
             "gcal_solve": ([vp, vp, vp, i64, i32, i32, i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
                             i32, i32, vp, vp, vp, vp], st),
         }

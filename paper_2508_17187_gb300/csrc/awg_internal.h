@@ -183,6 +183,15 @@ void count_launches(int n);
 // Error state (thread-local message).
 awg_status set_error(awg_status st, const std::string& msg);
 awg_status cuda_error(cudaError_t e, const char* where);
+// Every device allocation of the library goes through dev_alloc / dev_free: they count the live
+// allocations, and a test hook (awg_debug_fail_allocations) can make the n-th allocation fail as
+// out of memory without reaching the driver.
+cudaError_t dev_alloc_raw(void** p, size_t bytes);
+void dev_free(void* p);
+template <typename T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc_raw(reinterpret_cast<void**>(p), bytes);
+}
 
 #define AWG_CUDA_TRY(expr)                                  \
   do {                                                      \

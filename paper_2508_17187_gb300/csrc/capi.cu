@@ -26,6 +26,31 @@ awg_status set_error(awg_status st, const std::string& msg) {
   return st;
 }
 
+// Allocations left before an injected out-of-memory failure (-1: no injection), and the number
+// of live device allocations.
+static std::atomic<int64_t> g_fail_after{-1};
+static std::atomic<int64_t> g_live_allocs{0};
+
+cudaError_t dev_alloc_raw(void** p, size_t bytes) {
+  int64_t left = g_fail_after.load();
+  while (left >= 0) {
+    if (left == 0) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  g_live_allocs.fetch_sub(1);
+}
+
 awg_status cuda_error(cudaError_t e, const char* where) {
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
@@ -112,13 +137,13 @@ void fill_slots(CfSetImpl* cf) {
 
 static void free_cf(CfSetImpl* cf) {
   if (!cf) return;
-  cudaFree(cf->d_data);
-  cudaFree(cf->d_off);
-  cudaFree(cf->d_sup);
-  cudaFree(cf->d_inv_taper);
-  cudaFree(cf->d_sep);
-  cudaFree(cf->d_sep_off);
-  cudaFree(cf->d_mix);
+  dev_free(cf->d_data);
+  dev_free(cf->d_off);
+  dev_free(cf->d_sup);
+  dev_free(cf->d_inv_taper);
+  dev_free(cf->d_sep);
+  dev_free(cf->d_sep_off);
+  dev_free(cf->d_mix);
   delete cf;
 }
 
@@ -161,16 +186,16 @@ static awg_status alloc_cf(CfSetImpl* cf, cudaStream_t st) {
   AWG_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   if (bytes + (size_t)(256u << 20) > free_b)
     return set_error(AWG_ERR_OOM, "CF set of " + std::to_string(bytes >> 20) + " MiB does not fit in device memory");
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_data, bytes));
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_off, sizeof(int64_t) * cf->n_cf));
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_data, bytes));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_off, sizeof(int64_t) * cf->n_cf));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_off, cf->offsets.data(), sizeof(int64_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sup, cf->supports.data(), sizeof(int32_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
   std::vector<double> taper;
   taper_image(cf->p, taper);
   std::vector<float> inv(cf->p.grid_n);
   for (int i = 0; i < cf->p.grid_n; ++i) inv[i] = (float)(1.0 / taper[i]);
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_inv_taper, inv.data(), sizeof(float) * cf->p.grid_n, cudaMemcpyHostToDevice, st));
   AWG_CUDA_TRY(cudaStreamSynchronize(st));
   fill_slots(cf);
@@ -217,19 +242,19 @@ static awg_status upload_separable(CfSetImpl* cf, const std::vector<std::vector<
       }
     }
   }
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep, sizeof(float) * h.size()));
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sep_off, sizeof(int64_t) * cf->sep_offsets.size()));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_sep, sizeof(float) * h.size()));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_sep_off, sizeof(int64_t) * cf->sep_offsets.size()));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sep_off, cf->sep_offsets.data(), sizeof(int64_t) * cf->sep_offsets.size(),
                                cudaMemcpyHostToDevice, st));
   // the support / offset bookkeeping the plan and the kernels share with the 2-D layout
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_sup, sizeof(int32_t) * cf->n_cf));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_sup, cf->supports.data(), sizeof(int32_t) * cf->n_cf, cudaMemcpyHostToDevice, st));
   std::vector<double> taper;
   taper_image(cf->p, taper);
   std::vector<float> inv(cf->p.grid_n);
   for (int i = 0; i < cf->p.grid_n; ++i) inv[i] = (float)(1.0 / taper[i]);
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_inv_taper, sizeof(float) * cf->p.grid_n));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_inv_taper, inv.data(), sizeof(float) * cf->p.grid_n, cudaMemcpyHostToDevice, st));
   AWG_CUDA_TRY(cudaStreamSynchronize(st));
   fill_slots(cf);
@@ -340,7 +365,7 @@ static awg_status upload_mix(CfSetImpl* cf, cudaStream_t st) {
     mix[(size_t)k * 32 + 4 * qq + pp] = make_float2(sr, -si);
     mix[(size_t)k * 32 + 16 + 4 * pp + qq] = make_float2(sr, si);
   }
-  AWG_CUDA_TRY(cudaMalloc(&cf->d_mix, sizeof(float2) * mix.size()));
+  AWG_CUDA_TRY(dev_alloc(&cf->d_mix, sizeof(float2) * mix.size()));
   AWG_CUDA_TRY(cudaMemcpyAsync(cf->d_mix, mix.data(), sizeof(float2) * mix.size(), cudaMemcpyHostToDevice, st));
   AWG_CUDA_TRY(cudaStreamSynchronize(st));
   return AWG_OK;
@@ -394,6 +419,14 @@ static CfSetImpl* new_cf_set(const awg_cf_params* params) {
 using namespace awg;
 
 extern "C" {
+
+awg_status awg_debug_fail_allocations(int64_t after) {
+  if (after < -1) return set_error(AWG_ERR_INVALID_ARG, "after must be >= -1");
+  g_fail_after.store(after);
+  return AWG_OK;
+}
+
+int64_t awg_debug_live_allocations(void) { return g_live_allocs.load(); }
 
 const char* awg_last_error(void) { return g_last_error.c_str(); }
 
@@ -879,25 +912,25 @@ awg_status cf_set_copy_table(awg_cf_set h, int32_t ci, float* out) {
 
 static awg_status plan_free(PlanImpl* pl) {
   if (!pl) return AWG_OK;
-  cudaFree(pl->d_rec);
-  cudaFree(pl->d_rec_tmp);
-  cudaFree(pl->d_part);
-  cudaFree(pl->d_key);
-  cudaFree(pl->d_drop);
-  cudaFree(pl->d_bcount);
-  cudaFree(pl->d_boff);
-  cudaFree(pl->d_icount);
-  cudaFree(pl->d_ioff);
-  cudaFree(pl->d_scan_tmp);
-  cudaFree(pl->d_items);
-  cudaFree(pl->d_class_range);
-  cudaFree(pl->d_slot_range);
-  cudaFree(pl->d_queue);
-  cudaFree(pl->d_counters);
-  cudaFree(pl->d_uvw);
-  cudaFree(pl->d_freq);
-  cudaFree(pl->d_row_dlm);
-  cudaFree(pl->d_phasor);
+  dev_free(pl->d_rec);
+  dev_free(pl->d_rec_tmp);
+  dev_free(pl->d_part);
+  dev_free(pl->d_key);
+  dev_free(pl->d_drop);
+  dev_free(pl->d_bcount);
+  dev_free(pl->d_boff);
+  dev_free(pl->d_icount);
+  dev_free(pl->d_ioff);
+  dev_free(pl->d_scan_tmp);
+  dev_free(pl->d_items);
+  dev_free(pl->d_class_range);
+  dev_free(pl->d_slot_range);
+  dev_free(pl->d_queue);
+  dev_free(pl->d_counters);
+  dev_free(pl->d_uvw);
+  dev_free(pl->d_freq);
+  dev_free(pl->d_row_dlm);
+  dev_free(pl->d_phasor);
   delete pl;
   return AWG_OK;
 }
@@ -945,7 +978,7 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
   const size_t nr = (size_t)std::max<int64_t>(pl->n_rec, 1);
   const size_t nb = (size_t)pl->n_buckets + 1;
   cudaError_t e = cudaSuccess;
-  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = dev_alloc(p, bytes); };
   A((void**)&pl->d_rec, nr * sizeof(SampleRec));
   A((void**)&pl->d_rec_tmp, nr * sizeof(SampleRec));
   A((void**)&pl->d_key, nr * sizeof(int32_t));
@@ -988,7 +1021,7 @@ awg_status plan_set_row_phase(awg_plan h, const double* row_dlm, const double* u
   if (!row_dlm) {   // back to the plan-wide shift (or none)
     if (pl->d_row_dlm) {
       AWG_CUDA_TRY(cudaStreamSynchronize(st));
-      cudaFree(pl->d_row_dlm);
+      dev_free(pl->d_row_dlm);
       pl->d_row_dlm = nullptr;
     }
     pl->has_phase = pl->global_phase;
@@ -996,10 +1029,10 @@ awg_status plan_set_row_phase(awg_plan h, const double* row_dlm, const double* u
   }
   if (pl->R > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
   const size_t R = (size_t)std::max<int64_t>(pl->R, 1);
-  if (!pl->d_row_dlm) AWG_CUDA_TRY(cudaMalloc(&pl->d_row_dlm, R * 2 * sizeof(double)));
-  if (!pl->d_uvw) AWG_CUDA_TRY(cudaMalloc(&pl->d_uvw, R * 3 * sizeof(double)));
-  if (!pl->d_freq) AWG_CUDA_TRY(cudaMalloc(&pl->d_freq, (size_t)pl->C * sizeof(double)));
-  if (!pl->d_phasor) AWG_CUDA_TRY(cudaMalloc(&pl->d_phasor, (size_t)std::max<int64_t>(pl->n, 1) * sizeof(float2)));
+  if (!pl->d_row_dlm) AWG_CUDA_TRY(dev_alloc(&pl->d_row_dlm, R * 2 * sizeof(double)));
+  if (!pl->d_uvw) AWG_CUDA_TRY(dev_alloc(&pl->d_uvw, R * 3 * sizeof(double)));
+  if (!pl->d_freq) AWG_CUDA_TRY(dev_alloc(&pl->d_freq, (size_t)pl->C * sizeof(double)));
+  if (!pl->d_phasor) AWG_CUDA_TRY(dev_alloc(&pl->d_phasor, (size_t)std::max<int64_t>(pl->n, 1) * sizeof(float2)));
   if (pl->R > 0) {
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_row_dlm, row_dlm, R * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     AWG_CUDA_TRY(cudaMemcpyAsync(pl->d_uvw, uvw_m, R * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));

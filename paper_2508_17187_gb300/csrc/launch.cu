@@ -444,7 +444,7 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
   float *vis = nullptr, *wt = nullptr, *grid = nullptr, *out = nullptr;
   double* sumwt = nullptr;
   cudaError_t e = cudaSuccess;
-  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = dev_alloc(p, bytes); };
   A((void**)&vis, sizeof(float2) * std::max<int64_t>(n * P, 1));
   A((void**)&wt, sizeof(float) * std::max<int64_t>(n * P, 1));
   A((void**)&out, sizeof(float2) * std::max<int64_t>(n * P, 1));
@@ -454,7 +454,7 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
   for (auto& x : ev)
     if (e == cudaSuccess) e = cudaEventCreate(&x);
   auto cleanup = [&]() {
-    cudaFree(vis); cudaFree(wt); cudaFree(out); cudaFree(grid); cudaFree(sumwt);
+    dev_free(vis); dev_free(wt); dev_free(out); dev_free(grid); dev_free(sumwt);
     for (auto& x : ev)
       if (x) cudaEventDestroy(x);
   };
