@@ -1,7 +1,9 @@
-"""Multi-rank path on CPU (gloo, world size 2): every rank grids its own slice of integrations and
-one all-reduce sums the planes, which must equal gridding the whole track (the accumulation over
-time of Eq. ResIm).  The per-rank gridding here is the oracle; the GPU ranks run the library in
-its place, with NCCL instead of gloo."""
+"""Multi-rank path on CPU (gloo, world size 2 and 3): every rank grids its own slice of
+integrations and one all-reduce sums the planes, which must equal gridding the whole track (the
+accumulation over time of Eq. ResIm); the per-rank gridding here is the oracle, the GPU ranks run
+the library in its place, with NCCL instead of gloo.  A rank that fails before the collective
+(it raises and exits) is detected by the others, whose all-reduce fails; they form a new group and
+take over its partitions (paper_2508_17187_gb300.elastic)."""
 import os
 import socket
 
@@ -88,3 +90,52 @@ def _patched_rank(rank, world, port, n_int, out):
     import synth
     synth.CONFIGS["wproj"] = dict(synth.CONFIGS["wproj"], n_chan=4, grid_n=512, n_wplanes=6, max_support=24)
     _rank_main(rank, world, port, n_int, out)
+
+
+def _failover_rank(rank, world, port, n_parts, fail_rank, out_path):
+    """One rank of the failover test: the partitions' partial sums are small integer tensors (each
+    partition p contributes p + 1 in slot p), so the recovered total is checked exactly."""
+    import datetime
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_2508_17187_gb300 import elastic
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=datetime.timedelta(seconds=60))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+
+    def compute(parts):
+        t = torch.zeros(n_parts, dtype=torch.float64)
+        for p in parts:
+            t[p] += p + 1
+        return [t, torch.tensor([float(len(parts))], dtype=torch.float64)]
+
+    if rank == fail_rank:
+        raise SystemExit(3)   # the failure: this rank leaves before the collective
+    sums, failed = elastic.reduce_with_recovery(compute, n_parts, rank, world, store, timeout_s=10.0, grace_s=2.0)
+    np.save(f"{out_path}.{rank}.npy", np.concatenate([sums[0].numpy(), sums[1].numpy(), np.array(failed, float)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,fail_rank", [(2, 1), (3, 2), (3, 1)])
+def test_rank_failure_is_detected_and_its_partitions_regridded(tmp_path, world, fail_rank):
+    """A rank that leaves before the all-reduce: the others' collective fails, the survivors form a
+    new group, split the failed rank's partitions between them and still sum every partition once."""
+    n_parts = 7
+    port = _free_port()
+    out = str(tmp_path / "sums")
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_failover_rank, args=(r, world, port, n_parts, fail_rank, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    for r, p in enumerate(procs):
+        assert p.exitcode == (3 if r == fail_rank else 0), (r, p.exitcode)
+    want = np.arange(1, n_parts + 1, dtype=float)
+    for r in range(world):
+        if r == fail_rank:
+            continue
+        got = np.load(f"{out}.{r}.npy")
+        assert np.array_equal(got[:n_parts], want)        # every partition summed exactly once
+        assert got[n_parts] == n_parts                     # partitions gridded over all survivors
+        assert list(got[n_parts + 1:]) == [fail_rank]
