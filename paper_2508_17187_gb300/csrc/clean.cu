@@ -61,15 +61,29 @@ __device__ BestPix block_best(BestPix b) {
   return b;   // valid in thread 0
 }
 
+// Largest |residual| of the window per block: block b takes window rows y0 + b, y0 + b + gridDim.x,
+// ...; its threads stride the columns (coalesced, no division per pixel), 4 at a time with float4
+// loads when the window's columns and the row pitch are multiples of 4 (VEC).
+template <bool VEC>
 __global__ void __launch_bounds__(kCleanThreads) k_absmax_partial(const float* __restrict__ res, int N, int x0, int x1,
                                                                    int y0, int y1, BestPix* __restrict__ part) {
-  const int w = x1 - x0;
-  const int64_t total = (int64_t)w * (y1 - y0);
   BestPix b{-1.f, 0x7fffffff};
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-    const int y = y0 + (int)(k / w), x = x0 + (int)(k % w);
-    const int i = y * N + x;
-    b = better(b, BestPix{fabsf(res[i]), i});
+  for (int y = y0 + blockIdx.x; y < y1; y += gridDim.x) {
+    const float* row = res + (size_t)y * N;
+    if constexpr (VEC) {
+#pragma unroll 2
+      for (int x = x0 + 4 * threadIdx.x; x < x1; x += 4 * blockDim.x) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(row + x));
+        const int i = y * N + x;
+        b = better(b, BestPix{fabsf(v.x), i});
+        b = better(b, BestPix{fabsf(v.y), i + 1});
+        b = better(b, BestPix{fabsf(v.z), i + 2});
+        b = better(b, BestPix{fabsf(v.w), i + 3});
+      }
+    } else {
+#pragma unroll 4
+      for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) b = better(b, BestPix{fabsf(__ldg(row + x)), y * N + x});
+    }
   }
   b = block_best(b);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
@@ -96,17 +110,38 @@ __global__ void __launch_bounds__(1024) k_absmax_final(const BestPix* __restrict
   }
 }
 
-__global__ void k_subtract_psf(float* __restrict__ res, const float* __restrict__ psf, int N, int Np,
-                               const CleanState* __restrict__ st) {
+// residual[y][x] -= g peak psf[y - py + Np/2][x - px + Np/2] where that PSF pixel exists: each
+// thread takes 4 consecutive columns of rows blockIdx.y, blockIdx.y + gridDim.y, ... (one float4 of
+// the residual when N is a multiple of 4), each product rounded before the subtraction.
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_subtract_psf(float* __restrict__ res, const float* __restrict__ psf, int N,
+                                                      int Np, const CleanState* __restrict__ st) {
   const float gp = st->gp;
   if (gp == 0.f) return;
   const int py = st->idx / N, px = st->idx - (st->idx / N) * N;
-  const int64_t total = (int64_t)N * N;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(k / N), x = (int)(k - (int64_t)y * N);
-    const int dy = y - py + Np / 2, dx = x - px + Np / 2;
-    if (dy < 0 || dy >= Np || dx < 0 || dx >= Np) continue;
-    res[k] = __fsub_rn(res[k], __fmul_rn(gp, psf[(int64_t)dy * Np + dx]));
+  const int xs = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (xs >= N) return;
+  const int dx0 = xs - px + Np / 2;
+  for (int y = blockIdx.y; y < N; y += gridDim.y) {
+    const int dy = y - py + Np / 2;
+    if (dy < 0 || dy >= Np) continue;
+    float* r = res + (size_t)y * N + xs;
+    const float* q = psf + (size_t)dy * Np;
+    if constexpr (VEC) {
+      float4 v = *reinterpret_cast<float4*>(r);
+      float* e = &v.x;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int dx = dx0 + i;
+        if (dx >= 0 && dx < Np) e[i] = __fsub_rn(e[i], __fmul_rn(gp, __ldg(q + dx)));
+      }
+      *reinterpret_cast<float4*>(r) = v;
+    } else {
+      for (int i = 0; i < 4 && xs + i < N; ++i) {
+        const int dx = dx0 + i;
+        if (dx >= 0 && dx < Np) r[i] = __fsub_rn(r[i], __fmul_rn(gp, __ldg(q + dx)));
+      }
+    }
   }
 }
 
@@ -151,14 +186,20 @@ extern "C" awg_status clean_hogbom(float* residual, float* model, int32_t N, con
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t wpix = (int64_t)(x1 - x0) * (y1 - y0);
-  const int nb = (int)std::min<int64_t>(kCleanBlocks, (wpix + kCleanThreads - 1) / kCleanThreads);
+  const int nb = std::min(kCleanBlocks, y1 - y0);   // peak search: window rows over up to kCleanBlocks blocks
+  const bool vec4_search = N % 4 == 0 && x0 % 4 == 0 && (x1 - x0) % 4 == 0 && ((uintptr_t)residual & 15) == 0;
+  // subtraction: 4 columns per thread, 256 threads per block in x, rows over about 8 blocks per SM
+  const bool vec = N % 4 == 0 && ((uintptr_t)residual & 15) == 0;
+  const int gx = (N + 4 * 256 - 1) / (4 * 256);
+  const dim3 sub_grid(gx, (unsigned)std::max(1, std::min(N, std::max(sms, 1) * 8 / gx)));
   k_clean_init<<<1, 1, 0, s>>>(st);
   AWG_CUDA_TRY(cudaGetLastError());
   for (int it = 0; it < n_iter; ++it) {
-    k_absmax_partial<<<nb, kCleanThreads, 0, s>>>(residual, N, x0, x1, y0, y1, part);
+    if (vec4_search) k_absmax_partial<true><<<nb, kCleanThreads, 0, s>>>(residual, N, x0, x1, y0, y1, part);
+    else k_absmax_partial<false><<<nb, kCleanThreads, 0, s>>>(residual, N, x0, x1, y0, y1, part);
     k_absmax_final<<<1, 1024, 0, s>>>(part, nb, residual, model, gain, threshold, st);
-    k_subtract_psf<<<std::max(sms, 1) * 8, 256, 0, s>>>(residual, psf, N, psf_n, st);
+    if (vec) k_subtract_psf<true><<<sub_grid, 256, 0, s>>>(residual, psf, N, psf_n, st);
+    else k_subtract_psf<false><<<sub_grid, 256, 0, s>>>(residual, psf, N, psf_n, st);
   }
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(1 + 3 * n_iter);

@@ -907,11 +907,19 @@ constexpr int fused_stage() {
   else return fused_stage<S, T, P, RK, ST0 / 2>();
 }
 
+// Staging depth the fused kernels start from: configuration 0's, except where a sweep of the batched
+// AW-projection workload (4 terms, 4 pols; per-launch times) found twice the depth faster:
+// gridding at support 40 (45.4 -> 41.9 ms) and degridding at support 32 (31.9 -> 31.3 ms).  Deeper
+// staging elsewhere cost occupancy (e.g. support 24: 18.4 -> 26 ms).
+constexpr int fused_stage0(int S, int P, int RK, bool grid, int base) {
+  return P == 4 && RK == 4 && ((grid && S == 40) || (!grid && S == 32)) ? 2 * base : base;
+}
+
 template <int S, int P, int RK, bool MIX = false>
 awg_status run_grid_fused(const GridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr ExactCfg e = exact_cfg(S, 0);
   constexpr int nt = S * e.g_grid;
-  constexpr int stage = fused_stage<S, e.tile, P, RK, e.stage>();
+  constexpr int stage = fused_stage<S, e.tile, P, RK, fused_stage0(S, P, RK, true, e.stage)>();
   using L = SepLayout<S, e.tile, P, stage, RK>;
   static_assert(L::bytes <= 227 * 1024, "fused gridding window does not fit in shared memory");
   auto kern = k_grid_sep<S - 1, S, nt, e.tile, P, stage, RK, MIX>;
@@ -931,7 +939,7 @@ template <int S, int P, int RK, bool MIX = false>
 awg_status run_degrid_fused(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr ExactCfg e = exact_cfg(S, 0);
   constexpr int nt = S * e.g_degrid;
-  constexpr int stage = fused_stage<S, e.tile, P, RK, e.stage>();
+  constexpr int stage = fused_stage<S, e.tile, P, RK, fused_stage0(S, P, RK, false, e.stage)>();
   using L = SepLayout<S, e.tile, P, stage, RK>;
   static_assert(L::bytes <= 227 * 1024, "fused degridding window does not fit in shared memory");
   auto kern = k_degrid_sep<S - 1, S, nt, e.tile, P, stage, RK, MIX>;

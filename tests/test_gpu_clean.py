@@ -11,11 +11,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _dirty(N, n_src, seed):
-    """A PSF with a main lobe and ringing sidelobes, and a residual made of PSF-convolved point
-    sources plus noise (FP32)."""
+def _dirty(N, n_src, seed, Np=None):
+    """A PSF (Np x Np, default 2N) with a main lobe and ringing sidelobes, and a residual made of
+    PSF-convolved point sources plus noise (FP32)."""
     rng = np.random.default_rng(seed)
-    Np = 2 * N
+    Np = Np or 2 * N
     yy, xx = np.mgrid[0:Np, 0:Np].astype(np.float64)
     r = np.hypot(yy - Np // 2, xx - Np // 2)
     psf = (np.exp(-r ** 2 / 8.0) + 0.15 * np.cos(r / 2.5) * np.exp(-r / 40.0)).astype(np.float32)
@@ -24,16 +24,21 @@ def _dirty(N, n_src, seed):
     for _ in range(n_src):
         y, x = rng.integers(N // 8, 7 * N // 8, 2)
         a = np.float32(rng.uniform(0.2, 1.0))
-        img += a * psf[Np // 2 - y:Np // 2 - y + N, Np // 2 - x:Np // 2 - x + N]
+        ya, yb = max(0, y - Np // 2), min(N, y - Np // 2 + Np)
+        xa, xb = max(0, x - Np // 2), min(N, x - Np // 2 + Np)
+        img[ya:yb, xa:xb] += a * psf[ya - y + Np // 2:yb - y + Np // 2, xa - x + Np // 2:xb - x + Np // 2]
     return psf, img.astype(np.float32)
 
 
-@pytest.mark.parametrize("window", [None, (64, 192, 40, 200)])
-def test_clean_matches_oracle_bit_for_bit(window):
+@pytest.mark.parametrize("N,Np,window", [(256, None, None), (256, None, (64, 192, 40, 200)), (256, None, (3, 250, 5, 200)),
+                                         (250, 101, None), (250, 101, (3, 247, 10, 11))])
+def test_clean_matches_oracle_bit_for_bit(N, Np, window):
+    """N = 256: float4 subtraction and (4-aligned windows) float4 peak search, PSF covering the
+    image; an unaligned window takes the scalar search; N = 250 with a 101-pixel PSF: the scalar
+    paths and a PSF that overlaps only part of the image (and a one-row window)."""
     import paper_2508_17187_gb300 as awg
     from oracle import clean
-    N = 256
-    psf, img = _dirty(N, 30, 11)
+    psf, img = _dirty(N, 30, 11, Np)
     res_o, model_o, comps = clean.hogbom(img, psf, 400, 0.1, threshold=0.05, window=window)
     res = torch.as_tensor(img).cuda()
     model = torch.zeros_like(res)
