@@ -238,8 +238,9 @@ def fp32_alu_peak_tflops(sms: int, mhz: float) -> float:
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def run_cpu_baseline(wl, every: int):
-    """Time the FP64 oracle (G and D, OpenMP over all cores) on every `every`-th integration."""
+def run_cpu_baseline(wl, every: int, single_thread: bool = False):
+    """Time the FP64 oracle (G and D, OpenMP over all cores) on every `every`-th integration, and
+    with single_thread also on one thread over a tenth of that sample."""
     from oracle import cf as ocf
     from oracle import index as oindex
     from oracle import ops as oops
@@ -259,10 +260,44 @@ def run_cpu_baseline(wl, every: int):
     d = oops.degrid(idx, buf, off, wl.oversampling, g, nthreads=threads)
     t2 = time.perf_counter()
     n_vis = int(idx.valid.size) * wl.n_pol
-    return {"value": 2 * n_vis / (t2 - t0), "unit": "visibilities/s", "cores": threads, "kind": "oracle",
-            "sample": f"every {every}th integration: {len(rows)} rows x {wl.n_chan} channels x {wl.n_pol} pols "
-                      f"= {n_vis} visibilities, gridded then degridded (grid {t1 - t0:.2f} s, degrid {t2 - t1:.2f} s)",
-            "seconds": t2 - t0, "rows": rows, "grid": g, "degrid": d}
+    out = {"value": 2 * n_vis / (t2 - t0), "unit": "visibilities/s", "cores": threads, "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": f"every {every}th integration: {len(rows)} rows x {wl.n_chan} channels x {wl.n_pol} pols "
+                     f"= {n_vis} visibilities, gridded then degridded (grid {t1 - t0:.2f} s, degrid {t2 - t1:.2f} s)",
+           "seconds": t2 - t0, "rows": rows, "grid": g, "degrid": d}
+    if single_thread and len(rows) >= 10 * wl.n_bl:
+        # one thread on the first tenth of the sample's integrations
+        sub = rows[:len(rows) // 10 // wl.n_bl * wl.n_bl]
+        idx1 = oindex.sample_index(op, wl.uvw_m[sub], wl.freq_hz)
+        v1 = np.asarray(wl.vis)[sub].reshape(-1, wl.n_pol)
+        w1 = np.asarray(wl.weight)[sub].reshape(-1, wl.n_pol)
+        t0 = time.perf_counter()
+        g1, _ = oops.grid(idx1, buf, off, wl.oversampling, wl.grid_n, v1, w1, nthreads=1)
+        oops.degrid(idx1, buf, off, wl.oversampling, g1, nthreads=1)
+        t1 = time.perf_counter()
+        n1 = int(idx1.valid.size) * wl.n_pol
+        out["single_thread"] = {"value": 2 * n1 / (t1 - t0), "unit": "visibilities/s",
+                                "sample": f"{len(sub)} rows of the sample ({n1} visibilities), 1 thread"}
+    return out
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    import subprocess
+    try:
+        for ln in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def sample_accuracy(cf, wl, vis, wt, cb, dev) -> dict:
@@ -302,6 +337,51 @@ def sample_accuracy(cf, wl, vis, wt, cb, dev) -> dict:
            "sample": "the cpu_baseline sample, FP64 oracle vs the library"}
     plan.close()
     return err
+
+
+def plain_fp64_on_sample(wl, vis, wt, cb, dev) -> dict:
+    """The plain FP64 GPU baseline (one launch per channel, full CF tables, FP64 grid) on the
+    cpu_baseline sample: its throughput and its error against the oracle."""
+    import ctypes
+
+    import torch
+
+    import paper_2508_17187_gb300 as awg
+    from paper_2508_17187_gb300 import _lib
+    lib = _lib.load()
+    cf = awg.cf_set_create(**cf_kwargs(wl), separable=False)
+    rows = torch.as_tensor(cb["rows"], device=dev)
+    uvw = torch.as_tensor(wl.uvw_m, device=dev)[rows].contiguous()
+    v, w = vis[rows].contiguous(), wt[rows].contiguous()
+    R, C, P, N = len(cb["rows"]), wl.n_chan, wl.n_pol, wl.grid_n
+    fr = np.ascontiguousarray(wl.freq_hz)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    g64 = torch.zeros((N, N, P), dtype=torch.complex128, device=dev)
+    sw = torch.zeros(P, dtype=torch.float64, device=dev)
+    out = torch.empty_like(v)
+    g_o = torch.as_tensor(cb["grid"], device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    rc = lib.grid_visibilities_plain_fp64(cf.handle, vp(uvw), R, fr.ctypes.data_as(ctypes.c_void_p), C, 0, C, None,
+                                          None, vp(v), vp(w), P, vp(g64), vp(sw), st)
+    e[1].record()
+    assert rc == 0, lib.awg_last_error()
+    g_err = float(torch.linalg.vector_norm(g64 - g_o) / torch.linalg.vector_norm(g_o))
+    g64.copy_(g_o)
+    e[2].record()
+    rc = lib.degrid_visibilities_plain_fp64(cf.handle, vp(uvw), R, fr.ctypes.data_as(ctypes.c_void_p), C, 0, C, None,
+                                            None, vp(g64), vp(out), P, st)
+    e[3].record()
+    assert rc == 0, lib.awg_last_error()
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) + e[2].elapsed_time(e[3])
+    d_o = torch.as_tensor(cb["degrid"], device=dev).reshape(out.shape)
+    d_err = float(torch.linalg.vector_norm(out.to(torch.complex128) - d_o) / torch.linalg.vector_norm(d_o))
+    n_vis = R * C * P
+    cf.close()
+    return {"value": 2 * n_vis / (ms / 1e3), "unit": "visibilities/s", "grid_rel_rms": g_err, "degrid_rel_rms": d_err,
+            "sample": "the cpu_baseline sample: one FP64 launch per channel over full CF tables (CUDA events)"}
 
 
 def reference_arm(args):
@@ -878,8 +958,9 @@ def main():
         line["executed_tflops"] = {k: mult * ops[k]["tflops"] for k in ops}
     if not args.no_cpu_baseline and CONFIG == "wproj" and not args.mosaic:
         host_wl = dataclasses.replace(wl, vis=vis.cpu().numpy(), weight=wt.cpu().numpy())
-        cb = run_cpu_baseline(host_wl, args.cpu_sample_every or 40)
+        cb = run_cpu_baseline(host_wl, args.cpu_sample_every or 40, single_thread=True)
         line["accuracy"] = sample_accuracy(cf, wl, vis, wt, cb, dev)
+        line["plain_fp64_gpu"] = plain_fp64_on_sample(wl, vis, wt, cb, dev)
         for k in ("seconds", "rows", "grid", "degrid"):
             cb.pop(k)
         line["cpu_baseline"] = cb
