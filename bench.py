@@ -852,18 +852,50 @@ def main():
         h_grid = torch.empty(grid.shape, dtype=grid.dtype).pin_memory()
         h_sw = torch.empty(sumwt.shape, dtype=sumwt.dtype).pin_memory()
 
+        # Two buffer sets and three streams: step k+1's inputs are copied in (s_in) while step k
+        # computes, and step k's results are copied out (s_out) while step k+1 computes.  Each
+        # copy waits for the compute that last used its buffers; every step still copies all its
+        # inputs in and all its results out inside the timed region.
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        ins = [(vis, wt, uvw, freq, pa_bin, chan_sb),
+               tuple(torch.empty_like(t) if t is not None else None for t in (vis, wt, uvw, freq, pa_bin, chan_sb))]
+        outs = [(vis_out, grid, sumwt), (torch.empty_like(vis_out), torch.empty_like(grid), torch.empty_like(sumwt))]
+        ev_in, ev_comp, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+        k_step = [0]
+
         def e2e_step():
-            vis.copy_(h_vis, non_blocking=True)
-            wt.copy_(h_wt, non_blocking=True)
-            uvw.copy_(h_uvw, non_blocking=True)
-            freq.copy_(h_freq, non_blocking=True)
-            if h_pa is not None:
-                pa_bin.copy_(h_pa, non_blocking=True)
-                chan_sb.copy_(h_sb, non_blocking=True)
-            step()
-            h_out.copy_(vis_out, non_blocking=True)
-            h_grid.copy_(grid, non_blocking=True)
-            h_sw.copy_(sumwt, non_blocking=True)
+            i = k_step[0] % 2
+            k_step[0] += 1
+            v, w, u, f, pa, sb = ins[i]
+            vo, g, sw = outs[i]
+            s_in.wait_event(ev_comp[i])
+            with torch.cuda.stream(s_in):
+                v.copy_(h_vis, non_blocking=True)
+                w.copy_(h_wt, non_blocking=True)
+                u.copy_(h_uvw, non_blocking=True)
+                f.copy_(h_freq, non_blocking=True)
+                if h_pa is not None:
+                    pa.copy_(h_pa, non_blocking=True)
+                    sb.copy_(h_sb, non_blocking=True)
+                ev_in[i].record(s_in)
+            stream.wait_event(ev_in[i])
+            stream.wait_event(ev_out[i])
+            plan.update(u, f, pa, sb)
+            g.zero_()
+            sw.zero_()
+            awg.grid_visibilities(cf, plan, v, w, g, sw)
+            if world > 1:
+                dist.all_reduce(torch.view_as_real(g))
+                dist.all_reduce(sw)
+            awg.grid_normalize(cf, g, sw, direction=0)
+            awg.degrid_visibilities(cf, plan, mgrid, vo)
+            ev_comp[i].record(stream)
+            s_out.wait_event(ev_comp[i])
+            with torch.cuda.stream(s_out):
+                h_out.copy_(vo, non_blocking=True)
+                h_grid.copy_(g, non_blocking=True)
+                h_sw.copy_(sw, non_blocking=True)
+                ev_out[i].record(s_out)
 
         for _ in range(2):
             e2e_step()
@@ -871,8 +903,11 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        s_in.wait_event(e0)
         for _ in range(args.steps):
             e2e_step()
+        for x in ev_out:
+            stream.wait_event(x)
         e1.record(stream)
         barrier()
         e_ms = e0.elapsed_time(e1) / args.steps

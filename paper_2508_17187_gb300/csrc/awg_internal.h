@@ -34,9 +34,11 @@ __host__ __device__ constexpr int class_of_support(int S) {
 // row groups G of the gridding and degridding kernels (each thread owns S / G rows of one column
 // residue; S * G threads per CTA, a whole number of warps), the tile of first-tap positions per
 // work item, which the plan uses for these supports when the CF set is separable, and the
-// samples staged per chunk.  Small tiles and shallow stages let two CTAs share an SM.  Every
-// support has kNumCand compiled candidates; candidate 0 is the default and cf_set_autotune picks
-// per support by timing.  The supports listed here and AWG_FOR_EXACT_AND_POLS must agree.
+// samples staged per chunk.  Small tiles let two CTAs share an SM; deeper stages spread the
+// barriers of a chunk (and the unequal flush work between warps) over more samples, which won
+// where two CTAs still fit (candidate 1 of supports 24-56: 1-3% on the W-projection workload).
+// Every support has kNumCand compiled candidates; candidate 0 is the default and cf_set_autotune
+// picks per support by timing.  The supports listed here and AWG_FOR_EXACT_AND_POLS must agree.
 struct ExactCfg {
   int S, g_grid, g_degrid, tile, stage;
 };
@@ -55,11 +57,11 @@ constexpr ExactCfg kExactCand[kNumCand][8] = {
     {
         {8, 8, 8, 16, 8},
         {16, 16, 16, 32, 16},
-        {24, 8, 8, 8, 8},
-        {32, 8, 8, 8, 8},
-        {40, 8, 8, 16, 8},
-        {48, 8, 8, 8, 8},
-        {56, 8, 8, 8, 8},
+        {24, 8, 8, 8, 16},
+        {32, 8, 8, 8, 16},
+        {40, 8, 8, 8, 12},
+        {48, 8, 8, 8, 16},
+        {56, 8, 8, 8, 16},
         {64, 8, 8, 8, 4},
     },
 };
