@@ -8,7 +8,7 @@
 // k_scatter : counting-sort scatter of the kept samples into bucket order.
 // k_items   : work items of at most kItemChunk samples per bucket; buckets are ordered by
 //             support, so the items of each kernel class form one contiguous range.
-// k_sort_items : samples of each item ordered by first-tap position (row-major).
+// k_sort_items : samples of each item ordered by first-tap position (row-major; counting sort).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -279,47 +279,108 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ key, const Samp
 }
 
 // Orders the samples of every work item by first-tap position, row-major (y, then x), with a
-// bitonic sort of up to kItemChunk records in shared memory.  Consecutive samples then share
-// their first-tap row for long runs and move right along it, so the gridding and degridding
-// kernels recompute their row state only at row changes and a thread's pixels change rarely.
-__global__ void __launch_bounds__(kItemChunk) k_sort_items(const int32_t* __restrict__ n_items_ptr,
-                                                          const WorkItem* __restrict__ items, SampleRec* rec) {
+// counting sort in shared memory: all first taps of an item lie in one tile of at most 32 x 32
+// positions, so the positions relative to the item's smallest x and y index at most kItemChunk
+// bins.  Each record takes its rank in its bin (shared-memory atomic), the bin counts are scanned,
+// and the records go back to the item's range in bin order (equal positions in atomic order).
+// Consecutive samples then share their first-tap row for long runs and move right along it, so
+// the gridding and degridding kernels recompute their row state only at row changes and a
+// thread's pixels change rarely.
+constexpr int kSortThreads = 256;
+constexpr int kSortPer = kItemChunk / kSortThreads;   // records and bins per thread
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_items(const int32_t* __restrict__ n_items_ptr,
+                                                             const WorkItem* __restrict__ items,
+                                                             SampleRec* __restrict__ rec) {
   __shared__ SampleRec s_rec[kItemChunk];
-  __shared__ unsigned s_key[kItemChunk];
-  __shared__ unsigned short s_idx[kItemChunk];
+  __shared__ int s_cnt[kItemChunk];
+  __shared__ unsigned short s_bin[kItemChunk];
+  __shared__ unsigned short s_rank[kItemChunk];
+  __shared__ int s_warp[kSortThreads / 32][4];
+  __shared__ int s_ext[4];
   const int n_items = *n_items_ptr;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const WorkItem wi = items[it];
-    if (t < wi.count) {
-      s_rec[t] = rec[wi.start + t];
-      s_key[t] = ((unsigned)s_rec[t].p0y << 16) | s_rec[t].p0x;
-    } else {
-      s_key[t] = 0xffffffffu;
+    const int n = wi.count;
+    // records into shared memory, with the smallest and largest first tap per axis
+    int mnx = 0x7fffffff, mny = 0x7fffffff, mxx = -1, mxy = -1;
+    for (int i = t; i < n; i += kSortThreads) {
+      const SampleRec r = rec[wi.start + i];
+      s_rec[i] = r;
+      mnx = min(mnx, (int)r.p0x);
+      mny = min(mny, (int)r.p0y);
+      mxx = max(mxx, (int)r.p0x);
+      mxy = max(mxy, (int)r.p0y);
     }
-    s_idx[t] = (unsigned short)t;
+    for (int o = 16; o > 0; o >>= 1) {
+      mnx = min(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+      mny = min(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+      mxx = max(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+      mxy = max(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    if (lane == 0) {
+      s_warp[wid][0] = mnx;
+      s_warp[wid][1] = mny;
+      s_warp[wid][2] = mxx;
+      s_warp[wid][3] = mxy;
+    }
     __syncthreads();
-    // the network of the item's own power of two (the padding keys sort last either way)
-    int n2 = 2;
-    while (n2 < wi.count) n2 <<= 1;
-    for (int k = 2; k <= n2; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const int ixj = t ^ j;
-        if (ixj > t) {
-          const bool up = (t & k) == 0;
-          const unsigned a = s_key[t], b = s_key[ixj];
-          if ((a > b) == up) {
-            s_key[t] = b;
-            s_key[ixj] = a;
-            const unsigned short ti = s_idx[t];
-            s_idx[t] = s_idx[ixj];
-            s_idx[ixj] = ti;
-          }
-        }
-        __syncthreads();
+    if (t == 0) {
+      int a = 0x7fffffff, b = 0x7fffffff, c = -1, d = -1;
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        a = min(a, s_warp[w][0]);
+        b = min(b, s_warp[w][1]);
+        c = max(c, s_warp[w][2]);
+        d = max(d, s_warp[w][3]);
       }
+      s_ext[0] = a;
+      s_ext[1] = b;
+      s_ext[2] = c - a + 1;   // extent in x
+      s_ext[3] = d - b + 1;   // extent in y
     }
-    if (t < wi.count) rec[wi.start + t] = s_rec[s_idx[t]];
+    __syncthreads();
+    const int x0 = s_ext[0], y0 = s_ext[1], ex = s_ext[2];
+    const int nb = n > 0 ? ex * s_ext[3] : 0;
+    if (nb > kItemChunk) {   // not one tile of at most 32 x 32 positions: leave the item as it is
+      __syncthreads();
+      continue;
+    }
+    for (int b = t; b < nb; b += kSortThreads) s_cnt[b] = 0;
+    __syncthreads();
+    for (int i = t; i < n; i += kSortThreads) {
+      const int b = ((int)s_rec[i].p0y - y0) * ex + ((int)s_rec[i].p0x - x0);
+      s_bin[i] = (unsigned short)b;
+      s_rank[i] = (unsigned short)atomicAdd(&s_cnt[b], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the bin counts: kSortPer consecutive bins per thread, then the threads
+    int v[kSortPer];
+    int run = 0;
+#pragma unroll
+    for (int k = 0; k < kSortPer; ++k) {
+      const int b = t * kSortPer + k;
+      v[k] = b < nb ? s_cnt[b] : 0;
+      run += v[k];
+    }
+    int incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid][0] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < wid; ++w) before += s_warp[w][0];
+    int off = before + incl - run;
+#pragma unroll
+    for (int k = 0; k < kSortPer; ++k) {
+      const int b = t * kSortPer + k;
+      if (b < nb) s_cnt[b] = off;
+      off += v[k];
+    }
+    __syncthreads();
+    for (int i = t; i < n; i += kSortThreads) rec[wi.start + s_cnt[s_bin[i]] + s_rank[i]] = s_rec[i];
     __syncthreads();
   }
 }
@@ -418,7 +479,7 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
     k_scatter<<<blocks, 256, 0, st>>>(pl->n_rec, pl->d_key, pl->d_rec_tmp, pl->d_bcount, pl->d_rec);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
-    k_sort_items<<<sms * 8, kItemChunk, 0, st>>>(pl->d_ioff + nb, pl->d_items, pl->d_rec);
+    k_sort_items<<<sms * 8, kSortThreads, 0, st>>>(pl->d_ioff + nb, pl->d_items, pl->d_rec);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   }
