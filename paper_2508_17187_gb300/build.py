@@ -82,7 +82,7 @@ def build(verbose: bool = False, ptxas_info: bool = False, jobs: int | None = No
         print("\n".join(o for o in outs if o))
     if cmds or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lcudart"])
+        _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lcudart", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

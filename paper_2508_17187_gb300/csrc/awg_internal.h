@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -11,6 +12,15 @@
 #include "awgrid.h"
 
 namespace awg {
+
+// NVTX range over one host call of the library (a profiler shows the call's extent on the CPU
+// timeline next to the kernels it launches; without a profiler attached the calls cost nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr double kCLight = 299792458.0;
 constexpr int kMaxSupport = 64;

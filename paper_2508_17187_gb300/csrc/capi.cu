@@ -433,6 +433,7 @@ const char* awg_last_error(void) { return g_last_error.c_str(); }
 int64_t awg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 awg_status cf_set_create(const awg_cf_params* params, void* stream, awg_cf_set* out) {
+  NvtxRange nvtx_range("awg cf_set_create (CF build)");
   if (!out) return set_error(AWG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   awg_status s = check_params(params, false);
@@ -734,6 +735,7 @@ awg_status cf_set_save(awg_cf_set h, const char* path) {
 }
 
 awg_status cf_set_load(const char* path, void* stream, awg_cf_set* out) {
+  NvtxRange nvtx_range("awg cf_set_load");
   if (!path || !out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   FILE* f = std::fopen(path, "rb");
@@ -938,6 +940,7 @@ static awg_status plan_free(PlanImpl* pl) {
 awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const double* freq_hz, int32_t n_chan,
                        const int32_t* pa_bin, const int32_t* chan_subband, const double* phase_shift, void* stream,
                        awg_plan* out) {
+  NvtxRange nvtx_range("awg plan_create");
   if (!out) return set_error(AWG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!h) return set_error(AWG_ERR_INVALID_ARG, "cf set is NULL");
@@ -1044,6 +1047,7 @@ awg_status plan_set_row_phase(awg_plan h, const double* row_dlm, const double* u
 
 awg_status plan_update(awg_plan h, const double* uvw_m, const double* freq_hz, const int32_t* pa_bin,
                        const int32_t* chan_subband, void* stream) {
+  NvtxRange nvtx_range("awg plan_update");
   if (!h) return set_error(AWG_ERR_INVALID_ARG, "plan is NULL");
   PlanImpl* pl = (PlanImpl*)h;
   if (pl->n > 0 && (!uvw_m || !freq_hz)) return set_error(AWG_ERR_INVALID_ARG, "uvw_m and freq_hz must not be NULL");
@@ -1073,6 +1077,7 @@ awg_status plan_stats(awg_plan h, int64_t* n_kept, int64_t* n_dropped, int64_t* 
 
 awg_status grid_visibilities(awg_cf_set hc, awg_plan hp, const void* vis, const float* weight, int32_t n_pol,
                              void* grid, void* grid_lo, double* sumwt, int32_t flags, void* stream) {
+  NvtxRange nvtx_range("awg grid_visibilities");
   if (!hc || !hp) return set_error(AWG_ERR_INVALID_ARG, "cf set and plan must not be NULL");
   CfSetImpl* cf = (CfSetImpl*)hc;
   PlanImpl* pl = (PlanImpl*)hp;
@@ -1089,6 +1094,7 @@ awg_status grid_visibilities(awg_cf_set hc, awg_plan hp, const void* vis, const 
 
 awg_status degrid_visibilities(awg_cf_set hc, awg_plan hp, const void* grid, void* vis_out, int32_t n_pol,
                                int32_t flags, void* stream) {
+  NvtxRange nvtx_range("awg degrid_visibilities");
   if (!hc || !hp) return set_error(AWG_ERR_INVALID_ARG, "cf set and plan must not be NULL");
   CfSetImpl* cf = (CfSetImpl*)hc;
   PlanImpl* pl = (PlanImpl*)hp;
@@ -1101,6 +1107,7 @@ awg_status degrid_visibilities(awg_cf_set hc, awg_plan hp, const void* grid, voi
 
 awg_status grid_normalize(awg_cf_set hc, void* image, int32_t n_pol, const double* sumwt, int32_t direction,
                           void* stream) {
+  NvtxRange nvtx_range("awg grid_normalize");
   if (!hc || !image) return set_error(AWG_ERR_INVALID_ARG, "cf set and image must not be NULL");
   if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
   if (direction != 0 && direction != 1) return set_error(AWG_ERR_INVALID_ARG, "direction must be 0 or 1");

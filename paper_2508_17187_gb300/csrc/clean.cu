@@ -164,6 +164,7 @@ extern "C" int64_t clean_hogbom_workspace_bytes(void) {
 extern "C" awg_status clean_hogbom(float* residual, float* model, int32_t N, const float* psf, int32_t psf_n,
                                    int32_t n_iter, float gain, float threshold, const int32_t* window, void* workspace,
                                    void* stream) {
+  NvtxRange nvtx_range("awg clean_hogbom");
   if (!residual || !model || !psf || !workspace)
     return set_error(AWG_ERR_INVALID_ARG, "residual, model, psf and workspace must not be NULL");
   if (N < 1 || psf_n < 1 || n_iter < 0) return set_error(AWG_ERR_INVALID_ARG, "N, psf_n >= 1 and n_iter >= 0 required");

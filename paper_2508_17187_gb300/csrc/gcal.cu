@@ -331,6 +331,7 @@ extern "C" awg_status gcal_solve(const void* vis, const void* model, const float
                                  int32_t n_pol, int32_t n_bl, const int32_t* ant1, const int32_t* ant2, int32_t n_ant,
                                  int32_t sol_int, int32_t sol_chan, double alpha, double delta, int32_t max_iter,
                                  int32_t ref_ant, void* gains, int32_t* iterations, void* workspace, void* stream) {
+  NvtxRange nvtx_range("awg gcal_solve");
   GcalDims d;
   awg_status s = gcal_dims(n_rows, n_chan, n_pol, n_bl, n_ant, sol_int, sol_chan, d);
   if (s != AWG_OK) return s;
