@@ -225,6 +225,7 @@ static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* v
   a.sumwt = sumwt;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
+  a.n_sep_off = (int)cf->sep_offsets.size();
   a.rank = pl->rank;
   a.mix = nullptr;
   a.pmask = (1 << P) - 1;
@@ -260,6 +261,7 @@ static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const voi
   if (pl->rank > 1) a.vstride = P;
   a.sep = (const float*)cf->d_sep;
   a.sep_off = cf->d_sep_off;
+  a.n_sep_off = (int)cf->sep_offsets.size();
   a.rank = pl->rank;
   a.mix = nullptr;
   a.pmask = (1 << P) - 1;

@@ -47,6 +47,7 @@ struct GridArgs {
   double* sumwt;         // [P]
   const float* sep;      // separable CF factors (c64), or NULL
   const int64_t* sep_off;
+  int n_sep_off;         // entries of sep_off
   int rank;              // records per sample; only term 0 (cf % rank == 0) adds its weight
   // Mueller element launches (separable kernels): factor offsets at sep_off[cf_shift + rc.cf];
   // sample s reads vis / weight at s vstride + voff and pixel i of the grid is i gstride + goff
@@ -77,6 +78,7 @@ struct DegridArgs {
   float* vis_out;        // c64 [n][P]; with rank > 1 the per-term values [n][rank][P]
   const float* sep;      // separable CF factors (c64), or NULL
   const int64_t* sep_off;
+  int n_sep_off;         // entries of sep_off
   int rank;              // records per sample (term k of sample s writes vis_out row s * rank + k)
   int64_t cf_shift;      // as in GridArgs; the output row r goes to vis_out at r vstride + voff,
   int vstride, voff, gstride, goff;

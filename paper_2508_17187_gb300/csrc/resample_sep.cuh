@@ -121,9 +121,14 @@ __device__ __forceinline__ void stage_recs(const SampleRec* rec, int start, int 
   if ((int)threadIdx.x < nst) cp_async(sl.rec() + threadIdx.x, rec + start + threadIdx.x, 16);
 }
 
-// From staged records: packed window offsets, factor-row offsets, sample index, phasor.
+// Factor offsets the rank-1 kernels keep in shared memory when the whole table fits (one entry
+// per CF and term: 127 for the W-projection set of 64 planes).
+constexpr int kSepOffCache = 256;
+
+// From staged records: packed window offsets, factor-row offsets, sample index, phasor.  `offs` is
+// the factor-offset table (a.sep_off, or its copy in shared memory).
 template <int SMAX, int TILE, int P, int ST, int RK, class Args>
-__device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, int Y0,
+__device__ __forceinline__ void derive(const Args& a, const int64_t* offs, int nst, int S, int X0, int Y0,
                                        const SepSlot<SMAX, TILE, P, ST, RK>& sl) {
   const int j = threadIdx.x;
   if (j < nst) {
@@ -131,7 +136,7 @@ __device__ __forceinline__ void derive(const Args& a, int nst, int S, int X0, in
     // RK == 1: the record's own term; RK > 1: the CF's RK terms at sep_off[cf RK + t]
 #pragma unroll
     for (int t = 0; t < RK; ++t) {
-      const long long base = a.sep_off[a.cf_shift + (RK == 1 ? rc.cf : rc.cf * RK + t)];
+      const long long base = offs[a.cf_shift + (RK == 1 ? rc.cf : rc.cf * RK + t)];
       sl.fxo()[j * RK + t] = base + (long long)rc.ox * S;
       sl.fyo()[j * RK + t] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
     }
@@ -349,10 +354,15 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
   float2* alpha = reinterpret_cast<float2*>(smem + SepLayout<SMAX, TILE, P, ST, RK>::al_off);
   __shared__ int s_item;
   __shared__ double s_wsum[NT / 32][P];
+  __shared__ int64_t s_off[RK == 1 ? kSepOffCache : 1];
   static_assert(NT % 32 == 0, "the warp reductions need whole warps");
 
   const int tid = threadIdx.x;
   const int begin = a.class_range[cls], end = a.class_range[cls + 1];
+  // a small factor-offset table is read from shared memory (visible after the item loop's first
+  // barrier), so that derive() makes no global round trip while the other warps wait
+  if (RK == 1 && a.n_sep_off <= kSepOffCache)
+    for (int i = tid; i < a.n_sep_off; i += NT) s_off[i] = a.sep_off[i];
   double wsum[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) wsum[p] = 0.0;
@@ -387,8 +397,8 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      derive(a, nst_of(0), S, X0, Y0, s0);
-      if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
+      derive(a, RK == 1 && a.n_sep_off <= kSepOffCache ? s_off : a.sep_off, nst_of(0), S, X0, Y0, s0);
+      if (nch > 1) derive(a, RK == 1 && a.n_sep_off <= kSepOffCache ? s_off : a.sep_off, nst_of(1), S, X0, Y0, s1);
       __syncthreads();
       stage_payload<SMAX, TILE, P, ST, NT, RK>(a.sep, a.vis, a.weight, nst_of(0), S, s0, a.vstride, a.voff);
       cp_async_commit();
@@ -501,7 +511,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       cp_async_wait_all();
       __syncthreads();
       // slot A is free: derive chunk c+2 into it; chunk c+1's payload has landed in B: form w V
-      if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
+      if (c + 2 < nch) derive(a, RK == 1 && a.n_sep_off <= kSepOffCache ? s_off : a.sep_off, nst_of(c + 2), S, X0, Y0, A);
       if (c + 1 < nch) form_alpha<SMAX, TILE, P, ST, NT, RK, MIX>(B, alpha, nst_of(c + 1), S, a.rank, wsum, a.mix, a.pmask);
       __syncthreads();
     }
@@ -571,9 +581,13 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
   constexpr int NBW = (NB + NW - 1) / NW;       // batches combined by one warp
   __shared__ float s_red[NB][NW][32];
   __shared__ int s_item;
+  __shared__ int64_t s_off[RK == 1 ? kSepOffCache : 1];
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int begin = a.class_range[cls], end = a.class_range[cls + 1];
+  // a small factor-offset table is read from shared memory (as in k_grid_sep)
+  if (RK == 1 && a.n_sep_off <= kSepOffCache)
+    for (int i = tid; i < a.n_sep_off; i += NT) s_off[i] = a.sep_off[i];
 
   for (;;) {
     __syncthreads();
@@ -601,18 +615,24 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
       stage_recs(a.rec, wi.start, nst_of(0), s0);
       if (nch > 1) stage_recs(a.rec, wi.start + ST, nst_of(1), s1);
       cp_async_commit();
+      // the window: asynchronous 8-byte copies of the on-grid pixels (in flight together with the
+      // records instead of one dependent load and store after another), zeros off the grid
       for (int i = tid; i < UU; i += NT) {
         const int ly = i / U, lx = i - ly * U;
         const int gy = Y0 + ly, gx = X0 + lx;
-        const bool in = gy < a.N && gx < a.N;
-        const float2* src = reinterpret_cast<const float2*>(a.grid) + ((size_t)gy * a.N + gx) * a.gstride + a.goff;
+        if (gy < a.N && gx < a.N) {
+          const float2* src = reinterpret_cast<const float2*>(a.grid) + ((size_t)gy * a.N + gx) * a.gstride + a.goff;
 #pragma unroll
-        for (int p = 0; p < P; ++p) tile[p * UU + i] = in ? __ldg(src + p) : make_float2(0.f, 0.f);
+          for (int p = 0; p < P; ++p) cp_async(tile + p * UU + i, src + p, 8);
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) tile[p * UU + i] = make_float2(0.f, 0.f);
+        }
       }
       cp_async_wait_all();
       __syncthreads();
-      derive(a, nst_of(0), S, X0, Y0, s0);
-      if (nch > 1) derive(a, nst_of(1), S, X0, Y0, s1);
+      derive(a, RK == 1 && a.n_sep_off <= kSepOffCache ? s_off : a.sep_off, nst_of(0), S, X0, Y0, s0);
+      if (nch > 1) derive(a, RK == 1 && a.n_sep_off <= kSepOffCache ? s_off : a.sep_off, nst_of(1), S, X0, Y0, s1);
       __syncthreads();
       stage_payload<SMAX, TILE, P, ST, NT, RK>(a.sep, nullptr, nullptr, nst_of(0), S, s0);
       cp_async_commit();
@@ -804,7 +824,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
           }
         }
       }
-      if (c + 2 < nch) derive(a, nst_of(c + 2), S, X0, Y0, A);
+      if (c + 2 < nch) derive(a, RK == 1 && a.n_sep_off <= kSepOffCache ? s_off : a.sep_off, nst_of(c + 2), S, X0, Y0, A);
       if (c + 1 < nch) form_beta<SMAX, TILE, P, ST, NT, RK>(Bs, beta, nst_of(c + 1), S);
       __syncthreads();
     }
