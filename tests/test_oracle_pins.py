@@ -316,6 +316,44 @@ def test_wprojection_corrects_noncoplanar_baselines(oracle_built):
     assert out[True] < out[False] / 5
 
 
+def test_chi2_gradient_matches_central_differences(oracle_built):
+    """Eq. ImChisq and Eq. ResIm: the gradient of chi^2(I) = sum w |V - D F T^-1 I|^2 over the real
+    image I is -2 Re[T^-1 F^H G W (V - D F T^-1 I)], with G = D^H (unit weights) and F^H the
+    unnormalised inverse transform.  chi^2 is quadratic in I, so a central difference with any step
+    carries rounding only (FP64).  A missing N^2 in F^H, one taper division instead of two, or a
+    flipped sign fails it."""
+    wl = synth.make_workload("autograd", n_int=3, n_chan=2, grid_n=128, n_src=5, n_wplanes=4, max_support=16)
+    N = wl.grid_n
+    p = cf.CFParams(grid_n=N, cell_rad=wl.cell_rad, oversampling=wl.oversampling, ps_support=wl.ps_support,
+                    use_w=True, n_wplanes=wl.n_wplanes, w_max_lambda=wl.w_max_lambda, max_support=wl.max_support)
+    idx = index.sample_index(p, wl.uvw_m, wl.freq_hz)
+    assert idx.valid.all()
+    buf, off, _ = cf.flatten_cf_set(p, cf.cf_set(p, which=set(np.unique(idx.cf).tolist())))
+    V = wl.vis.reshape(-1, 1).astype(np.complex128)
+    w = wl.weight.reshape(-1, 1).astype(np.float64)
+    inner = np.zeros((N, N, 1))
+    inner[N // 4:3 * N // 4, N // 4:3 * N // 4] = 1.0
+    rng = np.random.default_rng(synth.SEED_FD)
+    I0 = rng.standard_normal((N, N, 1)) * inner
+
+    def model_vis(I):
+        return ops.degrid(idx, buf, off, p.oversampling, image.model_to_grid(I, p.ps_support))
+
+    def chi2(I):
+        r = V - model_vis(I)
+        return float((w * (r.real ** 2 + r.imag ** 2)).sum())
+
+    g, _ = ops.grid(idx, buf, off, p.oversampling, N, w * (V - model_vis(I0)), np.ones_like(w))
+    t = image.taper_image(N, p.ps_support)
+    grad = -2.0 * (image.grid_to_image(g) / (t[:, None] * t[None, :])[:, :, None]).real
+    for _ in range(3):
+        d = rng.standard_normal(I0.shape) * inner
+        eps = float(np.linalg.norm(I0) / np.linalg.norm(d))
+        fd = (chi2(I0 + eps * d) - chi2(I0 - eps * d)) / (2.0 * eps)
+        an = float((grad * d).sum())
+        assert abs(fd - an) <= 1e-8 * abs(an), (fd, an)
+
+
 def test_degrid_model_matches_analytic_visibilities(oracle_built):
     """D of F(model / T T) for point sources at pixel centres ~ their analytic visibilities."""
     wl = synth.make_workload("standard", n_int=10, with_vis=False)
