@@ -842,9 +842,9 @@ def main():
     from paper_2508_17187_gb300 import _lib
 
     world, rank, local = dist_env()
+    torch.cuda.set_device(local)   # before the process group, so NCCL binds this rank's GPU
     if world > 1:
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     n_int = args.n_int or synth.CONFIGS[CONFIG]["n_int"]
     wl = rank_workload(world, rank, n_int, dev)
