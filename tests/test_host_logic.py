@@ -66,3 +66,16 @@ def test_cf_params_marshalling():
     assert [p.pa_bin_centers_rad[i] for i in range(2)] == [0.1, -0.2]
     assert p.subband_freq_hz[0] == 3e9
     assert len(keep) >= 2   # the arrays the struct points into stay alive with it
+
+
+def test_bench_rank_slices_tile_the_track():
+    """Weak scaling in bench.py: rank r of N takes integrations [r n, (r + 1) n) of a track N n
+    long, so the ranks' rows together are the whole track, each row once, with its own PA bins."""
+    import bench
+    world, n_int = 3, 4
+    full = bench.synth.make_workload("wproj", with_vis=False, n_int=world * n_int)
+    parts = [bench.rank_workload(world, r, n_int, "cpu", with_vis=False) for r in range(world)]
+    assert all(p.n_int == n_int and p.n_rows == n_int * full.n_bl for p in parts)
+    assert np.array_equal(np.concatenate([p.uvw_m for p in parts]), full.uvw_m)
+    assert np.array_equal(np.concatenate([p.pa_bin for p in parts]), full.pa_bin)
+    assert all(p.grid_n == full.grid_n and p.cell_rad == full.cell_rad for p in parts)
