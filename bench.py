@@ -258,7 +258,7 @@ def run_cpu_baseline(wl, every: int, single_thread: bool = False):
     wt = np.asarray(wl.weight)[rows].reshape(-1, wl.n_pol)
     threads = oops.default_threads()
     t0 = time.perf_counter()
-    g, _ = oops.grid(idx, buf, off, wl.oversampling, wl.grid_n, vis, wt, nthreads=threads)
+    g, sw = oops.grid(idx, buf, off, wl.oversampling, wl.grid_n, vis, wt, nthreads=threads)
     t1 = time.perf_counter()
     d = oops.degrid(idx, buf, off, wl.oversampling, g, nthreads=threads)
     t2 = time.perf_counter()
@@ -267,7 +267,8 @@ def run_cpu_baseline(wl, every: int, single_thread: bool = False):
            "cpu_model": cpu_model(),
            "sample": f"every {every}th integration: {len(rows)} rows x {wl.n_chan} channels x {wl.n_pol} pols "
                      f"= {n_vis} visibilities, gridded then degridded (grid {t1 - t0:.2f} s, degrid {t2 - t1:.2f} s)",
-           "seconds": t2 - t0, "rows": rows, "grid": g, "degrid": d}
+           "seconds": t2 - t0, "rows": rows, "grid": g, "sumwt": sw, "degrid": d,
+           "support": idx.support[idx.valid]}
     if single_thread and len(rows) >= 10 * wl.n_bl:
         # one thread on the first tenth of the sample's integrations
         sub = rows[:len(rows) // 10 // wl.n_bl * wl.n_bl]
@@ -306,11 +307,14 @@ def cpu_model() -> str:
 def sample_accuracy(cf, wl, vis, wt, cb, dev) -> dict:
     """The library against the oracle on the baseline's sample: the gridded plane and the
     degridding of the oracle's own FP64 plane (relative RMS over their full extent), and the
-    dirty image Re(F^H grid) / (sum w T T) over the inner half of the field (where T >= 0.25; the
-    error measure of the 1e-5 accuracy target)."""
+    dirty image over the inner half of the field (where T >= 0.25; the error measure of the 1e-5
+    accuracy target).  The library's image is its whole path: gridding, the inverse FFT on the
+    GPU and grid_normalize with the library's sum of weights; the oracle's is
+    oracle.image.dirty_image of its FP64 grid with its own sum of weights and taper."""
     import torch
 
     import paper_2508_17187_gb300 as awg
+    from oracle import image as oimage
     rows = torch.as_tensor(cb["rows"], device=dev)
     N, P = wl.grid_n, wl.n_pol
     plan = awg.plan_create(cf, torch.as_tensor(wl.uvw_m, device=dev)[rows], torch.as_tensor(wl.freq_hz, device=dev))
@@ -325,19 +329,18 @@ def sample_accuracy(cf, wl, vis, wt, cb, dev) -> dict:
     def rel(a, b):
         return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
-    # 1 / (T T) per pixel from the library's own taper division, then both images in FP64
-    inv_tt = torch.ones((N, N, 1), dtype=torch.complex64, device=dev)
-    awg.grid_normalize(cf, inv_tt, None, direction=1)
-    inv_tt = inv_tt.real.double()
-
-    def image(grid):
-        x = torch.fft.ifftshift(grid.to(torch.complex128), dim=(0, 1))
-        return torch.fft.fftshift(torch.fft.ifft2(x, dim=(0, 1), norm="forward"), dim=(0, 1)).real * inv_tt
-
+    x = torch.fft.ifftshift(g, dim=(0, 1))
+    img = torch.fft.fftshift(torch.fft.ifft2(x, dim=(0, 1), norm="forward"), dim=(0, 1)).contiguous()
+    awg.grid_normalize(cf, img, sw, direction=0)
     q = slice(N // 4, 3 * N // 4)
+    img_lib = img.real[q, q].double().cpu().numpy()
+    img_o = oimage.dirty_image(cb["grid"], cb["sumwt"], wl.ps_support)[q, q]
+    img_err = float(np.linalg.norm(img_lib - img_o) / np.linalg.norm(img_o))
     err = {"grid_rel_rms": rel(g.to(torch.complex128), g_o), "degrid_rel_rms": rel(out.to(torch.complex128), d_o),
-           "image_rel_rms_inner_half": rel(image(g)[q, q], image(g_o)[q, q]),
-           "sample": "the cpu_baseline sample, FP64 oracle vs the library"}
+           "image_rel_rms_inner_half": img_err,
+           "sumwt_rel": float(np.max(np.abs(sw.cpu().numpy() - cb["sumwt"]) / np.abs(cb["sumwt"]))),
+           "sample": "the cpu_baseline sample, FP64 oracle vs the library (image: library gridding + GPU FFT + "
+                     "grid_normalize vs oracle dirty_image with the oracle's taper and sum of weights)"}
     plan.close()
     return err
 
@@ -383,7 +386,20 @@ def plain_fp64_on_sample(wl, vis, wt, cb, dev) -> dict:
     d_err = float(torch.linalg.vector_norm(out.to(torch.complex128) - d_o) / torch.linalg.vector_norm(d_o))
     n_vis = R * C * P
     cf.close()
+    # its ceiling: the FP64 FMA rate of this GPU (8 FLOP per tap and pol, as for the FP32 path)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    o64 = torch.empty(sms * 8 * 256, dtype=torch.float64, device=dev)
+    fl = ctypes.c_double()
+    for _ in range(2):   # warm-up, then the timed launch
+        e[0].record()
+        assert lib.awg_fp64_fma_probe(vp(o64), sms * 8, 1 << 12, st, ctypes.byref(fl)) == 0
+        e[1].record()
+    torch.cuda.synchronize()
+    fp64_peak = fl.value / (e[0].elapsed_time(e[1]) / 1e3) / 1e12
+    taps = float(np.sum(cb["support"].astype(np.float64) ** 2))
+    fp64_tflops = 2 * 8.0 * P * taps / (ms / 1e3) / 1e12
     return {"value": 2 * n_vis / (ms / 1e3), "unit": "visibilities/s", "grid_rel_rms": g_err, "degrid_rel_rms": d_err,
+            "tflops": fp64_tflops, "fp64_fma_peak_tflops": fp64_peak, "frac_of_fp64_peak": fp64_tflops / fp64_peak,
             "sample": "the cpu_baseline sample: one FP64 launch per channel over full CF tables (CUDA events)"}
 
 
@@ -1125,7 +1141,7 @@ def main():
         cb = run_cpu_baseline(host_wl, args.cpu_sample_every or 40, single_thread=True)
         line["accuracy"] = sample_accuracy(cf, wl, vis, wt, cb, dev)
         line["plain_fp64_gpu"] = plain_fp64_on_sample(wl, vis, wt, cb, dev)
-        for k in ("seconds", "rows", "grid", "degrid"):
+        for k in ("seconds", "rows", "grid", "sumwt", "degrid", "support"):
             cb.pop(k)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)

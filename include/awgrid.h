@@ -207,6 +207,15 @@ awg_status cf_set_get_supports(awg_cf_set cf, int32_t* supports_out);
  * is expanded as the sum of its FP32 products fy_k fx_k). Blocking. */
 awg_status cf_set_copy_table(awg_cf_set cf, int32_t cf_index, float* table_out);
 
+/* Host copy of the stored factors of one term of a separable CF: CF_ci = scale * sum over the terms
+ * k of fy_k[oy][ty] fx_k[ox][tx].  fx_out, fy_out: host c64 [OS+1][S] (term `term` < the set's
+ * rank; zero rows for the padding terms of CFs fitted with fewer); scale_out: host float [2] or
+ * NULL, the element scalar s_pq (re, im) of a Mueller element stored as a base CF, else (1, 0).
+ * The FP32 values are the ones the kernels read.  Blocking.  Errors: INVALID_ARG (NULL, full-table
+ * set, index or term out of range), CUDA. */
+awg_status cf_set_copy_factors(awg_cf_set cf, int32_t cf_index, int32_t term, float* fx_out, float* fy_out,
+                               float* scale_out);
+
 /*
  * Create a plan: per-visibility index and the tiled ordering of all R*C samples
  * (PreSolvePrep re-ordering, Sec. 5.2 and Sec. 6.1).  For every (row r, channel c), in FP64 with
@@ -257,6 +266,18 @@ awg_status plan_destroy(awg_plan plan);
 awg_status plan_stats(awg_plan plan, int64_t* n_kept, int64_t* n_dropped, int64_t* sum_taps);
 
 /*
+ * Host copy of the plan's per-sample index (the CF_ij(nu, w, t) selection of Eq. CIJ and the pixel
+ * and offset rules of plan_create), in sample order s = row * n_chan + chan, for inspection and
+ * tests: kept[s] = number of records of sample s in the plan (1 when kept, 0 when dropped), and for
+ * kept samples cf_out[s] (the CF index), p0x[s], p0y[s] (first tap pixel) and ox[s], oy[s]
+ * (oversampling offsets in [0, OS]); -1 for dropped ones.  All outputs: host int32 [n_rows * n_chan].
+ * Synchronises the plan's last stream and copies the records back (blocking).
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+awg_status plan_copy_index(awg_plan plan, int32_t* kept, int32_t* cf_out, int32_t* p0x, int32_t* p0y, int32_t* ox,
+                           int32_t* oy);
+
+/*
  * Gridding G (Eq. IMAGE-MOD): for every kept sample s and pol p,
  *   grid[p0y+ty][p0x+tx][p] += conj(CF_cf[oy][ox][ty][tx]) * weight[s][p] * vis[s][p] (* phasor),
  * accumulated (+=) into the caller's grid; sumwt[p] += sum of weight[s][p] over kept samples (FP64).
@@ -305,7 +326,10 @@ awg_status grid_normalize(awg_cf_set cf, void* image, int32_t n_pol, const doubl
  * Arguments: as plan_create (uvw_m, freq_hz, pa_bin, chan_subband: device) and grid_visibilities
  * (vis, weight, grid, sumwt: device, accumulated).
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture on the device.
+ * that device current); make that first call before any stream capture on the device.  The address
+ * is kept per device and CUDA context: after a cudaDeviceReset the next call looks it up again in
+ * the new context (where the array starts over with unspecified contents).  The call leaves the
+ * caller's current device as it found it.
  * Every call on a device shares the one array and it keeps what the last call left there; each
  * call clears what it accumulates into before use, so sequential calls are independent, but calls
  * whose work overlaps on the GPU (different streams, not ordered by events) race and corrupt each
@@ -346,6 +370,11 @@ awg_status degrid_visibilities_plain_fp64(awg_cf_set cf, const double* uvw_m, in
  * Errors: INVALID_ARG, CUDA.
  */
 awg_status awg_fp32_fma_probe(float* out, int32_t n_blocks, int64_t iters, void* stream, double* flop);
+
+/* The same probe in FP64 (out: device, n_blocks * 256 doubles): the FP64 FMA rate that bounds the
+ * plain FP64 baseline (grid_visibilities_plain_fp64 / degrid_visibilities_plain_fp64).
+ * Asynchronous.  Errors: INVALID_ARG, CUDA. */
+awg_status awg_fp64_fma_probe(double* out, int32_t n_blocks, int64_t iters, void* stream, double* flop);
 
 /*
  * Hogbom CLEAN minor cycle (the deconvolution step of the major cycle, Sec. 5.2; Eq. ModelUpdate

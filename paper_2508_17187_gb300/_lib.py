@@ -17,10 +17,10 @@ AWG_GRID_KAHAN, AWG_GRID_FP64 = 1, 2
 
 EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_fused_terms", "cf_set_get_params", "cf_set_save", "cf_set_load",
             "cf_set_get_supports",
-            "cf_set_copy_table", "plan_create", "plan_update", "plan_destroy", "plan_stats", "grid_visibilities",
+            "cf_set_copy_table", "cf_set_copy_factors", "plan_create", "plan_update", "plan_destroy", "plan_stats", "plan_copy_index", "grid_visibilities",
             "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
             "grid_visibilities_noalloc", "grid_visibilities_plain_fp64", "degrid_visibilities_plain_fp64",
-            "awg_fp32_fma_probe", "cf_set_autotune", "cf_set_choose", "clean_hogbom_workspace_bytes",
+            "awg_fp32_fma_probe", "awg_fp64_fma_probe", "cf_set_autotune", "cf_set_choose", "clean_hogbom_workspace_bytes",
             "clean_hogbom", "clean_hogbom_components", "plan_set_row_phase", "gcal_workspace_bytes", "gcal_solve",
             "cf_set_mueller", "awg_debug_fail_allocations", "awg_debug_live_allocations"]
 
@@ -86,10 +86,12 @@ def load():
             "cf_set_load": ([ctypes.c_char_p, vp, ctypes.POINTER(vp)], st),
             "cf_set_get_supports": ([vp, vp], st),
             "cf_set_copy_table": ([vp, i32, vp], st),
+            "cf_set_copy_factors": ([vp, i32, i32, vp, vp, vp], st),
             "plan_create": ([vp, vp, i64, vp, i32, vp, vp, vp, vp, ctypes.POINTER(vp)], st),
             "plan_update": ([vp, vp, vp, vp, vp, vp], st),
             "plan_destroy": ([vp], st),
             "plan_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
+            "plan_copy_index": ([vp, vp, vp, vp, vp, vp, vp], st),
             "grid_visibilities": ([vp, vp, vp, vp, i32, vp, vp, vp, i32, vp], st),
             "degrid_visibilities": ([vp, vp, vp, vp, i32, i32, vp], st),
             "grid_normalize": ([vp, vp, i32, vp, i32, vp], st),
@@ -99,6 +101,7 @@ def load():
             "grid_visibilities_plain_fp64": ([vp, vp, i64, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp, vp], st),
             "degrid_visibilities_plain_fp64": ([vp, vp, i64, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp], st),
             "awg_fp32_fma_probe": ([vp, i32, i64, vp, ctypes.POINTER(ctypes.c_double)], st),
+            "awg_fp64_fma_probe": ([vp, i32, i64, vp, ctypes.POINTER(ctypes.c_double)], st),
             "cf_set_autotune": ([vp, vp, i64, vp, i32, vp, vp, i32, vp, vp, vp], st),
             "cf_set_choose": ([vp, i32, i32], st),
             "clean_hogbom_workspace_bytes": ([], ctypes.c_int64),

@@ -127,6 +127,20 @@ class CFSet:
               "cf_set_copy_table")
         return out[..., 0] + 1j * out[..., 1]
 
+    def copy_factors(self, cf_index: int):
+        """Stored factors of a separable CF (cf_set_copy_factors): (fx, fy, scale) with fx, fy
+        complex64 [rank, OS+1, S] and the element scalar; CF = scale * sum_k fy[k] (x) fx[k]."""
+        S = int(self.supports()[cf_index])
+        OS = self.oversampling
+        fx = np.zeros((self.rank, OS + 1, S, 2), dtype=np.float32)
+        fy = np.zeros_like(fx)
+        sc = np.zeros(2, dtype=np.float32)
+        for k in range(self.rank):
+            check(_lib.load().cf_set_copy_factors(self.handle, int(cf_index), k, fx[k].ctypes.data_as(ctypes.c_void_p),
+                                                  fy[k].ctypes.data_as(ctypes.c_void_p),
+                                                  sc.ctypes.data_as(ctypes.c_void_p)), "cf_set_copy_factors")
+        return fx[..., 0] + 1j * fx[..., 1], fy[..., 0] + 1j * fy[..., 1], complex(sc[0], sc[1])
+
     def close(self):
         if self._h is not None:
             check(_lib.load().cf_set_destroy(self._h), "cf_set_destroy")
@@ -266,6 +280,16 @@ class Plan:
         k, d, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         check(_lib.load().plan_stats(self.handle, ctypes.byref(k), ctypes.byref(d), ctypes.byref(t)), "plan_stats")
         return int(k.value), int(d.value), int(t.value)
+
+    def index(self) -> dict:
+        """Host copy of the per-sample index in sample order (plan_copy_index): int32 arrays
+        [R * C] 'kept' (records of the sample), 'cf', 'p0x', 'p0y', 'ox', 'oy' (-1 when dropped);
+        synchronises."""
+        n = self.n_rows * self.n_chan
+        out = {k: np.empty(max(n, 1), dtype=np.int32) for k in ("kept", "cf", "p0x", "p0y", "ox", "oy")}
+        ptrs = [out[k].ctypes.data_as(ctypes.c_void_p) for k in ("kept", "cf", "p0x", "p0y", "ox", "oy")]
+        check(_lib.load().plan_copy_index(self.handle, *ptrs), "plan_copy_index")
+        return {k: v[:n] for k, v in out.items()}
 
     def close(self):
         if self._h is not None:

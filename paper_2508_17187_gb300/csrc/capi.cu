@@ -912,6 +912,32 @@ awg_status cf_set_copy_table(awg_cf_set h, int32_t ci, float* out) {
   return AWG_OK;
 }
 
+awg_status cf_set_copy_factors(awg_cf_set h, int32_t ci, int32_t term, float* fx_out, float* fy_out,
+                               float* scale_out) {
+  if (!h || !fx_out || !fy_out) return set_error(AWG_ERR_INVALID_ARG, "NULL argument");
+  CfSetImpl* cf = (CfSetImpl*)h;
+  if (!cf->separable) return set_error(AWG_ERR_INVALID_ARG, "the CF set holds full tables, not factors");
+  if (term < 0 || term >= cf->rank) return set_error(AWG_ERR_INVALID_ARG, "term out of range");
+  float scale_r = 1.f, scale_i = 0.f;
+  if (cf->n_mb > 1 && !cf->mb_elements) {   // a Mueller element is s_pq times its stored base CF
+    if (ci < 0 || ci >= cf->n_elem * cf->n_base) return set_error(AWG_ERR_INVALID_ARG, "cf index out of range");
+    const int e = ci / cf->n_base;
+    scale_r = (float)cf->elem_s[e][0];
+    scale_i = (float)cf->elem_s[e][1];
+    ci = cf->elem_mb[e] * cf->n_base + ci % cf->n_base;
+  }
+  if (ci < 0 || ci >= cf->n_cf) return set_error(AWG_ERR_INVALID_ARG, "cf index out of range");
+  const int64_t q = (int64_t)(cf->p.oversampling + 1) * cf->supports[ci];
+  const float* src = (const float*)cf->d_sep + 2 * cf->sep_offsets[(size_t)ci * cf->rank + term];
+  AWG_CUDA_TRY(cudaMemcpy(fx_out, src, 8 * q, cudaMemcpyDeviceToHost));
+  AWG_CUDA_TRY(cudaMemcpy(fy_out, src + 2 * q, 8 * q, cudaMemcpyDeviceToHost));
+  if (scale_out) {
+    scale_out[0] = scale_r;
+    scale_out[1] = scale_i;
+  }
+  return AWG_OK;
+}
+
 static awg_status plan_free(PlanImpl* pl) {
   if (!pl) return AWG_OK;
   dev_free(pl->d_rec);
@@ -1072,6 +1098,43 @@ awg_status plan_stats(awg_plan h, int64_t* n_kept, int64_t* n_dropped, int64_t* 
   if (n_kept) *n_kept = (int64_t)c[0];
   if (n_dropped) *n_dropped = (int64_t)c[1];
   if (sum_taps) *sum_taps = (int64_t)c[2];
+  return AWG_OK;
+}
+
+awg_status plan_copy_index(awg_plan h, int32_t* kept, int32_t* cf_out, int32_t* p0x, int32_t* p0y, int32_t* ox,
+                           int32_t* oy) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "plan is NULL");
+  PlanImpl* pl = (PlanImpl*)h;
+  if (pl->n > 0 && (!kept || !cf_out || !p0x || !p0y || !ox || !oy))
+    return set_error(AWG_ERR_INVALID_ARG, "output arrays must not be NULL");
+  if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
+  AWG_CUDA_TRY(cudaStreamSynchronize(pl->last_stream));
+  unsigned long long c[4];
+  AWG_CUDA_TRY(cudaMemcpy(c, pl->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+  const int64_t n_kept_rec = (int64_t)c[0] * pl->rank;
+  std::vector<SampleRec> rec;
+  try {
+    rec.resize((size_t)n_kept_rec);
+  } catch (const std::bad_alloc&) {
+    return set_error(AWG_ERR_OOM, "host allocation failed");
+  }
+  if (n_kept_rec > 0)
+    AWG_CUDA_TRY(cudaMemcpy(rec.data(), pl->d_rec, sizeof(SampleRec) * (size_t)n_kept_rec, cudaMemcpyDeviceToHost));
+  for (int64_t s = 0; s < pl->n; ++s) {
+    kept[s] = 0;
+    cf_out[s] = p0x[s] = p0y[s] = ox[s] = oy[s] = -1;
+  }
+  for (const SampleRec& r : rec) {
+    if (r.src < 0 || r.src >= pl->n) return set_error(AWG_ERR_CUDA, "plan record outside the sample range");
+    if (pl->rank > 1 && r.cf % pl->rank != 0) continue;   // term k > 0 of a sample: same index
+    const int64_t s = r.src;
+    kept[s] += 1;
+    cf_out[s] = r.cf / pl->rank;
+    p0x[s] = r.p0x;
+    p0y[s] = r.p0y;
+    ox[s] = r.ox;
+    oy[s] = r.oy;
+  }
   return AWG_OK;
 }
 

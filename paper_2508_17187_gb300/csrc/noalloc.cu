@@ -38,23 +38,72 @@ constexpr size_t kScratchBytes = 2 * kRecBytes + 2 * kKeyBytes + 4 * kBucketByte
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchCache {
+  unsigned long long ctx_id;   // the CUDA context the address belongs to (0: not known)
+  void* addr;
+};
+ScratchCache g_scratch[kMaxDevices] = {};
+
+// Identifier of the calling thread's current CUDA context, unique for the life of the process (a
+// context created after cudaDeviceReset gets a new one), through the driver entry points the
+// runtime exposes; 0 when the driver does not offer them.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrent)(void**);
+  typedef int (*GetId)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+  }
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 // Device address of the scratch array on `device` (which must be current).  In host code the
-// array's name stands for a host-side shadow, not device memory, so the address is looked up
-// once per device with cudaGetSymbolAddress.
+// array's name stands for a host-side shadow, not device memory, so the address is looked up with
+// cudaGetSymbolAddress once per device and context, and again after the context changed (a
+// cudaDeviceReset reloads the library's module, possibly elsewhere).
 awg_status scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return set_error(AWG_ERR_UNSUPPORTED, "device ordinal too large");
+  // cudaSetDevice (by the caller) made the device's primary context current to this thread
+  const unsigned long long ctx = current_context_id();
+  cudaError_t e = cudaSuccess;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[device]) {
+  ScratchCache& c = g_scratch[device];
+  if (!c.addr || (ctx != 0 && c.ctx_id != ctx)) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_scratch_addr[device] = p;
+    c.addr = p;
+    c.ctx_id = ctx;
   }
-  *out = (unsigned char*)g_scratch_addr[device];
+  *out = (unsigned char*)c.addr;
   return AWG_OK;
 }
+
+// Restores the caller's current device when the entry point returns.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace
 }  // namespace awg
@@ -69,13 +118,16 @@ extern "C" awg_status grid_visibilities_noalloc(awg_cf_set hc, const double* uvw
   CfSetImpl* cf = (CfSetImpl*)hc;
   if (n_rows < 0 || n_chan < 1) return set_error(AWG_ERR_INVALID_ARG, "n_rows must be >= 0 and n_chan >= 1");
   if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
-  const int64_t n = n_rows * (int64_t)n_chan;
   const int rank = cf->separable && !cf->fused ? cf->rank : 1;   // records per sample
-  if (n * rank > kNoAllocMaxSamples)
+  // compare before multiplying, so that no product can overflow
+  if (n_rows > kNoAllocMaxSamples / n_chan / rank)
     return set_error(AWG_ERR_INVALID_ARG, "grid_visibilities_noalloc takes at most " +
                                               std::to_string(kNoAllocMaxSamples) +
                                               " samples (rows x channels, times the CF terms) per call, got " +
-                                              std::to_string(n * rank) + "; use plan_create + grid_visibilities");
+                                              std::to_string(n_rows) + " rows x " + std::to_string(n_chan) +
+                                              " channels x " + std::to_string(rank) +
+                                              " terms; use plan_create + grid_visibilities");
+  const int64_t n = n_rows * (int64_t)n_chan;
   const int nb = cf->slots.base[cf->slots.n];
   if (nb > kNoAllocMaxBuckets)
     return set_error(AWG_ERR_INVALID_ARG, "grid_visibilities_noalloc supports at most " +
@@ -87,6 +139,7 @@ extern "C" awg_status grid_visibilities_noalloc(awg_cf_set hc, const double* uvw
   if (cf->p.n_subbands > 1 && !chan_subband)
     return set_error(AWG_ERR_INVALID_ARG, "chan_subband is required with n_subbands > 1");
   if (!grid || !sumwt) return set_error(AWG_ERR_INVALID_ARG, "grid and sumwt must not be NULL");
+  DeviceGuard restore_device;
   if (cudaSetDevice(cf->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
   unsigned char* base = nullptr;
   awg_status s = scratch_address(cf->device, &base);

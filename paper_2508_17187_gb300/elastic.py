@@ -25,6 +25,25 @@ def owned(n_parts: int, rank: int, world: int) -> List[int]:
     return list(range(rank, n_parts, world))
 
 
+_calls = [0]   # reduce_with_recovery calls made by this process (every rank makes them in the same order)
+
+
+def _agree(store, key: str, rank: int, world: int, mine: str, wait_s: float) -> dict:
+    """Publish this rank's outcome under key/<rank>, then collect every rank's outcome, waiting at
+    most wait_s for the missing ones; a rank that never publishes (it died) is absent."""
+    rank_key = f"{key}/{{}}"
+    store.set(rank_key.format(rank), mine)
+    deadline = time.monotonic() + wait_s
+    seen = {}
+    while True:
+        for r in range(world):
+            if r not in seen and store.check([rank_key.format(r)]):
+                seen[r] = store.get(rank_key.format(r)).decode()
+        if len(seen) == world or time.monotonic() >= deadline:
+            return seen
+        time.sleep(0.05)
+
+
 def reduce_with_recovery(compute: Callable[[Sequence[int]], List[torch.Tensor]], n_parts: int, rank: int, world: int,
                          store, backend: str = "gloo", timeout_s: float = 10.0,
                          grace_s: float = 2.0) -> Tuple[List[torch.Tensor], List[int]]:
@@ -32,23 +51,32 @@ def reduce_with_recovery(compute: Callable[[Sequence[int]], List[torch.Tensor]],
     given partitions, the same shapes for any list, zeros for an empty one), across the ranks of the
     default process group, which must have been initialised with `store`.  Returns (the sums, the
     ranks that failed).  After a failure the default process group is the survivors' group (ranks
-    renumbered in order)."""
+    renumbered in order).
+
+    The ranks agree on the outcome through the store before returning: every rank publishes whether
+    all of its all-reduces completed, and the sums are returned only when every rank of the world
+    published success.  Otherwise - a collective failed on some rank, or a rank never published
+    (it died, possibly between two all-reduces, after some ranks had completed the first) - every
+    survivor discards what the all-reduces left and sums again from its own partial sums."""
+    call = _calls[0]
+    _calls[0] += 1
     partial = compute(owned(n_parts, rank, world))
     keep = [t.clone() for t in partial]   # an interrupted all-reduce may leave a tensor half summed
+    ok = True
     try:
         for t in partial:
             dist.all_reduce(t)
-        return partial, []
     except RuntimeError:
-        pass
-    # recovery: who is left?
-    store.set(f"elastic/alive/{rank}", "1")
-    time.sleep(grace_s)
-    survivors = [r for r in range(world) if store.check([f"elastic/alive/{r}"])]
+        ok = False
+    outcomes = _agree(store, f"elastic/{call}/outcome", rank, world, "ok" if ok else "fail", timeout_s + grace_s)
+    if len(outcomes) == world and all(v == "ok" for v in outcomes.values()):
+        return partial, []
+    # recovery: the survivors are the ranks that published an outcome
+    survivors = sorted(outcomes)
     failed = [r for r in range(world) if r not in survivors]
     new_rank, new_world = survivors.index(rank), len(survivors)
     dist.destroy_process_group()
-    dist.init_process_group(backend, store=dist.PrefixStore("elastic/recovery", store), rank=new_rank,
+    dist.init_process_group(backend, store=dist.PrefixStore(f"elastic/{call}/recovery", store), rank=new_rank,
                             world_size=new_world, timeout=datetime.timedelta(seconds=timeout_s))
     lost = [p for r in failed for p in owned(n_parts, r, world)]
     extra = compute(lost[new_rank::new_world])

@@ -92,9 +92,11 @@ def _patched_rank(rank, world, port, n_int, out):
     _rank_main(rank, world, port, n_int, out)
 
 
-def _failover_rank(rank, world, port, n_parts, fail_rank, out_path):
+def _failover_rank(rank, world, port, n_parts, fail_rank, out_path, when="before"):
     """One rank of the failover test: the partitions' partial sums are small integer tensors (each
-    partition p contributes p + 1 in slot p), so the recovered total is checked exactly."""
+    partition p contributes p + 1 in slot p), so the recovered total is checked exactly.  The
+    failing rank leaves before the first all-reduce (when="before") or after taking part in the
+    first of the two (when="between")."""
     import datetime
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -109,22 +111,28 @@ def _failover_rank(rank, world, port, n_parts, fail_rank, out_path):
         return [t, torch.tensor([float(len(parts))], dtype=torch.float64)]
 
     if rank == fail_rank:
-        raise SystemExit(3)   # the failure: this rank leaves before the collective
+        if when == "between":   # its first all-reduce completes everywhere, then it is gone
+            dist.all_reduce(compute(elastic.owned(n_parts, rank, world))[0])
+        raise SystemExit(3)   # the failure: this rank leaves
     sums, failed = elastic.reduce_with_recovery(compute, n_parts, rank, world, store, timeout_s=10.0, grace_s=2.0)
     np.save(f"{out_path}.{rank}.npy", np.concatenate([sums[0].numpy(), sums[1].numpy(), np.array(failed, float)]))
     dist.barrier()
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,fail_rank", [(2, 1), (3, 2), (3, 1)])
-def test_rank_failure_is_detected_and_its_partitions_regridded(tmp_path, world, fail_rank):
-    """A rank that leaves before the all-reduce: the others' collective fails, the survivors form a
-    new group, split the failed rank's partitions between them and still sum every partition once."""
+@pytest.mark.parametrize("world,fail_rank,when", [(2, 1, "before"), (3, 2, "before"), (3, 1, "before"),
+                                                  (3, 1, "between"), (3, 2, "between")])
+def test_rank_failure_is_detected_and_its_partitions_regridded(tmp_path, world, fail_rank, when):
+    """A rank that leaves before the all-reduces, or between the first and the second: the others'
+    collective fails, the survivors agree on it through the store, form a new group, split the
+    failed rank's partitions between them and still sum every partition exactly once (the first
+    tensor, already summed with the failed rank's share, is summed again from the kept partials)."""
     n_parts = 7
     port = _free_port()
     out = str(tmp_path / "sums")
     ctx = mp.get_context("spawn")
-    procs = [ctx.Process(target=_failover_rank, args=(r, world, port, n_parts, fail_rank, out)) for r in range(world)]
+    procs = [ctx.Process(target=_failover_rank, args=(r, world, port, n_parts, fail_rank, out, when))
+             for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
