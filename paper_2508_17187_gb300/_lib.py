@@ -17,12 +17,12 @@ AWG_GRID_KAHAN, AWG_GRID_FP64 = 1, 2
 
 EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_fused_terms", "cf_set_get_params", "cf_set_save", "cf_set_load",
             "cf_set_get_supports",
-            "cf_set_copy_table", "cf_set_copy_factors", "plan_create", "plan_update", "plan_destroy", "plan_stats", "plan_copy_index", "grid_visibilities",
+            "cf_set_copy_table", "cf_set_copy_factors", "plan_create", "plan_update", "plan_destroy", "plan_stats", "plan_check", "plan_copy_index", "grid_visibilities",
             "degrid_visibilities", "grid_normalize", "awg_last_error", "awg_kernel_launches",
             "grid_visibilities_noalloc", "grid_visibilities_plain_fp64", "degrid_visibilities_plain_fp64",
             "awg_fp32_fma_probe", "awg_fp64_fma_probe", "cf_set_autotune", "cf_set_choose", "clean_hogbom_workspace_bytes",
             "clean_hogbom", "clean_hogbom_components", "plan_set_row_phase", "gcal_workspace_bytes", "gcal_solve",
-            "cf_set_mueller", "awg_debug_fail_allocations", "awg_debug_live_allocations"]
+            "cf_set_mueller", "awg_debug_fail_allocations", "awg_debug_live_allocations", "awg_debug_ws_withhold"]
 
 
 class AwgError(RuntimeError):
@@ -92,6 +92,7 @@ def load():
             "plan_destroy": ([vp], st),
             "plan_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
             "plan_copy_index": ([vp, vp, vp, vp, vp, vp, vp], st),
+            "plan_check": ([vp], st),
             "grid_visibilities": ([vp, vp, vp, vp, i32, vp, vp, vp, i32, vp], st),
             "degrid_visibilities": ([vp, vp, vp, vp, i32, i32, vp], st),
             "grid_normalize": ([vp, vp, i32, vp, i32, vp], st),
@@ -112,6 +113,7 @@ def load():
             "cf_set_mueller": ([vp, vp, vp, vp], st),
             "awg_debug_fail_allocations": ([ctypes.c_int64], st),
             "awg_debug_live_allocations": ([], ctypes.c_int64),
+            "awg_debug_ws_withhold": ([ctypes.c_int32], st),
             "gcal_solve": ([vp, vp, vp, i64, i32, i32, i32, vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
                             i32, i32, vp, vp, vp, vp], st),
         }

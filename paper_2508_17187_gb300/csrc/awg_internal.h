@@ -48,11 +48,12 @@ __host__ __device__ constexpr int class_of_support(int S) {
 // barriers of a chunk (and the unequal flush work between warps) over more samples, which won
 // where two CTAs still fit (candidate 1 of supports 24-56: 1-3% on the W-projection workload).
 // Every support has kNumCand compiled candidates; candidate 0 is the default and cf_set_autotune
-// picks per support by timing.  The supports listed here and AWG_FOR_EXACT_AND_POLS must agree.
+// picks per support by timing.  Candidate 2 is the warp-specialised pair of kernels.  The supports
+// listed here and AWG_FOR_EXACT_AND_POLS must agree.
 struct ExactCfg {
   int S, g_grid, g_degrid, tile, stage;
 };
-constexpr int kNumCand = 2;
+constexpr int kNumCand = 3;
 constexpr ExactCfg kExactCand[kNumCand][8] = {
     {
         {8, 8, 8, 32, 16},
@@ -67,6 +68,18 @@ constexpr ExactCfg kExactCand[kNumCand][8] = {
     {
         {8, 8, 8, 16, 8},
         {16, 16, 16, 32, 16},
+        {24, 8, 8, 8, 16},
+        {32, 8, 8, 8, 16},
+        {40, 8, 8, 8, 12},
+        {48, 8, 8, 8, 16},
+        {56, 8, 8, 8, 16},
+        {64, 8, 8, 8, 4},
+    },
+    {
+        // candidate 2: the warp-specialised kernels (resample_ws.cuh) with these tiles; the
+        // cp.async kernels compiled with the same tiles serve the calls those cannot take
+        {8, 8, 8, 16, 8},
+        {16, 8, 8, 16, 8},
         {24, 8, 8, 8, 16},
         {32, 8, 8, 8, 16},
         {40, 8, 8, 8, 12},

@@ -622,7 +622,7 @@ awg_status cf_set_choose(awg_cf_set h, int32_t support, int32_t config) {
   CfSetImpl* cf = (CfSetImpl*)h;
   if (support < 1 || support > kMaxSupport || !has_exact(support))
     return set_error(AWG_ERR_INVALID_ARG, "support " + std::to_string(support) + " has no kernel configurations");
-  if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0 or 1");
+  if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0, 1 or 2");
   if (cf->fused && config != 0) return set_error(AWG_ERR_UNSUPPORTED, "fused kernels have one configuration");
   cf->cand[support] = (int8_t)config;
   fill_slots(cf);
@@ -1134,6 +1134,22 @@ awg_status plan_copy_index(awg_plan h, int32_t* kept, int32_t* cf_out, int32_t* 
     p0y[s] = r.p0y;
     ox[s] = r.ox;
     oy[s] = r.oy;
+  }
+  return AWG_OK;
+}
+
+awg_status plan_check(awg_plan h) {
+  if (!h) return set_error(AWG_ERR_INVALID_ARG, "plan is NULL");
+  PlanImpl* pl = (PlanImpl*)h;
+  if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
+  AWG_CUDA_TRY(cudaStreamSynchronize(pl->last_stream));
+  unsigned long long c[4];
+  AWG_CUDA_TRY(cudaMemcpy(c, pl->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c[3] != 0) {
+    const unsigned long long zero = 0;
+    AWG_CUDA_TRY(cudaMemcpy(pl->d_counters + 3, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    return set_error(AWG_ERR_TIMEOUT, "a bounded wait of a gridding or degridding kernel gave up (its results are "
+                                      "incomplete)");
   }
   return AWG_OK;
 }

@@ -1,0 +1,6 @@
+// Instantiations of the warp-specialised degridding kernels, supports 40-64.
+#include "resample_ws.cuh"
+
+namespace awg {
+AWG_FOR_WS_B(AWG_INSTANTIATE_DEGRID_WS)
+}  // namespace awg

@@ -3,8 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
-#include "resample_sep.cuh"
+#include "resample_ws.cuh"
 
 namespace awg {
 
@@ -18,6 +20,12 @@ AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 0)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 0)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 1)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 1)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 2)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 2)
+AWG_FOR_WS_A(AWG_DECLARE_GRID_WS)
+AWG_FOR_WS_B(AWG_DECLARE_GRID_WS)
+AWG_FOR_WS_A(AWG_DECLARE_DEGRID_WS)
+AWG_FOR_WS_B(AWG_DECLARE_DEGRID_WS)
 AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 2)
 AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 3)
 AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 4)
@@ -54,14 +62,34 @@ awg_status grid_class(int c, int P, const GridArgs& a, int sms, cudaStream_t st)
   return set_error(AWG_ERR_UNSUPPORTED, "no gridding kernel for this class / pol count");
 }
 
+// The warp-specialised kernels take P-contiguous visibilities and grids (no Mueller element
+// passes or pol mixing), 16-byte aligned buffers, and grids of at most 32768 pixels (window
+// origins packed in 16 bits); other calls on candidate 2 run the cp.async kernels of its tiles.
+bool ws_grid_ok(const GridArgs& a, int P) {
+  return a.mix == nullptr && a.vstride == P && a.voff == 0 && a.gstride == P && a.goff == 0 && a.N <= 32768 &&
+         ((uintptr_t)a.vis & 15) == 0 && ((uintptr_t)a.weight & 15) == 0 && ((uintptr_t)a.grid & 15) == 0;
+}
+
+bool ws_degrid_ok(const DegridArgs& a, int P) {
+  return a.mix == nullptr && a.gstride == P && a.goff == 0 && a.N <= 32768 && ((uintptr_t)a.grid & 15) == 0;
+}
+
 // Separable kernels run once per distinct support (slot): the exact-support kernel when there is
 // one for S, else the class kernel restricted to the slot's items.
 awg_status grid_slot_sep(int S, int cand, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
   if (has_exact(S)) {   // the plan binned this support by its exact-kernel tile
+    if (cand == 2 && ws_grid_ok(a, P)) {
+#define AWG_CASE(SS, PP) \
+  if (S == SS && P == PP) return run_grid_ws<SS, PP>(a, slot, sms, st);
+      AWG_FOR_WS_A(AWG_CASE)
+      AWG_FOR_WS_B(AWG_CASE)
+#undef AWG_CASE
+    }
 #define AWG_CASE(SS, PP, CC) \
   if (S == SS && P == PP && cand == CC) return run_grid_exact<SS, PP, CC>(a, slot, sms, st);
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 0)
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 1)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 2)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
   }
@@ -115,10 +143,18 @@ awg_status degrid_slot_fused(int S, int rk, int slot, int P, const DegridArgs& a
 
 awg_status degrid_slot_sep(int S, int cand, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
   if (has_exact(S)) {   // the plan binned this support by its exact-kernel tile
+    if (cand == 2 && ws_degrid_ok(a, P)) {
+#define AWG_CASE(SS, PP) \
+  if (S == SS && P == PP) return run_degrid_ws<SS, PP>(a, slot, sms, st);
+      AWG_FOR_WS_A(AWG_CASE)
+      AWG_FOR_WS_B(AWG_CASE)
+#undef AWG_CASE
+    }
 #define AWG_CASE(SS, PP, CC) \
   if (S == SS && P == PP && cand == CC) return run_degrid_exact<SS, PP, CC>(a, slot, sms, st);
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 0)
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 1)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 2)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
   }
@@ -217,6 +253,57 @@ __global__ void k_sum_terms(const float2* __restrict__ part, float2* __restrict_
   }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry points (the library does not link the
+// driver library itself).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)f;
+  });
+  return fn;
+}
+
+// The grid c64 [N][N][P] as a TMA tensor of FP32 values whose box is one U x U window: P >= 2 a
+// 3-D tensor (2P values of a pixel, x, y) with box (2P, U, U); P = 1 a 2-D tensor (2N values of a
+// row, y) with box (2 UB, U), UB = U rounded up to even, so that a box row is a whole number of
+// 16-byte units.  Out-of-grid parts of a box read as zero.
+awg_status make_grid_tensor_map(CUtensorMap* map, const void* grid, int N, int P, int U, int UB) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return set_error(AWG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  CUresult r;
+  if (P >= 2) {
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * P), (cuuint64_t)N, (cuuint64_t)N};
+    const cuuint64_t strides[2] = {(cuuint64_t)(2 * P * 4), (cuuint64_t)N * 2 * P * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * P), (cuuint32_t)U, (cuuint32_t)U};
+    const cuuint32_t es[3] = {1, 1, 1};
+    r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(grid), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)N * 2 * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * UB), (cuuint32_t)U};
+    const cuuint32_t es[2] = {1, 1};
+    r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(grid), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return set_error(AWG_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return AWG_OK;
+}
+
+// Test hook of awg_debug_ws_withhold: the next warp-specialised launch withholds a hand-over.
+static std::atomic<int> g_ws_withhold{0};
+
 static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* vis, const float* weight, void* grid,
                           void* grid_lo, double* sumwt, int flags, int P) {
   GridArgs a;
@@ -252,6 +339,8 @@ static GridArgs grid_args(const CfSetImpl* cf, const PlanImpl* pl, const void* v
   a.rank = pl->rank;
   a.mix = nullptr;
   a.pmask = (1 << P) - 1;
+  a.err = pl->d_counters + 3;
+  a.withhold = 0;
   return a;
 }
 
@@ -288,6 +377,8 @@ static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const voi
   a.rank = pl->rank;
   a.mix = nullptr;
   a.pmask = (1 << P) - 1;
+  a.err = pl->d_counters + 3;
+  a.withhold = 0;
   return a;
 }
 
@@ -304,7 +395,8 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
   if (s != AWG_OK) return s;
   pl->last_stream = st;
   if (pl->n == 0) return AWG_OK;
-  const GridArgs a = grid_args(cf, pl, vis, weight, grid, grid_lo, sumwt, flags, P);
+  GridArgs a = grid_args(cf, pl, vis, weight, grid, grid_lo, sumwt, flags, P);
+  a.withhold = g_ws_withhold.exchange(0);
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
   if (cf->n_mb > 1 && cf->mb_elements) {
@@ -375,7 +467,8 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   if (s != AWG_OK) return s;
   pl->last_stream = st;
   if (pl->n == 0) return AWG_OK;
-  const DegridArgs a = degrid_args(cf, pl, grid, vis_out, P);
+  DegridArgs a = degrid_args(cf, pl, grid, vis_out, P);
+  a.withhold = g_ws_withhold.exchange(0);
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
   if (cf->n_mb > 1 && cf->mb_elements) {
@@ -585,3 +678,9 @@ awg_status launch_normalize(CfSetImpl* cf, void* image, int P, const double* sum
 }
 
 }  // namespace awg
+
+extern "C" awg_status awg_debug_ws_withhold(int32_t on) {
+  if (on != 0 && on != 1) return awg::set_error(AWG_ERR_INVALID_ARG, "on must be 0 or 1");
+  awg::g_ws_withhold.store(on);
+  return AWG_OK;
+}

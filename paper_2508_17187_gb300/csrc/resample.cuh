@@ -59,6 +59,8 @@ struct GridArgs {
   // add their weights to sumwt.  Otherwise mix = NULL and pmask has all P bits set.
   const float2* mix;
   int pmask;
+  unsigned long long* err;   // error word of the launch (a bounded wait that gave up), or NULL
+  int withhold;              // test hook (awg_debug_ws_withhold): withhold the first chunk's hand-over
 };
 
 struct DegridArgs {
@@ -88,6 +90,8 @@ struct DegridArgs {
   // set in pmask are written.
   const float2* mix;
   int pmask;
+  unsigned long long* err;   // error word of the launch (a bounded wait that gave up), or NULL
+  int withhold;              // test hook (awg_debug_ws_withhold): withhold the first chunk's hand-over
 };
 
 template <bool BF16>

@@ -12,16 +12,19 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("config", ["wproj", "awproj"])
+@pytest.mark.parametrize("config", ["wproj", "awproj", "wproj_ws"])
 def test_step_replays_from_cuda_graph(config):
     import paper_2508_17187_gb300 as awg
-    if config == "wproj":
+    if config in ("wproj", "wproj_ws"):
         wl = synth.make_workload("wproj", n_int=24, n_chan=8, grid_n=1024, n_wplanes=8, vis_device="cuda")
     else:
         wl = synth.make_workload("awproj", n_int=12, n_chan=8, grid_n=512, n_pa=3, n_sb=2, n_wplanes=4,
                                  max_support=32, oversampling=8, vis_device="cuda")
     op = oracle_params(wl)
     cf = awg.cf_set_create(**library_params(op))
+    if config == "wproj_ws":   # the warp-specialised kernels (their tensor maps are built at capture)
+        for S in sorted(set(cf.supports().tolist())):
+            cf.choose(S, 2)
     uvw = torch.as_tensor(wl.uvw_m).cuda()
     freq = torch.as_tensor(wl.freq_hz).cuda()
     pa = torch.as_tensor(wl.pa_bin).cuda() if wl.use_a else None

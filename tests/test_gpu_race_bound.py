@@ -26,8 +26,8 @@ pytestmark = pytest.mark.gpu
 U = 2.0 ** -24
 
 
-@pytest.mark.parametrize("separable", [True, False])
-def test_every_pixel_within_its_rounding_bound(separable):
+@pytest.mark.parametrize("separable,config", [(True, 0), (False, 0), (True, 2)])
+def test_every_pixel_within_its_rounding_bound(separable, config):
     import paper_2508_17187_gb300 as awg
     from paper_2508_17187_gb300 import _lib
     _lib.load()
@@ -38,6 +38,10 @@ def test_every_pixel_within_its_rounding_bound(separable):
     n = R * C
     cf = awg.cf_set_create(**library_params(op, separable=separable))
     assert cf.separable == separable
+    if config:   # the warp-specialised kernels on every exact support
+        for S in sorted(set(cf.supports().tolist())):
+            if S % 8 == 0:
+                cf.choose(S, config)
     uvw = torch.as_tensor(wl.uvw_m).cuda()
     freq = torch.as_tensor(wl.freq_hz).cuda()
     plan = awg.plan_create(cf, uvw, freq)
@@ -49,6 +53,7 @@ def test_every_pixel_within_its_rounding_bound(separable):
     out = torch.empty_like(vis)
     awg.degrid_visibilities(cf, plan, g, out)
     torch.cuda.synchronize()
+    plan.check()
     g_gpu = g.cpu().numpy().astype(np.complex128)
     d_gpu = out.cpu().numpy().reshape(n, P).astype(np.complex128)
 
@@ -80,7 +85,8 @@ def test_every_pixel_within_its_rounding_bound(separable):
     d_err = np.abs(d_gpu - d_ref)
     d_worst = float((d_err / np.where(d_bound > 0, d_bound, 1.0)).max())
     assert np.all(d_err <= d_bound), d_worst
-    print(f"separable={separable}: worst pixel at {worst:.3f} of its bound, worst sample at {d_worst:.3f}")
+    print(f"separable={separable} config={config}: worst pixel at {worst:.3f} of its bound, "
+          f"worst sample at {d_worst:.3f}")
 
 
 def _factor_tables(cf, op, used):
