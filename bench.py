@@ -876,10 +876,11 @@ def main():
     pa_bin = torch.as_tensor(wl.pa_bin, device=dev) if wl.use_a else None
     chan_sb = torch.as_tensor(wl.chan_subband, device=dev) if wl.use_a else None
     vis, wt = wl.vis, wl.weight
-    tuned, t_tune = None, None
+    tuned, t_tune, tune_ms = None, None, None
     if not args.no_autotune:
         t_tune = time.perf_counter()
-        tuned, _ = cf.autotune(uvw, freq, pa_bin, chan_sb, n_pol=wl.n_pol)
+        tuned, tune_ms = cf.autotune(uvw, freq, pa_bin, chan_sb, n_pol=wl.n_pol)
+        tune_ms = {S: [round(t, 3) for t in v] for S, v in tune_ms.items()}
         t_tune = time.perf_counter() - t_tune
     plan = awg.plan_create(cf, uvw, freq, pa_bin, chan_sb)
     if args.mosaic:
@@ -1105,6 +1106,7 @@ def main():
                    "cf_terms": max(cf.rank, 1), "cf_storage":
                    "separable factors" if cf.separable else "full tables", "cf_build_s": t_cf,
                    "kernel_config_per_support": tuned, "autotune_s": t_tune,
+                   "autotune_ms_per_config": tune_ms,
                    "visibilities_per_step": vis_per_step, "kept_samples": kept, "dropped_samples": dropped,
                    "mean_taps": sum_taps / max(kept, 1), "l2": "inputs larger than L2 (2.7 GB per step)",
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},

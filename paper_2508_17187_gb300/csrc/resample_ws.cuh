@@ -3,18 +3,19 @@
 // CTA barriers replaced by a ring of shared-memory stages handed over on mbarriers.
 //
 // Roles (one persistent CTA pulls work items of one support from its queue):
-//  * warp 0, the producer, walks the CTA's items chunk by chunk.  For chunk k it copies the records
-//    of chunk k + 1 and the factor rows, visibilities, weights and phasors of chunk k with cp.async,
-//    and while those are in flight it finishes chunk k - 1 (gridding: the table
-//    alpha[j][rx][p] = conj(fx_j[(rx - mx_j) mod S]) w_jp V_jp, the weight sums) and hands its
-//    stage to the consumers.  fy is stored rotated, fyr[j][ry] = fy_j[(ry - my_j) mod S], so a
-//    consumer finds the factor of each of its rows at a fixed offset.
+//  * warp 0, the producer, walks the CTA's items chunk by chunk.  It keeps the records of the next
+//    two chunks and the visibilities, weights and phasors of the next one in registers (loads
+//    issued ahead), and for each chunk writes the packed first-tap positions, w V times the phasor
+//    (gridding) or the output rows and phasors (degridding) into a free stage and moves each
+//    sample's two factor rows fx[ox][.], fy[oy][.] into it with one TMA bulk copy per row, whose
+//    bytes complete the stage's barrier.
 //  * the consumer warps own the taps by residue as in resample_sep.cuh (thread: column residue rx,
 //    rows ry0 + k G) and run only the multiply-add loop over the samples of each stage; a stage is
-//    released to the producer when every consumer thread has read it.
-//  * gridding: warp 1 flushes.  The consumers accumulate an item in one of NWIN shared windows and
-//    hand it to the flush warp, which adds it to the grid (one vector atomic per non-zero pixel)
-//    and zeroes it, while the consumers go on with the next item in the other window.
+//    released when every consumer thread has read it.
+//  * gridding: the consumers accumulate an item in one of NWIN shared windows.  A window pixel is
+//    only ever touched by the thread whose residues it has, so at the end of the item each thread
+//    adds its own pixels to the grid (one vector atomic per non-zero pixel) and zeroes them, with
+//    no barrier; a window is reused NWIN items later, once every thread has flushed it.
 //  * degridding: warp 1 reduces.  The producer loads each item's grid window with one TMA tile
 //    copy (cp.async.bulk.tensor) into one of NWIN windows; the consumers leave one warp-reduced
 //    value per lane and batch of every stage, and the reduce warp adds the consumer warps' values,
@@ -37,8 +38,25 @@ struct __align__(16) WsHeader {
   int nst;     // samples in the stage; -1: no more work
   int flags;   // kWsFirst / kWsLast of the item
   int xy;      // X0 | Y0 << 16 of the item's window
-  int pad;
+  int nr;      // runs of equal first-tap position in the stage
 };
+
+// The runs of a chunk: samples [rs[r], rs[r + 1]) share the packed first-tap position rpk[r] (the
+// samples of an item are sorted by first tap).  Written by the producer warp from the packed
+// positions of its lanes (lane j < nst holds sample j's); returns the number of runs.
+__device__ __forceinline__ int ws_runs(int pk, int nst, int lane, int* rs, int* rpk) {
+  const int up = __shfl_up_sync(0xffffffffu, pk, 1);
+  const bool start = lane < nst && (lane == 0 || up != pk);
+  const unsigned m = __ballot_sync(0xffffffffu, start);
+  const int nr = __popc(m);
+  if (start) {
+    const int r = __popc(m & ((1u << lane) - 1u));
+    rs[r] = lane;
+    rpk[r] = pk;
+  }
+  if (lane == 0) rs[nr] = nst;
+  return nr;
+}
 
 // Column residue and first row of consumer thread t of NC warps (as tap_owner): a warp covers 8
 // consecutive columns x 4 row groups when the columns split into blocks of 8 that the warps tile,
@@ -59,85 +77,173 @@ __device__ __forceinline__ void ws_owner(int t, int& rx, int& ry0) {
 constexpr size_t ws_al16(size_t b) { return (b + 15) & ~(size_t)15; }
 constexpr size_t ws_al1k(size_t b) { return (b + 1023) & ~(size_t)1023; }
 
-// ------------------------------------------------------------------------------------ gridding
-
-template <int S, int P, int G, int TILE, int ST, int D, int NWIN>
-struct WsGridLayout {
-  static_assert(S % G == 0 && (S * G) % 32 == 0, "row groups must divide S and fill whole warps");
-  static constexpr int NC = S * G / 32;          // consumer warps
-  static constexpr int NT = 32 * (NC + 2);       // + producer + flush warp
-  static constexpr int R = S / G;                // rows per consumer thread
-  static constexpr int U = TILE + S - 1;
-  static constexpr int UU = U * U;
-  static constexpr size_t win_bytes = ws_al16((size_t)UU * P * 8);   // pol-planar float2 [P][U][U]
-  // a stage: header, packed positions, rotated fy rows, the alpha table
-  static constexpr size_t st_pk = 16;
-  static constexpr size_t st_fy = st_pk + ws_al16(4 * ST);
-  static constexpr size_t st_al = st_fy + (size_t)ST * S * 8;
-  static constexpr size_t stage_bytes = ws_al16(st_al + (size_t)ST * S * P * 8);
-  // a producer staging slot: records, fx rows, visibilities, weights, phasors, derived data
-  static constexpr size_t ps_rec = 0;
-  static constexpr size_t ps_fx = ps_rec + 16 * (size_t)ST;
-  static constexpr size_t ps_v = ps_fx + (size_t)ST * S * 8;
-  static constexpr size_t ps_w = ps_v + (size_t)ST * P * 8;
-  static constexpr size_t ps_ph = ps_w + ws_al16(4 * (size_t)ST * P);
-  static constexpr size_t ps_off = ps_ph + 8 * (size_t)ST;   // long long [ST][2]: fx, fy row offsets
-  static constexpr size_t ps_src = ps_off + 16 * (size_t)ST; // int [ST]
-  static constexpr size_t ps_pk = ps_src + ws_al16(4 * (size_t)ST);
-  static constexpr size_t ps_wt0 = ps_pk + ws_al16(4 * (size_t)ST);   // int [ST]: adds its weight
-  static constexpr size_t pstage_bytes = ws_al16(ps_wt0 + 4 * (size_t)ST);
-  static constexpr size_t off_stage = NWIN * win_bytes;
-  static constexpr size_t off_pstage = off_stage + D * stage_bytes;
-  static constexpr size_t off_bar = off_pstage + 2 * pstage_bytes;
-  static constexpr size_t off_misc = off_bar + 8 * (2 * D + 2 * NWIN);
-  static constexpr size_t off_soff = ws_al16(off_misc + 16 + 4 * NWIN);   // int64 [kSepOffCache]
-  static constexpr size_t bytes = off_soff + 8 * (size_t)kSepOffCache;
-  static constexpr size_t alloc = bytes + 1024;   // the layout starts at the first 1024-byte boundary
-};
-
 // The producer's walk over the CTA's items: descriptor of one chunk.
 struct WsChunk {
   int start, nst, xy, flags;
   bool valid;
 };
 
+// The producer's walk over the items a CTA takes from its queue, with the next item fetched ahead:
+// the queue atomic is issued when an item is taken, its result is read and the next item's
+// descriptor loaded one chunk later, and both are ready long before the current item ends (a
+// wait happens only when an item has a single chunk).  All lanes of the producer warp keep the
+// same state; the atomic's result lives in lane 0.
 struct WsItemWalker {
-  int begin, end, cls, tile;
+  int begin, end, cls, tile, st;
   int32_t* queue;
   const WorkItem* items;
-  int st;          // samples per chunk
-  int it;          // current item (>= end: none)
-  WorkItem wi;
-  int c, nch;      // next chunk of the current item, chunks of the item
-  int pending;     // index of the item after the current one (fetched when the current one starts)
+  WorkItem cur, nxt;
+  int c, nch;        // next chunk of the current item, chunks of the item
+  bool cur_valid;
+  int q_raw;         // lane 0: the queue position the atomic returned
+  int q_state;       // 1: atomic issued, 2: next item loaded, 3: queue exhausted
 
-  __device__ __forceinline__ int fetch() {
-    int v = 0;
-    if ((threadIdx.x & 31) == 0) v = begin + atomicAdd(queue + cls, 1);
-    return __shfl_sync(0xffffffffu, v, 0);
+  __device__ __forceinline__ void issue() {
+    if ((threadIdx.x & 31) == 0) q_raw = atomicAdd(queue + cls, 1);
+    q_state = 1;
   }
-  __device__ __forceinline__ void load(int i) {
-    it = i;
-    if (it < end) {
-      wi = items[it];
-      nch = (wi.count + st - 1) / st;
-      c = 0;
-      pending = fetch();
+  __device__ __forceinline__ void advance() {
+    if (q_state == 1) {
+      const int idx = begin + __shfl_sync(0xffffffffu, q_raw, 0);
+      if (idx < end) {
+        nxt = items[idx];
+        q_state = 2;
+      } else {
+        q_state = 3;
+      }
     }
   }
-  __device__ __forceinline__ void init() { load(fetch()); }
+  __device__ __forceinline__ void take() {
+    advance();
+    if (q_state == 2) {
+      cur = nxt;
+      cur_valid = true;
+      c = 0;
+      nch = (cur.count + st - 1) / st;
+      issue();
+    } else {
+      cur_valid = false;
+    }
+  }
+  __device__ __forceinline__ void init(int b, int e, int cl, int t, int stage, int32_t* q, const WorkItem* it) {
+    begin = b;
+    end = e;
+    cls = cl;
+    tile = t;
+    st = stage;
+    queue = q;
+    items = it;
+    cur_valid = false;
+    issue();
+    take();
+  }
   __device__ __forceinline__ WsChunk next() {
     WsChunk d{0, 0, 0, 0, false};
-    if (it < end && c >= nch) load(pending);
-    if (it >= end) return d;
-    d.start = wi.start + c * st;
-    d.nst = min(st, wi.count - c * st);
-    d.xy = (wi.tile_x * tile) | ((wi.tile_y * tile) << 16);
+    if (cur_valid && c >= nch) take();
+    if (!cur_valid) return d;
+    d.start = cur.start + c * st;
+    d.nst = min(st, cur.count - c * st);
+    d.xy = (cur.tile_x * tile) | ((cur.tile_y * tile) << 16);
     d.flags = (c == 0 ? kWsFirst : 0) | (c == nch - 1 ? kWsLast : 0);
     d.valid = true;
     ++c;
+    advance();   // one step of the fetch-ahead per chunk
     return d;
   }
+};
+
+// Record of sample `lane` of a chunk (a zero record past its end).
+__device__ __forceinline__ SampleRec ws_load_rec(const SampleRec* rec, const WsChunk& d, int lane) {
+  SampleRec r{};
+  if (d.valid && lane < d.nst) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(rec + d.start + lane));
+    r = *reinterpret_cast<const SampleRec*>(&v);
+  }
+  return r;
+}
+
+// Factor-row offsets (in complex values) of a record: fx[ox][.] and fy[oy][.] of its CF term.
+template <int S>
+__device__ __forceinline__ void ws_rows(const int64_t* offs, int64_t cf_shift, int OS, const SampleRec& rc,
+                                        long long& fxo, long long& fyo) {
+  const long long base = offs[cf_shift + rc.cf];
+  fxo = base + (long long)rc.ox * S;
+  fyo = base + (long long)(OS + 1) * S + (long long)rc.oy * S;
+}
+
+// Visibilities, weights and phasor of one sample, loaded by the producer a chunk ahead.
+template <int P>
+struct WsVis {
+  float2 v[P];
+  float w[P];
+  float2 ph;
+};
+
+template <int P>
+__device__ __forceinline__ WsVis<P> ws_load_vis(const GridArgs& a, const WsChunk& d, const SampleRec& rc, int lane) {
+  WsVis<P> x;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    x.v[p] = make_float2(0.f, 0.f);
+    x.w[p] = 0.f;
+  }
+  x.ph = make_float2(1.f, 0.f);
+  if (d.valid && lane < d.nst) {
+    const size_t s = (size_t)rc.src;
+    if constexpr (P == 4) {
+      const float4 a0 = __ldg(reinterpret_cast<const float4*>(a.vis + s * 8));
+      const float4 a1 = __ldg(reinterpret_cast<const float4*>(a.vis + s * 8 + 4));
+      const float4 ww = __ldg(reinterpret_cast<const float4*>(a.weight + s * 4));
+      x.v[0] = make_float2(a0.x, a0.y);
+      x.v[1] = make_float2(a0.z, a0.w);
+      x.v[2] = make_float2(a1.x, a1.y);
+      x.v[3] = make_float2(a1.z, a1.w);
+      x.w[0] = ww.x;
+      x.w[1] = ww.y;
+      x.w[2] = ww.z;
+      x.w[3] = ww.w;
+    } else if constexpr (P == 2) {
+      const float4 a0 = __ldg(reinterpret_cast<const float4*>(a.vis + s * 4));
+      const float2 ww = __ldg(reinterpret_cast<const float2*>(a.weight + s * 2));
+      x.v[0] = make_float2(a0.x, a0.y);
+      x.v[1] = make_float2(a0.z, a0.w);
+      x.w[0] = ww.x;
+      x.w[1] = ww.y;
+    } else {
+      x.v[0] = __ldg(reinterpret_cast<const float2*>(a.vis) + s);
+      x.w[0] = __ldg(a.weight + s);
+    }
+    if (a.phasor) x.ph = __ldg(a.phasor + rc.src);
+  }
+  return x;
+}
+
+// ------------------------------------------------------------------------------------ gridding
+
+template <int S, int P, int G, int TILE, int ST, int D, int NWIN>
+struct WsGridLayout {
+  static_assert(S % G == 0 && (S * G) % 32 == 0, "row groups must divide S and fill whole warps");
+  static_assert(S % 2 == 0, "factor rows move in 16-byte units");
+  static constexpr int NC = S * G / 32;          // consumer warps
+  static constexpr int NT = 32 * (NC + 1);       // + the producer
+  static constexpr int R = S / G;                // rows per consumer thread
+  static constexpr int U = TILE + S - 1;
+  static constexpr int UU = U * U;
+  static constexpr size_t win_bytes = ws_al16((size_t)UU * P * 8);   // pol-planar float2 [P][U][U]
+  // a stage: header, runs (starts, positions), fy rows twice over (fy[t] at t and t + S, so that a
+  // thread's rows sit at fixed offsets from S - my), fx rows, w V (times the phasor) per pol
+  static constexpr size_t st_rs = 16;
+  static constexpr size_t st_rpk = st_rs + ws_al16(4 * (ST + 1));
+  static constexpr size_t st_fy = st_rpk + ws_al16(4 * ST);
+  static constexpr size_t st_fx = st_fy + (size_t)ST * 2 * S * 8;
+  static constexpr size_t st_wv = st_fx + (size_t)ST * S * 8;
+  static constexpr size_t stage_bytes = ws_al16(st_wv + (size_t)ST * P * 8);
+  static constexpr size_t off_stage = NWIN * win_bytes;
+  static constexpr size_t off_bar = off_stage + D * stage_bytes;
+  static constexpr size_t off_misc = off_bar + 8 * (2 * D + NWIN);
+  static constexpr size_t off_soff = ws_al16(off_misc + 16);   // int64 [kSepOffCache]
+  static constexpr size_t bytes = off_soff + 8 * (size_t)kSepOffCache;
+  static constexpr size_t alloc = bytes + 1024;   // the layout starts at the first 1024-byte boundary
 };
 
 template <int S, int P, int G, int TILE, int ST, int D, int NWIN, int MINB>
@@ -150,10 +256,8 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
   int64_t* s_off = reinterpret_cast<int64_t*>(smem + L::off_soff);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);
   uint64_t* empty = full + D;
-  uint64_t* wfull = full + 2 * D;
-  uint64_t* wempty = wfull + NWIN;
+  uint64_t* wdone = full + 2 * D;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::off_misc);
-  int* win_info = reinterpret_cast<int*>(smem + L::off_misc + 16);
   unsigned long long* err = a.err;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -166,10 +270,7 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
       mbar_init(full + d, 32);
       mbar_init(empty + d, NC * 32);
     }
-    for (int w = 0; w < NWIN; ++w) {
-      mbar_init(wfull + w, NC * 32);
-      mbar_init(wempty + w, 32);
-    }
+    for (int w = 0; w < NWIN; ++w) mbar_init(wdone + w, NC * 32);
     *abort_flag = 0;
     mbar_fence_init();
   }
@@ -184,218 +285,131 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
     double wsum[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) wsum[p] = 0.0;
-    WsItemWalker walk{a.class_range[cls], a.class_range[cls + 1], cls, TILE, a.queue, a.items, ST, 0, {}, 0, 0, 0};
-    walk.init();
+    WsItemWalker walk;
+    walk.init(a.class_range[cls], a.class_range[cls + 1], cls, TILE, ST, a.queue, a.items);
     const float2* sep2 = reinterpret_cast<const float2*>(a.sep);
-    auto pst = [&](int i) { return smem + L::off_pstage + (size_t)(i & 1) * L::pstage_bytes; };
-    auto stg = [&](int i) { return smem + L::off_stage + (size_t)(i % D) * L::stage_bytes; };
-    auto issue_recs = [&](const WsChunk& d, unsigned char* ps) {
-      if (lane < d.nst) cp_async(ps + L::ps_rec + 16 * lane, a.rec + d.start + lane, 16);
-    };
-    WsChunk dk = walk.next();
-    if (dk.valid) issue_recs(dk, pst(0));
-    cp_async_commit();
-    WsChunk dprev{0, 0, 0, 0, false};
+    // loads run ahead of their use: the records three chunks, the visibilities two
+    WsChunk d0 = walk.next();
+    WsChunk d1 = walk.next();
+    WsChunk d2 = walk.next();
+    SampleRec r0 = ws_load_rec(a.rec, d0, lane);
+    SampleRec r1 = ws_load_rec(a.rec, d1, lane);
+    SampleRec r2 = ws_load_rec(a.rec, d2, lane);
+    WsVis<P> x0 = ws_load_vis<P>(a, d0, r0, lane);
+    WsVis<P> x1 = ws_load_vis<P>(a, d1, r1, lane);
     int k = 0;
     bool ok = true;
-    for (;;) {
-      cp_async_wait_all();
-      __syncwarp();
-      const WsChunk dn = dk.valid ? walk.next() : WsChunk{0, 0, 0, 0, false};
-      if (dk.valid) {
-        unsigned char* ps = pst(k);
-        unsigned char* sg = stg(k);
-        if (!mbar_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
-          ok = false;
-          break;
-        }
-        // derive chunk k from its records: packed window position, factor-row offsets, source row
-        if (lane < dk.nst) {
-          const SampleRec rc = reinterpret_cast<const SampleRec*>(ps + L::ps_rec)[lane];
-          const int X0 = dk.xy & 0xffff, Y0 = dk.xy >> 16;
-          const int mx = rc.p0x % S, my = rc.p0y % S;
-          const int pk = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | (mx << 16) | (my << 24);
-          const long long base = offs[a.cf_shift + rc.cf];
-          reinterpret_cast<long long*>(ps + L::ps_off)[2 * lane] = base + (long long)rc.ox * S;
-          reinterpret_cast<long long*>(ps + L::ps_off)[2 * lane + 1] =
-              base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
-          reinterpret_cast<int*>(ps + L::ps_src)[lane] = rc.src;
-          reinterpret_cast<int*>(ps + L::ps_pk)[lane] = pk;
-          reinterpret_cast<int*>(ps + L::ps_wt0)[lane] = (a.rank == 1 || rc.cf % a.rank == 0) ? 1 : 0;
-          reinterpret_cast<int*>(sg + L::st_pk)[lane] = pk;
-        }
-        __syncwarp();
-        // fy rotated into the stage, fx as stored into the staging slot (8-byte copies)
-        const long long* off = reinterpret_cast<const long long*>(ps + L::ps_off);
-        const int* pkv = reinterpret_cast<const int*>(ps + L::ps_pk);
-        float2* fyr = reinterpret_cast<float2*>(sg + L::st_fy);
-        float2* fxs = reinterpret_cast<float2*>(ps + L::ps_fx);
-        for (int i = lane; i < dk.nst * S; i += 32) {
-          const int j = i / S, t = i - j * S;
-          int ry = t + ((pkv[j] >> 24) & 0xff);   // fyr[j][(t + my) mod S] = fy_j[t]
-          ry -= (ry >= S) ? S : 0;
-          cp_async(fyr + j * S + ry, sep2 + off[2 * j + 1] + t, 8);
-          cp_async(fxs + i, sep2 + off[2 * j] + t, 8);
-        }
-        if (lane < dk.nst) {
-          const size_t s = (size_t)reinterpret_cast<const int*>(ps + L::ps_src)[lane];
-          const float* vp = a.vis + s * P * 2;
-          const float* wp = a.weight + s * P;
-          float2* v = reinterpret_cast<float2*>(ps + L::ps_v) + lane * P;
-          float* w = reinterpret_cast<float*>(ps + L::ps_w) + lane * P;
-          if constexpr (P == 4) {
-            cp_async(v, vp, 16);
-            cp_async(v + 2, vp + 4, 16);
-            cp_async(w, wp, 16);
-          } else if constexpr (P == 2) {
-            cp_async(v, vp, 16);
-            cp_async(w, wp, 8);
-          } else {
-            cp_async(v, vp, 8);
-            cp_async(w, wp, 4);
-          }
-          float2* ph = reinterpret_cast<float2*>(ps + L::ps_ph) + lane;
-          if (a.phasor) {
-            const SampleRec rc = reinterpret_cast<const SampleRec*>(ps + L::ps_rec)[lane];
-            cp_async(ph, a.phasor + rc.src, 8);
-          } else {
-            *ph = make_float2(1.f, 0.f);
-          }
-        }
-        if (dn.valid) issue_recs(dn, pst(k + 1));
-        cp_async_commit();
+    while (d0.valid) {
+      const int s = k % D;
+      unsigned char* sg = smem + L::off_stage + (size_t)s * L::stage_bytes;
+      if (!mbar_wait(empty + s, ((k / D) & 1) ^ 1, abort_flag, err)) {
+        ok = false;
+        break;
       }
-      if (dprev.valid) {
-        // finish chunk k - 1 (its copies landed at the top of this pass): alpha, weights, header
-        unsigned char* ps = pst(k - 1);
-        unsigned char* sg = stg(k - 1);
-        const int nst = dprev.nst;
-        const float2* v = reinterpret_cast<const float2*>(ps + L::ps_v);
-        const float* w = reinterpret_cast<const float*>(ps + L::ps_w);
-        const float2* ph = reinterpret_cast<const float2*>(ps + L::ps_ph);
-        if (lane < nst && reinterpret_cast<const int*>(ps + L::ps_wt0)[lane]) {
+      const int X0 = d0.xy & 0xffff, Y0 = d0.xy >> 16;
+      const int pk = (r0.p0x - X0) | ((r0.p0y - Y0) << 8) | ((r0.p0x % S) << 16) | ((r0.p0y % S) << 24);
+      const int nr = ws_runs(pk, d0.nst, lane, reinterpret_cast<int*>(sg + L::st_rs),
+                             reinterpret_cast<int*>(sg + L::st_rpk));
+      if (lane < d0.nst) {
+        long long fxo, fyo;
+        ws_rows<S>(offs, a.cf_shift, a.OS, r0, fxo, fyo);
+        fence_proxy_async_smem();   // the consumers' reads of this stage come before the copies
+        bulk_load(sg + L::st_fx + (size_t)lane * S * 8, sep2 + fxo, S * 8, full + s);
+        bulk_load(sg + L::st_fy + (size_t)lane * 2 * S * 8, sep2 + fyo, S * 8, full + s);
+        bulk_load(sg + L::st_fy + (size_t)lane * 2 * S * 8 + S * 8, sep2 + fyo, S * 8, full + s);
+        float2 o[P];
 #pragma unroll
-          for (int p = 0; p < P; ++p) wsum[p] += (double)w[lane * P + p];
+        for (int p = 0; p < P; ++p) {
+          const float xr = x0.w[p] * x0.v[p].x, xi = x0.w[p] * x0.v[p].y;
+          o[p] = make_float2(xr * x0.ph.x - xi * x0.ph.y, xr * x0.ph.y + xi * x0.ph.x);
         }
-        const int* pkv = reinterpret_cast<const int*>(ps + L::ps_pk);
-        const float2* fxs = reinterpret_cast<const float2*>(ps + L::ps_fx);
-        float2* al = reinterpret_cast<float2*>(sg + L::st_al);
-        for (int i = lane; i < nst * S; i += 32) {
-          const int j = i / S, rx = i - j * S;
-          int tx = rx - ((pkv[j] >> 16) & 0xff);
-          tx += (tx < 0) ? S : 0;
-          const float2 f = fxs[j * S + tx];
-          const float2 phj = ph[j];
-          float2 o[P];
+        float2* dst = reinterpret_cast<float2*>(sg + L::st_wv) + lane * P;
+        if constexpr (P % 2 == 0) {
 #pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const float wv = w[j * P + p];
-            const float2 vv = v[j * P + p];
-            const float xr = wv * vv.x, xi = wv * vv.y;
-            const float ar = xr * phj.x - xi * phj.y, ai = xr * phj.y + xi * phj.x;
-            o[p] = make_float2(f.x * ar + f.y * ai, f.x * ai - f.y * ar);   // conj(fx) w V ph
-          }
-          float2* dst = al + (size_t)i * P;
-          if constexpr (P % 2 == 0) {
-#pragma unroll
-            for (int q = 0; q < P / 2; ++q)
-              reinterpret_cast<float4*>(dst)[q] = make_float4(o[2 * q].x, o[2 * q].y, o[2 * q + 1].x, o[2 * q + 1].y);
-          } else {
-            dst[0] = o[0];
-          }
+          for (int q = 0; q < P / 2; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(o[2 * q].x, o[2 * q].y, o[2 * q + 1].x, o[2 * q + 1].y);
+        } else {
+          dst[0] = o[0];
         }
-        if (lane == 0) *reinterpret_cast<WsHeader*>(sg) = WsHeader{nst, dprev.flags, dprev.xy, 0};
-        if (!(a.withhold && k == 1)) mbar_arrive(full + (k - 1) % D);
+        if (a.rank == 1 || r0.cf % a.rank == 0) {   // term 0 of a sample adds its weights
+#pragma unroll
+          for (int p = 0; p < P; ++p) wsum[p] += (double)x0.w[p];
+        }
       }
-      if (!dk.valid) break;
-      dprev = dk;
-      dk = dn;
+      if (lane == 0) *reinterpret_cast<WsHeader*>(sg) = WsHeader{d0.nst, d0.flags, d0.xy, nr};
+      // hand over: lane 0 announces the bytes of the chunk's row copies; with the 32 arrivals and
+      // those bytes the stage is full
+      if (!(a.withhold && k == 0)) {
+        if (lane == 0) mbar_arrive_expect_tx(full + s, (unsigned)(d0.nst * 3 * S * 8));
+        else mbar_arrive(full + s);
+      }
+      const WsChunk d3 = walk.next();
+      const SampleRec r3 = ws_load_rec(a.rec, d3, lane);
+      const WsVis<P> x2 = ws_load_vis<P>(a, d2, r2, lane);
+      d0 = d1;
+      d1 = d2;
+      d2 = d3;
+      r0 = r1;
+      r1 = r2;
+      r2 = r3;
+      x0 = x1;
+      x1 = x2;
       ++k;
     }
     if (ok && mbar_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
-      if (lane == 0) *reinterpret_cast<WsHeader*>(stg(k)) = WsHeader{-1, 0, 0, 0};
+      if (lane == 0) *reinterpret_cast<WsHeader*>(smem + L::off_stage + (size_t)(k % D) * L::stage_bytes) =
+          WsHeader{-1, 0, 0, 0};
       mbar_arrive(full + k % D);
     }
-    cp_async_wait_all();
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      double s = wsum[p];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0 && s != 0.0 && a.sumwt) atomicAdd(a.sumwt + p, s);
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------------------------ flush warp
-    for (int ic = 0;; ++ic) {
-      const int w = ic % NWIN;
-      if (!mbar_wait(wfull + w, (ic / NWIN) & 1, abort_flag, err)) break;
-      const int info = win_info[w];
-      if (info < 0) break;
-      const int X0 = info & 0xffff, Y0 = info >> 16;
-      float2* win = reinterpret_cast<float2*>(smem + (size_t)w * L::win_bytes);
-      for (int i = lane; i < UU; i += 32) {
-        const int ly = i / U, lx = i - ly * U;
-        const int gy = Y0 + ly, gx = X0 + lx;
-        float2 v[P];
-        bool nz = false;
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          v[p] = win[p * UU + i];
-          nz |= (v[p].x != 0.f) || (v[p].y != 0.f);
-        }
-        if (nz) {
-#pragma unroll
-          for (int p = 0; p < P; ++p) win[p * UU + i] = make_float2(0.f, 0.f);
-          if (gy < a.N && gx < a.N) flush_pixel<P>(a, ((size_t)gy * a.N + gx) * P, v);
-        }
-      }
-      mbar_arrive(wempty + w);
+      double v = wsum[p];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && v != 0.0 && a.sumwt) atomicAdd(a.sumwt + p, v);
     }
   } else {
     // ------------------------------------------------------------------------------ consumers
-    const int ct = tid - 64;
+    const int ct = tid - 32;
     int rx, ry0;
     ws_owner<S, G>(ct, rx, ry0);
     float2 acc[R][P];
     int curY[R], Y[R];
-    int curX = -1, prev_pk = -1, prev_row = -1;
+    int curX = -1, tx = 0, rowoff = 0, prev_pk = -1, prev_row = -1;
+    int X0 = 0, Y0 = 0;
     float2* win = reinterpret_cast<float2*>(smem);
     int ic = 0;
+#pragma unroll
+    for (int kk = 0; kk < R; ++kk) {
+      curY[kk] = -1;
+      Y[kk] = 0;
+#pragma unroll
+      for (int p = 0; p < P; ++p) acc[kk][p] = make_float2(0.f, 0.f);
+    }
     for (int k = 0;; ++k) {
-      unsigned char* sg = smem + L::off_stage + (size_t)(k % D) * L::stage_bytes;
-      if (!mbar_wait(full + k % D, (k / D) & 1, abort_flag, err)) break;
+      const int s = k % D;
+      unsigned char* sg = smem + L::off_stage + (size_t)s * L::stage_bytes;
+      if (!mbar_wait(full + s, (k / D) & 1, abort_flag, err)) break;
       const WsHeader h = *reinterpret_cast<const WsHeader*>(sg);
+      if (h.nst < 0) break;
       const int w = ic % NWIN;
-      if (h.nst < 0 || (h.flags & kWsFirst)) {
-        // a new item (or the end): its window must have been flushed
-        if (!mbar_wait(wempty + w, ((ic / NWIN) & 1) ^ 1, abort_flag, err)) break;
-        if (ct == 0) win_info[w] = h.nst < 0 ? -1 : h.xy;
-        if (h.nst < 0) {
-          mbar_arrive(wfull + w);
-          break;
-        }
+      if (h.flags & kWsFirst) {
+        // a new item: its window must have been flushed by every thread
+        if (!mbar_wait(wdone + w, ((ic / NWIN) & 1) ^ 1, abort_flag, err)) break;
         win = reinterpret_cast<float2*>(smem + (size_t)w * L::win_bytes);
+        X0 = h.xy & 0xffff;
+        Y0 = h.xy >> 16;
         curX = -1;
         prev_pk = -1;
         prev_row = -1;
-#pragma unroll
-        for (int kk = 0; kk < R; ++kk) {
-          curY[kk] = -1;
-          Y[kk] = 0;
-#pragma unroll
-          for (int p = 0; p < P; ++p) acc[kk][p] = make_float2(0.f, 0.f);
-        }
       }
-      const int* pkv = reinterpret_cast<const int*>(sg + L::st_pk);
-      const float2* fyb = reinterpret_cast<const float2*>(sg + L::st_fy) + ry0;
-      const float2* alb = reinterpret_cast<const float2*>(sg + L::st_al) + rx * P;
-      for (int j = 0; j < h.nst; ++j) {
-        const int pk = pkv[j];
-        float2 al[P];
-        load_pols<P>(alb + j * S * P, al);
-        float2 f[R];
-#pragma unroll
-        for (int kk = 0; kk < R; ++kk) f[kk] = fyb[j * S + kk * G];
-        if (pk != prev_pk) {   // the first tap moved (the same test in every consumer thread)
+      const int* rsv = reinterpret_cast<const int*>(sg + L::st_rs);
+      const int* rpkv = reinterpret_cast<const int*>(sg + L::st_rpk);
+      const float2* fyb = reinterpret_cast<const float2*>(sg + L::st_fy);
+      const float2* fxb = reinterpret_cast<const float2*>(sg + L::st_fx);
+      const float2* wvb = reinterpret_cast<const float2*>(sg + L::st_wv);
+      for (int r = 0; r < h.nr; ++r) {
+        const int pk = rpkv[r];
+        if (pk != prev_pk) {   // the first tap moved (once per run, the same in every consumer thread)
           prev_pk = pk;
           const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
           const int row = pk & 0xff00ff00;
@@ -403,6 +417,7 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
           if (row != prev_row) {
             prev_row = row;
             const int dy = (pk >> 8) & 0xff, my = (pk >> 24) & 0xff;
+            rowoff = S - my + ry0;   // fy of row ry0 + kk G at rowoff + kk G of the doubled row
 #pragma unroll
             for (int kk = 0; kk < R; ++kk) {
               int t = ry0 + kk * G - my;
@@ -411,7 +426,7 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
             }
             row_changed = true;
           }
-          int tx = rx - mx;
+          tx = rx - mx;
           tx += (tx < 0) ? S : 0;
           const int X = dx + tx;
           if (X != curX || row_changed) {
@@ -434,17 +449,35 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
             curX = X;
           }
         }
+        const int j1 = rsv[r + 1];
+        const float2* fxp = fxb + rsv[r] * S + tx;
+        const float2* fyp = fyb + rsv[r] * 2 * S + rowoff;
+        const float2* wvp = wvb + rsv[r] * P;
+        for (int j = rsv[r]; j < j1; ++j, fxp += S, fyp += 2 * S, wvp += P) {
+          // alpha_p = conj(fx) w V_p for this thread's column
+          const float2 fx = *fxp;
+          float2 al[P];
+          load_pols<P>(wvp, al);
 #pragma unroll
-        for (int kk = 0; kk < R; ++kk) {
+          for (int p = 0; p < P; ++p) {
+            const float ar = al[p].x, ai = al[p].y;
+            al[p] = make_float2(fx.x * ar + fx.y * ai, fx.x * ai - fx.y * ar);
+          }
 #pragma unroll
-          for (int p = 0; p < P; ++p) {   // acc += conj(fy) alpha
-            acc[kk][p].x = fmaf(f[kk].x, al[p].x, fmaf(f[kk].y, al[p].y, acc[kk][p].x));
-            acc[kk][p].y = fmaf(f[kk].x, al[p].y, fmaf(-f[kk].y, al[p].x, acc[kk][p].y));
+          for (int kk = 0; kk < R; ++kk) {
+            const float2 f = fyp[kk * G];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {   // acc += conj(fy) alpha
+              acc[kk][p].x = fmaf(f.x, al[p].x, fmaf(f.y, al[p].y, acc[kk][p].x));
+              acc[kk][p].y = fmaf(f.x, al[p].y, fmaf(-f.y, al[p].x, acc[kk][p].y));
+            }
           }
         }
       }
-      mbar_arrive(empty + k % D);
+      mbar_arrive(empty + s);
       if (h.flags & kWsLast) {
+        // the item is complete: registers into the window, then this thread's own window pixels
+        // (absolute column = rx, rows = ry0 + kk G modulo S) to the grid
 #pragma unroll
         for (int kk = 0; kk < R; ++kk) {
           if (curY[kk] >= 0) {
@@ -458,7 +491,29 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
           }
           curY[kk] = -1;
         }
-        mbar_arrive(wfull + w);
+        const int xs = (rx - X0 % S + S) % S;
+        for (int X = xs; X < U; X += S) {
+#pragma unroll
+          for (int kk = 0; kk < R; ++kk) {
+            const int ys = (ry0 + kk * G - Y0 % S + S) % S;
+            for (int Yw = ys; Yw < U; Yw += S) {
+              float2 v[P];
+              bool nz = false;
+#pragma unroll
+              for (int p = 0; p < P; ++p) {
+                v[p] = win[p * UU + Yw * U + X];
+                nz |= (v[p].x != 0.f) || (v[p].y != 0.f);
+              }
+              if (nz) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) win[p * UU + Yw * U + X] = make_float2(0.f, 0.f);
+                const int gy = Y0 + Yw, gx = X0 + X;
+                if (gy < a.N && gx < a.N) flush_pixel<P>(a, ((size_t)gy * a.N + gx) * P, v);
+              }
+            }
+          }
+        }
+        mbar_arrive(wdone + w);
         ++ic;
       }
     }
@@ -470,6 +525,7 @@ __global__ void __launch_bounds__(WsGridLayout<S, P, G, TILE, ST, D, NWIN>::NT, 
 template <int S, int P, int G, int TILE, int ST, int D, int NWIN>
 struct WsDegridLayout {
   static_assert(S % G == 0 && (S * G) % 32 == 0, "row groups must divide S and fill whole warps");
+  static_assert(S % 2 == 0, "factor rows move in 16-byte units");
   static constexpr int NC = S * G / 32;
   static constexpr int NT = 32 * (NC + 2);        // + producer + reduce warp
   static constexpr int R = S / G;
@@ -481,17 +537,16 @@ struct WsDegridLayout {
   static constexpr int UB = (P == 1) ? ((U + 1) & ~1) : U;
   static constexpr unsigned box_bytes = (unsigned)U * UB * P * 8;
   static constexpr size_t win_bytes = ws_al1k(box_bytes);
-  static constexpr size_t st_pk = 16;
-  static constexpr size_t st_fy = st_pk + ws_al16(4 * ST);
-  static constexpr size_t st_fx = st_fy + (size_t)ST * S * 8;
+  static constexpr size_t st_rs = 16;
+  static constexpr size_t st_rpk = st_rs + ws_al16(4 * (ST + 1));
+  static constexpr size_t st_fy = st_rpk + ws_al16(4 * ST);   // fy rows twice over, as for gridding
+  static constexpr size_t st_fx = st_fy + (size_t)ST * 2 * S * 8;
   static constexpr size_t st_src = st_fx + (size_t)ST * S * 8;
   static constexpr size_t st_ph = st_src + ws_al16(4 * ST);
   static constexpr size_t st_red = st_ph + 8 * (size_t)ST;   // float [NB][NC][32]
   static constexpr size_t stage_bytes = ws_al16(st_red + (size_t)NB * NC * 32 * 4);
   static constexpr size_t off_stage = NWIN * win_bytes;
-  static constexpr size_t off_rec = off_stage + D * stage_bytes;   // SampleRec [2][ST]
-  static constexpr size_t off_drv = off_rec + 2 * 16 * (size_t)ST;  // long long [ST][2], int mx|my [ST]
-  static constexpr size_t off_bar = off_drv + ws_al16(16 * (size_t)ST + 4 * (size_t)ST);
+  static constexpr size_t off_bar = off_stage + D * stage_bytes;
   static constexpr size_t off_misc = off_bar + 8 * (3 * D + 2 * NWIN);
   static constexpr size_t off_soff = ws_al16(off_misc + 16);   // int64 [kSepOffCache]
   static constexpr size_t bytes = off_soff + 8 * (size_t)kSepOffCache;
@@ -537,35 +592,29 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
   if (warp == 0) {
     // ------------------------------------------------------------------------------ producer
     if (lane == 0) prefetch_tensormap(&gmap);
-    WsItemWalker walk{a.class_range[cls], a.class_range[cls + 1], cls, TILE, a.queue, a.items, ST, 0, {}, 0, 0, 0};
-    walk.init();
+    WsItemWalker walk;
+    walk.init(a.class_range[cls], a.class_range[cls + 1], cls, TILE, ST, a.queue, a.items);
     const float2* sep2 = reinterpret_cast<const float2*>(a.sep);
-    auto recs = [&](int i) { return reinterpret_cast<SampleRec*>(smem + L::off_rec) + (i & 1) * ST; };
-    auto stg = [&](int i) { return smem + L::off_stage + (size_t)(i % D) * L::stage_bytes; };
-    long long* drv_off = reinterpret_cast<long long*>(smem + L::off_drv);
-    int* drv_m = reinterpret_cast<int*>(smem + L::off_drv + 16 * (size_t)ST);
-    WsChunk dk = walk.next();
-    if (dk.valid && lane < dk.nst) cp_async(recs(0) + lane, a.rec + dk.start + lane, 16);
-    cp_async_commit();
-    WsChunk dprev{0, 0, 0, 0, false};
+    auto load_ph = [&](const WsChunk& d, const SampleRec& rc) {
+      return (a.phasor && d.valid && lane < d.nst) ? __ldg(a.phasor + rc.src) : make_float2(1.f, 0.f);
+    };
+    // loads run ahead of their use: the records three chunks, the phasors two
+    WsChunk d0 = walk.next();
+    WsChunk d1 = walk.next();
+    WsChunk d2 = walk.next();
+    SampleRec r0 = ws_load_rec(a.rec, d0, lane);
+    SampleRec r1 = ws_load_rec(a.rec, d1, lane);
+    SampleRec r2 = ws_load_rec(a.rec, d2, lane);
+    float2 ph0 = load_ph(d0, r0);
+    float2 ph1 = load_ph(d1, r1);
     int k = 0, ic = 0;
     unsigned tma_pending = 0;   // bit w: a window load whose completion nobody may have waited for
     int tma_use[NWIN];
 #pragma unroll
     for (int w = 0; w < NWIN; ++w) tma_use[w] = 0;
     bool ok = true;
-    for (;;) {
-      cp_async_wait_all();
-      __syncwarp();
-      // chunk k - 1 has landed: hand it over first, so that the consumers can finish its item
-      // while this warp waits below for a free window or stage
-      if (dprev.valid) {
-        if (lane == 0) *reinterpret_cast<WsHeader*>(stg(k - 1)) = WsHeader{dprev.nst, dprev.flags, dprev.xy, 0};
-        if (!(a.withhold && k == 1)) mbar_arrive(full + (k - 1) % D);
-      }
-      if (!dk.valid) break;
-      const WsChunk dn = walk.next();
-      if (dk.flags & kWsFirst) {
+    while (d0.valid) {
+      if (d0.flags & kWsFirst) {
         // the item's window: one TMA tile load into a free window
         const int w = ic % NWIN;
         if (!mbar_wait(wempty + w, ((ic / NWIN) & 1) ^ 1, abort_flag, err)) {
@@ -576,7 +625,7 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
           fence_proxy_async_smem();
           unsigned char* dst = smem + (size_t)w * L::win_bytes;
           mbar_arrive_expect_tx(wfull + w, L::box_bytes);
-          const int X0 = dk.xy & 0xffff, Y0 = dk.xy >> 16;
+          const int X0 = d0.xy & 0xffff, Y0 = d0.xy >> 16;
           if constexpr (P == 1) tma_load_2d(dst, &gmap, 2 * X0, Y0, wfull + w);
           else tma_load_3d(dst, &gmap, 0, X0, Y0, wfull + w);
         }
@@ -584,51 +633,49 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
         tma_use[w] = ic / NWIN;
         ++ic;
       }
-      unsigned char* sg = stg(k);
-      if (!mbar_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
+      const int s = k % D;
+      unsigned char* sg = smem + L::off_stage + (size_t)s * L::stage_bytes;
+      if (!mbar_wait(empty + s, ((k / D) & 1) ^ 1, abort_flag, err)) {
         ok = false;
         break;
       }
-      const SampleRec* rv = recs(k);
-      if (lane < dk.nst) {
-        const SampleRec rc = rv[lane];
-        const int X0 = dk.xy & 0xffff, Y0 = dk.xy >> 16;
-        const int mx = rc.p0x % S, my = rc.p0y % S;
-        const long long base = offs[a.cf_shift + rc.cf];
-        drv_off[2 * lane] = base + (long long)rc.ox * S;
-        drv_off[2 * lane + 1] = base + (long long)(a.OS + 1) * S + (long long)rc.oy * S;
-        drv_m[lane] = mx | (my << 8);
-        reinterpret_cast<int*>(sg + L::st_pk)[lane] = (rc.p0x - X0) | ((rc.p0y - Y0) << 8) | (mx << 16) | (my << 24);
-        reinterpret_cast<int*>(sg + L::st_src)[lane] = a.rank > 1 ? rc.src * a.rank + rc.cf % a.rank : rc.src;
-        float2* ph = reinterpret_cast<float2*>(sg + L::st_ph) + lane;
-        if (a.phasor) cp_async(ph, a.phasor + rc.src, 8);
-        else *ph = make_float2(1.f, 0.f);
+      const int X0 = d0.xy & 0xffff, Y0 = d0.xy >> 16;
+      const int pk = (r0.p0x - X0) | ((r0.p0y - Y0) << 8) | ((r0.p0x % S) << 16) | ((r0.p0y % S) << 24);
+      const int nr = ws_runs(pk, d0.nst, lane, reinterpret_cast<int*>(sg + L::st_rs),
+                             reinterpret_cast<int*>(sg + L::st_rpk));
+      if (lane < d0.nst) {
+        reinterpret_cast<int*>(sg + L::st_src)[lane] = a.rank > 1 ? r0.src * a.rank + r0.cf % a.rank : r0.src;
+        reinterpret_cast<float2*>(sg + L::st_ph)[lane] = ph0;
+        long long fxo, fyo;
+        ws_rows<S>(offs, a.cf_shift, a.OS, r0, fxo, fyo);
+        fence_proxy_async_smem();   // the consumers' reads of this stage come before the copies
+        bulk_load(sg + L::st_fx + (size_t)lane * S * 8, sep2 + fxo, S * 8, full + s);
+        bulk_load(sg + L::st_fy + (size_t)lane * 2 * S * 8, sep2 + fyo, S * 8, full + s);
+        bulk_load(sg + L::st_fy + (size_t)lane * 2 * S * 8 + S * 8, sep2 + fyo, S * 8, full + s);
       }
-      __syncwarp();
-      float2* fyr = reinterpret_cast<float2*>(sg + L::st_fy);
-      float2* fxr = reinterpret_cast<float2*>(sg + L::st_fx);
-      for (int i = lane; i < dk.nst * S; i += 32) {
-        const int j = i / S, t = i - j * S;
-        const int m = drv_m[j];
-        int ry = t + (m >> 8);        // fyr[j][(t + my) mod S] = fy_j[t]
-        ry -= (ry >= S) ? S : 0;
-        int rx = t + (m & 0xff);      // fxr[j][(t + mx) mod S] = fx_j[t]
-        rx -= (rx >= S) ? S : 0;
-        cp_async(fyr + j * S + ry, sep2 + drv_off[2 * j + 1] + t, 8);
-        cp_async(fxr + j * S + rx, sep2 + drv_off[2 * j] + t, 8);
+      if (lane == 0) *reinterpret_cast<WsHeader*>(sg) = WsHeader{d0.nst, d0.flags, d0.xy, nr};
+      if (!(a.withhold && k == 0)) {
+        if (lane == 0) mbar_arrive_expect_tx(full + s, (unsigned)(d0.nst * 3 * S * 8));
+        else mbar_arrive(full + s);
       }
-      if (dn.valid && lane < dn.nst) cp_async(recs(k + 1) + lane, a.rec + dn.start + lane, 16);
-      cp_async_commit();
-      __syncwarp();   // every lane has read drv_* before the next pass rewrites them
-      dprev = dk;
-      dk = dn;
+      const WsChunk d3 = walk.next();
+      const SampleRec r3 = ws_load_rec(a.rec, d3, lane);
+      const float2 ph2 = load_ph(d2, r2);
+      d0 = d1;
+      d1 = d2;
+      d2 = d3;
+      r0 = r1;
+      r1 = r2;
+      r2 = r3;
+      ph0 = ph1;
+      ph1 = ph2;
       ++k;
     }
     if (ok && mbar_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
-      if (lane == 0) *reinterpret_cast<WsHeader*>(stg(k)) = WsHeader{-1, 0, 0, 0};
+      if (lane == 0) *reinterpret_cast<WsHeader*>(smem + L::off_stage + (size_t)(k % D) * L::stage_bytes) =
+          WsHeader{-1, 0, 0, 0};
       mbar_arrive(full + k % D);
     }
-    cp_async_wait_all();
     if (!ok || *abort_flag) {
       // no consumer may wait for an issued window load any more: wait for it here (bounded)
       // before the CTA can exit
@@ -671,9 +718,14 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
     ws_owner<S, G>(ct, rx, ry0);
     float2 gc[R][P];
     int curY[R], Y[R];
-    int curX = -1, prev_pk = -1, prev_row = -1;
+    int curX = -1, tx = 0, rowoff = 0, prev_pk = -1, prev_row = -1;
     const float2* win = reinterpret_cast<const float2*>(smem);
     int ic = 0;
+#pragma unroll
+    for (int kk = 0; kk < R; ++kk) {
+      curY[kk] = -1;
+      Y[kk] = 0;
+    }
     for (int k = 0;; ++k) {
       unsigned char* sg = smem + L::off_stage + (size_t)(k % D) * L::stage_bytes;
       if (!mbar_wait(full + k % D, (k / D) & 1, abort_flag, err)) break;
@@ -690,15 +742,14 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
         prev_pk = -1;
         prev_row = -1;
 #pragma unroll
-        for (int kk = 0; kk < R; ++kk) {
-          curY[kk] = -1;
-          Y[kk] = 0;
-        }
+        for (int kk = 0; kk < R; ++kk) curY[kk] = -1;
       }
-      const int* pkv = reinterpret_cast<const int*>(sg + L::st_pk);
-      const float2* fyb = reinterpret_cast<const float2*>(sg + L::st_fy) + ry0;
-      const float2* fxb = reinterpret_cast<const float2*>(sg + L::st_fx) + rx;
+      const int* rsv = reinterpret_cast<const int*>(sg + L::st_rs);
+      const int* rpkv = reinterpret_cast<const int*>(sg + L::st_rpk);
+      const float2* fyb = reinterpret_cast<const float2*>(sg + L::st_fy);
+      const float2* fxb = reinterpret_cast<const float2*>(sg + L::st_fx);
       float* red = reinterpret_cast<float*>(sg + L::st_red);
+      int r = 0, next_run = 0;   // the next run starts at sample next_run
       for (int j0 = 0; j0 < h.nst; j0 += B) {
         float vals[2 * P * B];
 #pragma unroll
@@ -707,51 +758,55 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
         for (int b = 0; b < B; ++b) {
           const int j = j0 + b;
           if (j < h.nst) {
-            const int pk = pkv[j];
-            const float2 fx = fxb[j * S];
-            float2 f[R];
+            if (j == next_run) {
+              const int pk = rpkv[r];
+              ++r;
+              next_run = r < h.nr ? rsv[r] : h.nst;
+              if (pk != prev_pk) {
+                prev_pk = pk;
+                const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
+                const int row = pk & 0xff00ff00;
+                bool row_changed = false;
+                if (row != prev_row) {
+                  prev_row = row;
+                  const int dy = (pk >> 8) & 0xff, my = (pk >> 24) & 0xff;
+                  rowoff = S - my + ry0;
 #pragma unroll
-            for (int kk = 0; kk < R; ++kk) f[kk] = fyb[j * S + kk * G];
-            if (pk != prev_pk) {
-              prev_pk = pk;
-              const int dx = pk & 0xff, mx = (pk >> 16) & 0xff;
-              const int row = pk & 0xff00ff00;
-              bool row_changed = false;
-              if (row != prev_row) {
-                prev_row = row;
-                const int dy = (pk >> 8) & 0xff, my = (pk >> 24) & 0xff;
-#pragma unroll
-                for (int kk = 0; kk < R; ++kk) {
-                  int t = ry0 + kk * G - my;
-                  t += (t < 0) ? S : 0;
-                  Y[kk] = dy + t;
-                }
-                row_changed = true;
-              }
-              int tx = rx - mx;
-              tx += (tx < 0) ? S : 0;
-              const int X = dx + tx;
-              if (X != curX || row_changed) {
-                const bool xchg = X != curX;
-#pragma unroll
-                for (int kk = 0; kk < R; ++kk) {
-                  if (xchg || Y[kk] != curY[kk]) {
-                    curY[kk] = Y[kk];
-                    load_pols<P>(win + ((size_t)curY[kk] * UB + X) * P, gc[kk]);
+                  for (int kk = 0; kk < R; ++kk) {
+                    int t = ry0 + kk * G - my;
+                    t += (t < 0) ? S : 0;
+                    Y[kk] = dy + t;
                   }
+                  row_changed = true;
                 }
-                curX = X;
+                tx = rx - mx;
+                tx += (tx < 0) ? S : 0;
+                const int X = dx + tx;
+                if (X != curX || row_changed) {
+                  const bool xchg = X != curX;
+#pragma unroll
+                  for (int kk = 0; kk < R; ++kk) {
+                    if (xchg || Y[kk] != curY[kk]) {
+                      curY[kk] = Y[kk];
+                      load_pols<P>(win + ((size_t)curY[kk] * UB + X) * P, gc[kk]);
+                    }
+                  }
+                  curX = X;
+                }
               }
             }
+            const float2 fx = fxb[j * S + tx];
+            const float2* fyp = fyb + j * 2 * S + rowoff;
             float2 part[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) part[p] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int kk = 0; kk < R; ++kk) {
+              const float2 f = fyp[kk * G];
 #pragma unroll
               for (int p = 0; p < P; ++p) {
-                part[p].x = fmaf(f[kk].x, gc[kk][p].x, fmaf(-f[kk].y, gc[kk][p].y, part[p].x));
-                part[p].y = fmaf(f[kk].x, gc[kk][p].y, fmaf(f[kk].y, gc[kk][p].x, part[p].y));
+                part[p].x = fmaf(f.x, gc[kk][p].x, fmaf(-f.y, gc[kk][p].y, part[p].x));
+                part[p].y = fmaf(f.x, gc[kk][p].y, fmaf(f.y, gc[kk][p].x, part[p].y));
               }
             }
 #pragma unroll
@@ -792,31 +847,31 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
 // cannot take (strided-pol element passes, which the TMA window cannot describe; misaligned
 // buffers; grids above 32768 pixels).
 struct WsCfg {
-  int S, g_grid, g_degrid, st_grid, st_degrid, d, nwin_grid, nwin_degrid, minb_grid, minb_degrid;
+  int S, g_grid, g_degrid, st_grid, st_degrid, d_grid, d_degrid, nwin_grid, nwin_degrid, minb_grid, minb_degrid;
 };
 constexpr WsCfg kWsCfg[8] = {
-    {8, 8, 8, 16, 16, 4, 2, 2, 4, 4},
-    {16, 8, 8, 16, 16, 4, 2, 2, 2, 2},
-    {24, 8, 8, 16, 16, 3, 1, 2, 2, 2},
-    {32, 8, 8, 16, 16, 3, 1, 2, 2, 1},
-    {40, 8, 8, 12, 16, 3, 2, 2, 1, 1},
-    {48, 8, 8, 8, 8, 3, 1, 2, 1, 1},
-    {56, 8, 8, 8, 8, 3, 1, 1, 1, 1},
-    {64, 8, 8, 4, 8, 3, 1, 1, 1, 1},
+    {8, 8, 8, 16, 16, 4, 4, 2, 2, 4, 4},
+    {16, 8, 8, 16, 16, 4, 4, 2, 2, 2, 2},
+    {24, 8, 8, 16, 16, 3, 3, 2, 2, 2, 2},
+    {32, 8, 8, 16, 16, 3, 3, 1, 2, 2, 1},
+    {40, 8, 8, 12, 16, 4, 3, 2, 2, 1, 1},
+    {48, 8, 8, 8, 8, 3, 3, 1, 1, 1, 1},
+    {56, 8, 8, 8, 8, 3, 3, 1, 1, 1, 1},
+    {64, 8, 8, 4, 8, 3, 3, 1, 1, 1, 1},
 };
 constexpr WsCfg ws_cfg(int S) {
   for (const WsCfg& e : kWsCfg)
     if (e.S == S) return e;
-  return WsCfg{S, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  return WsCfg{S, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 }
 
 template <int S, int P>
 awg_status run_grid_ws(const GridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr WsCfg c = ws_cfg(S);
   constexpr int T = exact_cfg(S, 2).tile;
-  using L = WsGridLayout<S, P, c.g_grid, T, c.st_grid, c.d, c.nwin_grid>;
+  using L = WsGridLayout<S, P, c.g_grid, T, c.st_grid, c.d_grid, c.nwin_grid>;
   static_assert(L::alloc <= 227 * 1024, "gridding stages do not fit");
-  auto kern = k_grid_ws<S, P, c.g_grid, T, c.st_grid, c.d, c.nwin_grid, c.minb_grid>;
+  auto kern = k_grid_ws<S, P, c.g_grid, T, c.st_grid, c.d_grid, c.nwin_grid, c.minb_grid>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::alloc));
@@ -836,9 +891,9 @@ template <int S, int P>
 awg_status run_degrid_ws(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr WsCfg c = ws_cfg(S);
   constexpr int T = exact_cfg(S, 2).tile;
-  using L = WsDegridLayout<S, P, c.g_degrid, T, c.st_degrid, c.d, c.nwin_degrid>;
+  using L = WsDegridLayout<S, P, c.g_degrid, T, c.st_degrid, c.d_degrid, c.nwin_degrid>;
   static_assert(L::alloc <= 227 * 1024, "degridding stages do not fit");
-  auto kern = k_degrid_ws<S, P, c.g_degrid, T, c.st_degrid, c.d, c.nwin_degrid, c.minb_degrid>;
+  auto kern = k_degrid_ws<S, P, c.g_degrid, T, c.st_degrid, c.d_degrid, c.nwin_degrid, c.minb_degrid>;
   static int bps = 0;
   if (bps == 0) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::alloc));

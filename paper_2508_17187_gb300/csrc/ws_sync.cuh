@@ -1,7 +1,7 @@
 // Synchronisation and bulk-copy primitives of the warp-specialised kernels (sm_103a, inline PTX):
-// shared-memory mbarriers with bounded waits, the tensor-memory-access (TMA) tile load of a grid
-// window, and the cross-proxy fence that orders generic shared-memory accesses before an
-// asynchronous (TMA) write to the same memory.
+// shared-memory mbarriers with bounded waits, the tensor-memory-access (TMA) copies (the tile load
+// of a grid window, contiguous bulk loads of factor rows), and the cross-proxy fence that orders
+// generic shared-memory accesses before an asynchronous (TMA) write to the same memory.
 //
 // Every wait is bounded.  A thread whose wait does not complete within kWaitLimitNs of %globaltimer
 // (or that finds the CTA's abort flag raised) gives up: it raises the abort flag of its CTA, sets
@@ -51,14 +51,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
       : "memory");
 }
 
+// One bounded test of the phase: the thread may be suspended until the phase completes, for at
+// most about kTryWaitHintNs, so that a waiting warp does not spin on the issue slots.
+constexpr unsigned kTryWaitHintNs = 1000000u;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kTryWaitHintNs)
       : "memory");
   return ok != 0;
 }
@@ -77,7 +81,7 @@ static __device__ __noinline__ bool mbar_wait(uint64_t* bar, unsigned parity, vo
   const unsigned long long t0 = global_ns();
   for (unsigned i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 15) == 0) {
+    if ((i & 3) == 0) {
       if (*abort_flag) return false;
       if (global_ns() - t0 > kWaitLimitNs) {
         *abort_flag = 1;
@@ -111,6 +115,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
+}
+
+// One contiguous copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
+// this CTA's shared memory, completing its bytes on the barrier's transaction count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
