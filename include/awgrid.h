@@ -150,20 +150,25 @@ awg_status cf_set_fused_terms(awg_cf_set cf, int32_t* terms);
 
 /*
  * Per-support autotuner of the separable kernels (a project addition; the paper fixes no kernel
- * shapes).  Every support of the W-projection schedule (8, 16, ..., 64) has three compiled kernel
+ * shapes).  Every support of the W-projection schedule (8, 16, ..., 64) has four compiled kernel
  * configurations: 0 and 1 differ in the tile of first-tap positions per work item, threads per
  * CTA and samples staged per chunk; 2 is the warp-specialised pair (a producer warp stages chunks
  * into a ring of shared-memory stages handed over on mbarriers, consumer warps only multiply and
  * add, a flush warp (gridding) or reduce warp (degridding) finishes each item, and degridding
- * loads each item's grid window with one TMA tile copy).  For each configuration this builds a plan of the given geometry (uvw_m, freq_hz,
+ * loads each item's grid window with one TMA tile copy); 3 grids on the tensor cores (tcgen05,
+ * 3xTF32 products, FP32 accumulation in tensor memory: a window is the product of the item's
+ * x-factor rows times w V and its y-factor rows, relative RMS error a few 1e-6 against the FP64
+ * result) with tiles of odd side so that a window fills the MMA shape, and degrids with the
+ * warp-specialised kernel on those tiles.  For each configuration this builds a plan of the given
+ * geometry (uvw_m, freq_hz,
  * pa_bin, chan_subband: device arrays as for plan_create, typically the data to be imaged or a
  * slice of it), grids and degrids unit visibilities with n_pol pols once, then times every
  * support's gridding and degridding launch three times (CUDA events on `stream`), and keeps the
  * fastest configuration per support in the CF set.  Plans created before the call are invalid
  * afterwards (their calls return INVALID_ARG); create plans after tuning.  Blocking.  Allocates
  * scratch of about (R C n_pol) 20 B plus one grid and two plans, and frees it before returning.
- * choice_out: host int32 [65] or NULL, the chosen configuration (0, 1 or 2) per support, -1 where
- * none was timed; ms_out: host float [3][65] or NULL, grid + degrid milliseconds of each
+ * choice_out: host int32 [65] or NULL, the chosen configuration (0, 1, 2 or 3) per support, -1
+ * where none was timed; ms_out: host float [4][65] or NULL, grid + degrid milliseconds of each
  * configuration per support (0 where not timed).  Full-table CF sets have nothing to tune
  * (choices -1).  Errors: INVALID_ARG, OOM, CUDA.
  */
@@ -171,7 +176,7 @@ awg_status cf_set_autotune(awg_cf_set cf, const double* uvw_m, int64_t n_rows, c
                            const int32_t* pa_bin, const int32_t* chan_subband, int32_t n_pol, void* stream,
                            int32_t* choice_out, float* ms_out);
 
-/* Select configuration `config` (0, 1 or 2) of the separable kernels for one support of the
+/* Select configuration `config` (0, 1, 2 or 3) of the separable kernels for one support of the
  * W-projection schedule by hand (what cf_set_autotune does by timing); plans created before the
  * call are invalid afterwards.  Errors: INVALID_ARG (no configurations for that support). */
 awg_status cf_set_choose(awg_cf_set cf, int32_t support, int32_t config);
@@ -282,7 +287,7 @@ awg_status plan_copy_index(awg_plan plan, int32_t* kept, int32_t* cf_out, int32_
 
 /*
  * Completion check of the plan's gridding and degridding launches (synchronises the plan's last
- * stream).  The warp-specialised kernels (configuration 2 of cf_set_autotune / cf_set_choose) hand
+ * stream).  The warp-specialised kernels (configurations 2 and 3 of cf_set_autotune / cf_set_choose) hand
  * work between their warps on shared-memory barriers whose waits are bounded (2 s); a wait that
  * gives up ends its launch early and records it in the plan.  Returns AWG_ERR_TIMEOUT (and clears
  * the record) when a launch since the last plan_create / plan_update / plan_check did so - its
@@ -453,7 +458,7 @@ int64_t awg_debug_live_allocations(void);
 /*
  * Failure injection for tests of the bounded waits (no device fault, trap or endless wait): after
  * awg_debug_ws_withhold(1) the next grid_visibilities or degrid_visibilities call withholds,
- * in every CTA of its warp-specialised launches (configuration 2), the hand-over of the first
+ * in every CTA of its warp-specialised launches (configurations 2 and 3), the hand-over of the first
  * chunk from the producer warp to the consumer warps.  Their bounded waits give up after 2 s, the
  * launch ends early with incomplete results, and plan_check reports AWG_ERR_TIMEOUT; the CUDA
  * context stays usable.  awg_debug_ws_withhold(0) disarms it.  Errors: INVALID_ARG.

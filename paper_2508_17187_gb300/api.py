@@ -85,7 +85,7 @@ class CFSet:
                  chan_subband: Optional[torch.Tensor] = None, n_pol: int = 4, stream=None):
         """Pick the faster compiled kernel configuration per support by timing both on a plan of
         this geometry (see cf_set_autotune in awgrid.h); plans made earlier become invalid.
-        Returns ({support: choice}, {support: (ms of configurations 0, 1 and 2)})."""
+        Returns ({support: choice}, {support: (ms of configurations 0, 1, 2 and 3)})."""
         _need(uvw_m, "uvw_m", torch.float64)
         _need(freq_hz, "freq_hz", torch.float64)
         if pa_bin is not None:
@@ -93,13 +93,13 @@ class CFSet:
         if chan_subband is not None:
             _need(chan_subband, "chan_subband", torch.int32, (freq_hz.shape[0],))
         choice = np.zeros(65, dtype=np.int32)
-        ms = np.zeros((3, 65), dtype=np.float32)
+        ms = np.zeros((4, 65), dtype=np.float32)
         check(_lib.load().cf_set_autotune(self.handle, _ptr(uvw_m), uvw_m.shape[0], _ptr(freq_hz), freq_hz.shape[0],
                                           _ptr(pa_bin), _ptr(chan_subband), int(n_pol), _stream_ptr(stream),
                                           choice.ctypes.data_as(ctypes.c_void_p), ms.ctypes.data_as(ctypes.c_void_p)),
               "cf_set_autotune")
         picked = {S: int(choice[S]) for S in range(65) if choice[S] >= 0}
-        return picked, {S: tuple(float(ms[c, S]) for c in range(3)) for S in picked}
+        return picked, {S: tuple(float(ms[c, S]) for c in range(4)) for S in picked}
 
     def mueller(self):
         """[(p, q), ...] Mueller elements of a full-polarisation set (empty otherwise)."""
@@ -111,7 +111,7 @@ class CFSet:
         return [(int(ep[i]), int(eq[i])) for i in range(n.value)]
 
     def choose(self, support: int, config: int):
-        """Select kernel configuration 0, 1 or 2 for one support by hand (see cf_set_choose)."""
+        """Select kernel configuration 0, 1, 2 or 3 for one support by hand (see cf_set_choose)."""
         check(_lib.load().cf_set_choose(self.handle, int(support), int(config)), "cf_set_choose")
 
     def supports(self) -> np.ndarray:

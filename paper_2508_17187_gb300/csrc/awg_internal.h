@@ -48,12 +48,13 @@ __host__ __device__ constexpr int class_of_support(int S) {
 // barriers of a chunk (and the unequal flush work between warps) over more samples, which won
 // where two CTAs still fit (candidate 1 of supports 24-56: 1-3% on the W-projection workload).
 // Every support has kNumCand compiled candidates; candidate 0 is the default and cf_set_autotune
-// picks per support by timing.  Candidate 2 is the warp-specialised pair of kernels.  The supports
-// listed here and AWG_FOR_EXACT_AND_POLS must agree.
+// picks per support by timing.  Candidate 2 is the warp-specialised pair of kernels, candidate 3
+// tensor-core gridding with warp-specialised degridding.  The supports listed here and
+// AWG_FOR_EXACT_AND_POLS must agree.
 struct ExactCfg {
   int S, g_grid, g_degrid, tile, stage;
 };
-constexpr int kNumCand = 3;
+constexpr int kNumCand = 4;
 constexpr ExactCfg kExactCand[kNumCand][8] = {
     {
         {8, 8, 8, 32, 16},
@@ -86,6 +87,19 @@ constexpr ExactCfg kExactCand[kNumCand][8] = {
         {48, 8, 8, 8, 16},
         {56, 8, 8, 8, 16},
         {64, 8, 8, 8, 4},
+    },
+    {
+        // candidate 3: gridding on the tensor cores (resample_mma.cuh), degridding by the
+        // warp-specialised kernel, with these tiles (window side S + tile - 1 at or just below a
+        // multiple of 16); the cp.async kernels compiled with the same tiles serve the rest
+        {8, 8, 8, 9, 8},
+        {16, 8, 8, 17, 8},
+        {24, 8, 8, 9, 8},
+        {32, 8, 8, 17, 8},
+        {40, 8, 8, 9, 8},
+        {48, 8, 8, 17, 8},
+        {56, 8, 8, 9, 8},
+        {64, 8, 8, 9, 4},
     },
 };
 constexpr ExactCfg exact_cfg(int S, int cand = 0) {

@@ -622,7 +622,7 @@ awg_status cf_set_choose(awg_cf_set h, int32_t support, int32_t config) {
   CfSetImpl* cf = (CfSetImpl*)h;
   if (support < 1 || support > kMaxSupport || !has_exact(support))
     return set_error(AWG_ERR_INVALID_ARG, "support " + std::to_string(support) + " has no kernel configurations");
-  if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0, 1 or 2");
+  if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0, 1, 2 or 3");
   if (cf->fused && config != 0) return set_error(AWG_ERR_UNSUPPORTED, "fused kernels have one configuration");
   cf->cand[support] = (int8_t)config;
   fill_slots(cf);

@@ -6,7 +6,7 @@
 #include <atomic>
 #include <mutex>
 
-#include "resample_ws.cuh"
+#include "resample_mma.cuh"
 
 namespace awg {
 
@@ -22,6 +22,12 @@ AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 1)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 1)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 2)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 2)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 3)
+AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 3)
+AWG_FOR_WS_A(AWG_DECLARE_GRID_MMA)
+AWG_FOR_WS_B(AWG_DECLARE_GRID_MMA)
+AWG_FOR_WS_A(AWG_DECLARE_DEGRID_WS3)
+AWG_FOR_WS_B(AWG_DECLARE_DEGRID_WS3)
 AWG_FOR_WS_A(AWG_DECLARE_GRID_WS)
 AWG_FOR_WS_B(AWG_DECLARE_GRID_WS)
 AWG_FOR_WS_A(AWG_DECLARE_DEGRID_WS)
@@ -85,11 +91,19 @@ awg_status grid_slot_sep(int S, int cand, int slot, int P, const GridArgs& a, in
       AWG_FOR_WS_B(AWG_CASE)
 #undef AWG_CASE
     }
+    if (cand == 3 && ws_grid_ok(a, P)) {
+#define AWG_CASE(SS, PP) \
+  if (S == SS && P == PP) return run_grid_mma<SS, PP>(a, slot, sms, st);
+      AWG_FOR_WS_A(AWG_CASE)
+      AWG_FOR_WS_B(AWG_CASE)
+#undef AWG_CASE
+    }
 #define AWG_CASE(SS, PP, CC) \
   if (S == SS && P == PP && cand == CC) return run_grid_exact<SS, PP, CC>(a, slot, sms, st);
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 0)
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 1)
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 2)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 3)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
   }
@@ -150,11 +164,19 @@ awg_status degrid_slot_sep(int S, int cand, int slot, int P, const DegridArgs& a
       AWG_FOR_WS_B(AWG_CASE)
 #undef AWG_CASE
     }
+    if (cand == 3 && ws_degrid_ok(a, P)) {
+#define AWG_CASE(SS, PP) \
+  if (S == SS && P == PP) return run_degrid_ws<SS, PP, 3>(a, slot, sms, st);
+      AWG_FOR_WS_A(AWG_CASE)
+      AWG_FOR_WS_B(AWG_CASE)
+#undef AWG_CASE
+    }
 #define AWG_CASE(SS, PP, CC) \
   if (S == SS && P == PP && cand == CC) return run_degrid_exact<SS, PP, CC>(a, slot, sms, st);
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 0)
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 1)
     AWG_FOR_EXACT_AND_POLS(AWG_CASE, 2)
+    AWG_FOR_EXACT_AND_POLS(AWG_CASE, 3)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no exact-support kernel for this support / pol count");
   }

@@ -1,0 +1,521 @@
+// Gridding on the tensor cores (tcgen05, sm_103a) for separable rank-1 CF records on the exact
+// supports: configuration 3 of cf_set_autotune / cf_set_choose.
+//
+// With separable CFs the gridding of one work item is a dense product.  Sample j of the item adds
+// Y_j(y) X_j(x, p) to window pixel (x, y) of pol p, with Y_j(y) = conj(fy_j[y - dy_j]) and
+// X_j(x, p) = conj(fx_j[x - dx_j]) w_jp V_jp (zero outside the sample's S x S footprint), so the
+// window is W = sum_j X_j Y_j^T, a GEMM over the samples.  In real arithmetic, with row
+// m = (x, p, c) (c: real / imaginary part), column n = y and k = (j, c'):
+//   A[(x,p,0)][(j,0)] = Re X, A[(x,p,0)][(j,1)] = Im X, A[(x,p,1)][(j,0)] = Im X, A[(x,p,1)][(j,1)] = -Re X,
+//   B[y][(j,0)] = Re fy, B[y][(j,1)] = Im fy (= -Im Y),
+// D = A B^T holds Re W in rows c = 0 and Im W in rows c = 1.  The window is padded to UX x UN
+// pixels (UX: a multiple of 128 / 2P so that the rows fill 128-row MMA tiles; UN: a multiple of
+// 16); the padding is zero work that the tensor cores do anyway.
+//
+// Precision: the operands are FP32 values split into a TF32 head and a TF32 remainder (both
+// rounded to nearest); each k-step runs A_lo B_hi + A_hi B_lo + A_hi B_hi (the 3xTF32 scheme),
+// which keeps the relative error of a product near 2^-22 (the dropped A_lo B_lo term and the
+// remainders' rounding).  The sum over an item's samples runs in the FP32 accumulator of the
+// tensor memory, one accumulation per MMA (3 K/8 per chunk): over an item of 1024 samples that
+// is about 770 additions, whose rounding puts the relative RMS error of a window near
+// sqrt(770) 2^-23, a few 1e-6, whatever the flush mode.
+//
+// Roles (one persistent CTA per SM):
+//  * warp 0, the producer, stages chunks of J samples (records, factor rows by TMA bulk copies,
+//    w V times the phasor) into a ring of stages, as in the warp-specialised kernels;
+//  * the builder warps turn a stage into the A and B operands of the chunk (hi and lo parts) in the
+//    canonical no-swizzle K-major layout of the tensor cores, in one of two operand buffers;
+//  * warp 1 owns the tensor memory; its lane 0 issues the MMAs of each chunk into the item's
+//    accumulator (two accumulators, so that one item's flush overlaps the next item's MMAs) and
+//    commits them to the barriers that free the operand buffer and, at the end of an item, hand
+//    the accumulator to the epilogue;
+//  * four epilogue warps (one per tensor-memory lane quarter) read the accumulator and add it to the
+//    grid (the flush modes of grid_visibilities: plain, compensated, FP64).
+// Every hand-off is an mbarrier phase with a bounded wait (ws_sync.cuh); tensor memory is released
+// on every path before the CTA exits.
+#pragma once
+
+#include "resample_ws.cuh"
+
+namespace awg {
+
+// ------------------------------------------------------------------------- tcgen05 primitives
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling: core matrices of 8 rows
+// x 16 bytes; lbo = byte distance between core matrices adjacent in K, sbo = between adjacent
+// groups of 8 rows.
+__device__ __forceinline__ uint64_t umma_sdesc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of this architecture family
+  return d;                 // base offset 0, absolute LBO, layout 0: no swizzle
+}
+
+// Instruction descriptor of kind::tf32 with FP32 accumulation, both operands K-major.
+__host__ __device__ constexpr unsigned umma_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(unsigned d_tmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Arrive on `bar` once the tensor-core operations this thread issued so far have completed.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes (lane quarter warp % 4).  The
+// load is a warp-collective (.sync.aligned) instruction: the warp is reconverged first.
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  __syncwarp();
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// TF32 head of x and of the remainder x - head, both rounded to nearest (the tensor cores would
+// otherwise truncate the remainder's low 13 bits).
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  unsigned h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+  lo = __uint_as_float(l);
+}
+
+// ------------------------------------------------------------------------------------- layout
+
+template <int S, int P, int TILE, int J, int D>
+struct MmaGridLayout {
+  static_assert(S % 2 == 0 && J % 4 == 0, "factor rows move in 16-byte units; K steps take 4 samples");
+  static constexpr int U = TILE + S - 1;                              // window side
+  static constexpr int XQ = 128 / (2 * P);                            // pixels per 128-row tile
+  static constexpr int UX = (U + XQ - 1) / XQ * XQ;                   // padded columns (x)
+  static constexpr int UN = (U + 15) / 16 * 16;                       // padded rows (y): MMA N
+  static constexpr int M = UX * P * 2;                                // A rows
+  static constexpr int MT = M / 128;                                  // 128-row tiles
+  static constexpr int K = 2 * J;                                     // per chunk
+  static constexpr int KS = K / 8;                                    // MMA k-steps per chunk
+  static constexpr int NACC = (2 * MT * UN <= 512) ? 2 : 1;           // accumulators in tensor memory
+  static constexpr int TCOLS0 = NACC * MT * UN;
+  static constexpr int TCOLS = TCOLS0 <= 32 ? 32 : TCOLS0 <= 64 ? 64 : TCOLS0 <= 128 ? 128 : TCOLS0 <= 256 ? 256 : 512;
+  static_assert(TCOLS0 <= 512, "the accumulator does not fit in tensor memory");
+  static_assert(UN <= 256, "MMA N is at most 256");
+  // canonical K-major layout: LBO = 128 bytes (adjacent core matrices in K), SBO = (K / 4) * 128
+  static constexpr unsigned LBO = 128, SBO = (K / 4) * 128;
+  static constexpr size_t a_bytes = (size_t)M * K * 4;
+  static constexpr size_t b_bytes = (size_t)UN * K * 4;
+  // operand buffer: A_hi, A_lo, B_hi, B_lo, then a small header (flags, window origin)
+  static constexpr size_t ob_ahi = 0, ob_alo = a_bytes, ob_bhi = 2 * a_bytes, ob_blo = 2 * a_bytes + b_bytes;
+  static constexpr size_t ob_hdr = 2 * a_bytes + 2 * b_bytes;
+  static constexpr size_t ob_bytes = ws_al1k(ob_hdr + 16);
+  // raw stage (producer -> builders)
+  static constexpr size_t st_pk = 16;
+  static constexpr size_t st_fy = st_pk + ws_al16(4 * J);
+  static constexpr size_t st_fx = st_fy + (size_t)J * S * 8;
+  static constexpr size_t st_wv = st_fx + (size_t)J * S * 8;
+  static constexpr size_t stage_bytes = ws_al16(st_wv + (size_t)J * P * 8);
+  static constexpr int NB_WARPS = 8;                                  // builders
+  static constexpr int NT = 32 * (2 + 4 + NB_WARPS);                  // producer, MMA, epilogue, builders
+  static constexpr size_t off_ob = 0;
+  static constexpr size_t off_stage = 2 * ob_bytes;
+  static constexpr size_t off_bar = off_stage + D * stage_bytes;
+  // barriers: full[D], empty[D], ofull[2], oempty[2], afull[NACC], aempty[NACC], fin
+  static constexpr size_t off_misc = off_bar + 8 * (2 * D + 4 + 2 * NACC + 1);
+  static constexpr size_t off_soff = ws_al16(off_misc + 32 + 4 * NACC);
+  static constexpr size_t bytes = off_soff + 8 * (size_t)kSepOffCache;
+  // at least 116 KB so that one CTA holds an SM (and its tensor memory) alone
+  static constexpr size_t alloc = (bytes + 1024 > 116 * 1024 ? bytes + 1024 : 116 * 1024);
+};
+
+template <int S, int P, int TILE, int J, int D>
+__global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
+    k_grid_mma(const GridArgs a, const int cls) {
+  using L = MmaGridLayout<S, P, TILE, J, D>;
+  constexpr int MT = L::MT, KS = L::KS, UN = L::UN, NACC = L::NACC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  int64_t* s_off = reinterpret_cast<int64_t*>(smem + L::off_soff);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);
+  uint64_t* empty = full + D;
+  uint64_t* ofull = full + 2 * D;
+  uint64_t* oempty = ofull + 2;
+  uint64_t* afull = oempty + 2;
+  uint64_t* aempty = afull + NACC;
+  uint64_t* fin = aempty + NACC;   // completion of every MMA issued, before the tensor memory is freed
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::off_misc);
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + L::off_misc + 16);
+  int* acc_xy = reinterpret_cast<int*>(smem + L::off_misc + 32);   // [NACC] window origin of each accumulator
+  unsigned long long* err = a.err;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  const bool off_cached = a.n_sep_off <= kSepOffCache;
+  if (off_cached)
+    for (int i = tid; i < a.n_sep_off; i += L::NT) s_off[i] = a.sep_off[i];
+  const int64_t* offs = off_cached ? s_off : a.sep_off;
+  if (tid == 0) {
+    for (int d = 0; d < D; ++d) {
+      mbar_init(full + d, 32);
+      mbar_init(empty + d, 32 * L::NB_WARPS);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(ofull + b, 32 * L::NB_WARPS);
+      mbar_init(oempty + b, 1);
+    }
+    for (int b = 0; b < NACC; ++b) {
+      mbar_init(afull + b, 2);   // the MMA thread's arrival (window origin written) + the commit
+      mbar_init(aempty + b, 128);
+    }
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((unsigned)L::TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------------------ producer
+    double wsum[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) wsum[p] = 0.0;
+    WsItemWalker walk;
+    walk.init(a.class_range[cls], a.class_range[cls + 1], cls, TILE, J, a.queue, a.items);
+    const float2* sep2 = reinterpret_cast<const float2*>(a.sep);
+    WsChunk d0 = walk.next();
+    WsChunk d1 = walk.next();
+    WsChunk d2 = walk.next();
+    SampleRec r0 = ws_load_rec(a.rec, d0, lane);
+    SampleRec r1 = ws_load_rec(a.rec, d1, lane);
+    SampleRec r2 = ws_load_rec(a.rec, d2, lane);
+    WsVis<P> x0 = ws_load_vis<P>(a, d0, r0, lane);
+    WsVis<P> x1 = ws_load_vis<P>(a, d1, r1, lane);
+    int k = 0;
+    bool ok = true;
+    while (d0.valid) {
+      const int s = k % D;
+      unsigned char* sg = smem + L::off_stage + (size_t)s * L::stage_bytes;
+      if (!mbar_wait(empty + s, ((k / D) & 1) ^ 1, abort_flag, err)) {
+        ok = false;
+        break;
+      }
+      if (lane < d0.nst) {
+        const int X0 = d0.xy & 0xffff, Y0 = d0.xy >> 16;
+        reinterpret_cast<int*>(sg + L::st_pk)[lane] = (r0.p0x - X0) | ((r0.p0y - Y0) << 8);
+        long long fxo, fyo;
+        ws_rows<S>(offs, a.cf_shift, a.OS, r0, fxo, fyo);
+        fence_proxy_async_smem();
+        bulk_load(sg + L::st_fx + (size_t)lane * S * 8, sep2 + fxo, S * 8, full + s);
+        bulk_load(sg + L::st_fy + (size_t)lane * S * 8, sep2 + fyo, S * 8, full + s);
+        float2* dst = reinterpret_cast<float2*>(sg + L::st_wv) + lane * P;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const float xr = x0.w[p] * x0.v[p].x, xi = x0.w[p] * x0.v[p].y;
+          dst[p] = make_float2(xr * x0.ph.x - xi * x0.ph.y, xr * x0.ph.y + xi * x0.ph.x);
+        }
+        if (a.rank == 1 || r0.cf % a.rank == 0) {
+#pragma unroll
+          for (int p = 0; p < P; ++p) wsum[p] += (double)x0.w[p];
+        }
+      }
+      if (lane == 0) *reinterpret_cast<WsHeader*>(sg) = WsHeader{d0.nst, d0.flags, d0.xy, 0};
+      if (!(a.withhold && k == 0)) {
+        if (lane == 0) mbar_arrive_expect_tx(full + s, (unsigned)(d0.nst * 2 * S * 8));
+        else mbar_arrive(full + s);
+      }
+      const WsChunk d3 = walk.next();
+      const SampleRec r3 = ws_load_rec(a.rec, d3, lane);
+      const WsVis<P> x2 = ws_load_vis<P>(a, d2, r2, lane);
+      d0 = d1;
+      d1 = d2;
+      d2 = d3;
+      r0 = r1;
+      r1 = r2;
+      r2 = r3;
+      x0 = x1;
+      x1 = x2;
+      ++k;
+    }
+    if (ok && mbar_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
+      if (lane == 0) *reinterpret_cast<WsHeader*>(smem + L::off_stage + (size_t)(k % D) * L::stage_bytes) =
+          WsHeader{-1, 0, 0, 0};
+      mbar_arrive(full + k % D);
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      double v = wsum[p];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && v != 0.0 && a.sumwt) atomicAdd(a.sumwt + p, v);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr unsigned idesc = umma_idesc_tf32(128, UN);
+      int item = 0;
+      bool ok = true;
+      for (int k = 0;; ++k) {
+        const int ob = k & 1;
+        unsigned char* obuf = smem + L::off_ob + (size_t)ob * L::ob_bytes;
+        if (!mbar_wait(ofull + ob, (k >> 1) & 1, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int4 hdr = *reinterpret_cast<const int4*>(obuf + L::ob_hdr);   // nst, flags, xy
+        if (hdr.x < 0) break;
+        const int ab = item % NACC;
+        if (hdr.y & kWsFirst) {
+          // the accumulator must have been read out by the epilogue (its use item - NACC)
+          if (!mbar_wait(aempty + ab, ((item / NACC) & 1) ^ 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        const unsigned abase = smem_u32(obuf);
+        const unsigned dcol = tmem + (unsigned)(ab * MT * UN);
+#pragma unroll 1
+        for (int t = 0; t < MT; ++t) {
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks) {
+            const unsigned aoff = (unsigned)(t * 16 * L::SBO + ks * 2 * L::LBO);
+            const unsigned boff = (unsigned)(ks * 2 * L::LBO);
+            const uint64_t ahi = umma_sdesc(abase + (unsigned)L::ob_ahi + aoff, L::LBO, L::SBO);
+            const uint64_t alo = umma_sdesc(abase + (unsigned)L::ob_alo + aoff, L::LBO, L::SBO);
+            const uint64_t bhi = umma_sdesc(abase + (unsigned)L::ob_bhi + boff, L::LBO, L::SBO);
+            const uint64_t blo = umma_sdesc(abase + (unsigned)L::ob_blo + boff, L::LBO, L::SBO);
+            const unsigned first = (hdr.y & kWsFirst) && ks == 0;
+            const unsigned d = dcol + (unsigned)(t * UN);
+            umma_tf32(d, alo, bhi, idesc, first ? 0u : 1u);
+            umma_tf32(d, ahi, blo, idesc, 1u);
+            umma_tf32(d, ahi, bhi, idesc, 1u);
+          }
+        }
+        umma_commit(oempty + ob);   // the operand buffer is free once these MMAs are done
+        if (hdr.y & kWsLast) {
+          acc_xy[ab] = hdr.z;
+          mbar_arrive(afull + ab);   // window origin visible to the epilogue
+          umma_commit(afull + ab);   // accumulator complete
+          ++item;
+        }
+      }
+      // tell the epilogue warps to stop: a phase of the next accumulator with the end marker
+      const int ab = item % NACC;
+      if (ok && mbar_wait(aempty + ab, ((item / NACC) & 1) ^ 1, abort_flag, err)) {
+        acc_xy[ab] = -1;
+        mbar_arrive(afull + ab);
+        mbar_arrive(afull + ab);
+      }
+      // every MMA issued has completed before the tensor memory can be released (bounded wait
+      // that ignores the abort flag)
+      umma_commit(fin);
+      volatile int never = 0;
+      mbar_wait(fin, 0, &never, err);
+    }
+    __syncwarp();
+  } else if (warp < 6) {
+    // ------------------------------------------------------------------------------ epilogue
+    const int q = warp & 3;   // tensor-memory lane quarter of this warp
+    for (int item = 0;; ++item) {
+      const int ab = item % NACC;
+      if (!mbar_wait(afull + ab, (item / NACC) & 1, abort_flag, err)) break;
+      tc_fence_after();
+      const int xy = acc_xy[ab];
+      if (xy < 0) break;
+      const int X0 = xy & 0xffff, Y0 = xy >> 16;
+      for (int t = 0; t < MT; ++t) {
+        // row m = 128 t + 32 q + lane = (x, p, c): x = m / 2P, p = (m / 2) mod P, c = m mod 2
+        const int m = 128 * t + 32 * q + lane;
+        const int x = m / (2 * P), p = (m >> 1) % P, c = m & 1;
+        const int gx = X0 + x;
+        for (int y0 = 0; y0 < UN; y0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(ab * MT * UN + t * UN + y0), v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int gy = Y0 + y0 + i;
+            if (v[i] != 0.f && gx < a.N && gy < a.N) {
+              const size_t e = ((size_t)gy * a.N + gx) * P + p;   // complex element of the grid
+              if (a.flags & AWG_GRID_FP64) {
+                atomicAdd(reinterpret_cast<double*>(a.grid) + 2 * e + c, (double)v[i]);
+              } else if (a.flags & AWG_GRID_KAHAN) {
+                const float old = atomicAdd(a.grid + 2 * e + c, v[i]);
+                const float sum = old + v[i], bb = sum - old;
+                const float er = (old - (sum - bb)) + (v[i] - bb);
+                if (er != 0.f) atomicAdd(a.grid_lo + 2 * e + c, er);
+              } else {
+                atomicAdd(a.grid + 2 * e + c, v[i]);
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(aempty + ab);
+    }
+  } else {
+    // ------------------------------------------------------------------------------ builders
+    const int bt = tid - 6 * 32;   // 0 .. 32 NB_WARPS - 1
+    constexpr int NBT = 32 * L::NB_WARPS;
+    for (int k = 0;; ++k) {
+      const int s = k % D, ob = k & 1;
+      unsigned char* sg = smem + L::off_stage + (size_t)s * L::stage_bytes;
+      unsigned char* obuf = smem + L::off_ob + (size_t)ob * L::ob_bytes;
+      if (!mbar_wait(full + s, (k / D) & 1, abort_flag, err)) break;
+      // the operand buffer is free once the MMAs that read it (chunk k - 2) are done
+      if (!mbar_wait(oempty + ob, ((k >> 1) & 1) ^ 1, abort_flag, err)) break;
+      const WsHeader h = *reinterpret_cast<const WsHeader*>(sg);
+      if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(h.nst, h.flags, h.xy, 0);
+      if (h.nst >= 0) {
+        const int* pkv = reinterpret_cast<const int*>(sg + L::st_pk);
+        const float2* fyv = reinterpret_cast<const float2*>(sg + L::st_fy);
+        const float2* fxv = reinterpret_cast<const float2*>(sg + L::st_fx);
+        const float2* wvv = reinterpret_cast<const float2*>(sg + L::st_wv);
+        // A: one task per (x, p, sample pair): rows (x, p, 0) and (x, p, 1), 4 k values each
+        for (int task = bt; task < L::UX * P * (J / 2); task += NBT) {
+          const int kq = task % (J / 2);
+          const int xp = task / (J / 2);
+          const int x = xp / P, p = xp % P;
+          float v0[4], v1[4];   // rows c = 0 and c = 1, k = 4 kq .. 4 kq + 3
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int j = 2 * kq + h2;
+            float xr = 0.f, xi = 0.f;
+            if (j < h.nst) {
+              const int tx = x - (pkv[j] & 0xff);
+              if (tx >= 0 && tx < S) {
+                const float2 f = fxv[j * S + tx];
+                const float2 w = wvv[j * P + p];
+                xr = f.x * w.x + f.y * w.y;   // conj(fx) w V
+                xi = f.x * w.y - f.y * w.x;
+              }
+            }
+            v0[2 * h2] = xr;
+            v0[2 * h2 + 1] = xi;
+            v1[2 * h2] = xi;
+            v1[2 * h2 + 1] = -xr;
+          }
+          const int m0 = xp * 2;   // row (x, p, 0); (x, p, 1) is m0 + 1
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int m = m0 + c;
+            const float* vv = c ? v1 : v0;
+            float hi[4], lo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tf32_split(vv[i], hi[i], lo[i]);
+            const size_t off = (size_t)(m % 8) * 16 + (size_t)(m / 8) * L::SBO + (size_t)kq * L::LBO;
+            *reinterpret_cast<float4*>(obuf + L::ob_ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+          }
+        }
+        // B: one task per (y, sample pair)
+        for (int task = bt; task < UN * (J / 2); task += NBT) {
+          const int kq = task % (J / 2);
+          const int y = task / (J / 2);
+          float vv[4];
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int j = 2 * kq + h2;
+            float br = 0.f, bi = 0.f;
+            if (j < h.nst) {
+              const int ty = y - ((pkv[j] >> 8) & 0xff);
+              if (ty >= 0 && ty < S) {
+                const float2 f = fyv[j * S + ty];
+                br = f.x;
+                bi = f.y;
+              }
+            }
+            vv[2 * h2] = br;
+            vv[2 * h2 + 1] = bi;
+          }
+          float hi[4], lo[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tf32_split(vv[i], hi[i], lo[i]);
+          const size_t off = (size_t)(y % 8) * 16 + (size_t)(y / 8) * L::SBO + (size_t)kq * L::LBO;
+          *reinterpret_cast<float4*>(obuf + L::ob_bhi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<float4*>(obuf + L::ob_blo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        }
+      }
+      fence_proxy_async_smem();   // the operands are read by the tensor cores (async proxy)
+      mbar_arrive(empty + s);
+      mbar_arrive(ofull + ob);
+      if (h.nst < 0) break;
+    }
+  }
+
+  // every role has left its loop: release the tensor memory
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  __syncwarp();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)L::TCOLS));
+}
+
+// Tensor-core configuration per exact support: the tile of first-tap positions (window side
+// S + TILE - 1 at or just below a multiple of 16, so that little of the padded window is waste),
+// samples per chunk and stages.
+struct MmaCfg {
+  int S, tile, j, d;
+};
+constexpr MmaCfg kMmaCfg[8] = {
+    {8, 9, 8, 3}, {16, 17, 8, 3}, {24, 9, 8, 3}, {32, 17, 8, 3},
+    {40, 9, 8, 3}, {48, 17, 8, 3}, {56, 9, 8, 3}, {64, 9, 8, 3},
+};
+constexpr MmaCfg mma_cfg(int S) {
+  for (const MmaCfg& e : kMmaCfg)
+    if (e.S == S) return e;
+  return MmaCfg{S, 0, 0, 0};
+}
+
+template <int S, int P>
+awg_status run_grid_mma(const GridArgs& a, int slot, int sms, cudaStream_t st) {
+  constexpr MmaCfg c = mma_cfg(S);
+  static_assert(c.tile == exact_cfg(S, 3).tile, "the plan bins candidate 3 by this tile");
+  using L = MmaGridLayout<S, P, c.tile, c.j, c.d>;
+  static_assert(L::alloc <= 227 * 1024, "tensor-core gridding stages do not fit");
+  auto kern = k_grid_mma<S, P, c.tile, c.j, c.d>;
+  static int ok = 0;
+  if (!ok) {
+    AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::alloc));
+    int bps = 0;
+    AWG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, L::NT, L::alloc));
+    if (bps != 1) return set_error(AWG_ERR_CUDA, "tensor-core gridding kernel must hold an SM alone");
+    ok = 1;
+  }
+  kern<<<sms, L::NT, L::alloc, st>>>(a, slot);
+  AWG_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return AWG_OK;
+}
+
+#define AWG_FOR_MMA(M) M(8, 1) M(8, 2) M(8, 4) M(16, 1) M(16, 2) M(16, 4) M(24, 1) M(24, 2) M(24, 4) M(32, 1) M(32, 2) M(32, 4) \
+  M(40, 1) M(40, 2) M(40, 4) M(48, 1) M(48, 2) M(48, 4) M(56, 1) M(56, 2) M(56, 4) M(64, 1) M(64, 2) M(64, 4)
+#define AWG_DECLARE_GRID_MMA(S, P) extern template awg_status run_grid_mma<S, P>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_MMA(S, P) template awg_status run_grid_mma<S, P>(const GridArgs&, int, int, cudaStream_t);
+
+}  // namespace awg

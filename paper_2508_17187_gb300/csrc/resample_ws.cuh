@@ -533,8 +533,13 @@ struct WsDegridLayout {
   static constexpr int B = 32 / (2 * P);          // samples per butterfly batch
   static constexpr int NB = (ST + B - 1) / B;     // batches per stage
   // window as the TMA tile lands: P >= 2: [U][U][P] c64 (3-D box (2P, U, U)); P = 1: rows of UB
-  // pixels, UB = U rounded up to even (2-D box (2 UB, U): a whole number of 16-byte units per row)
-  static constexpr int UB = (P == 1) ? ((U + 1) & ~1) : U;
+  // pixels (2-D box (2 UB, U)).  A P = 1 box starts at an even pixel (its x coordinate, 8 bytes a
+  // pixel, must be a multiple of 16 bytes): with an odd tile the window origin X0 may be odd, and
+  // the box then starts one pixel early (XA = 1 extra column) and the window sits at X0 & 1 in it.
+  // UB is U + XA rounded up to even, so that a box row is a whole number of 16-byte units.
+  static constexpr int XA = (P == 1 && TILE % 2 == 1) ? 1 : 0;
+  static constexpr int UB = (P == 1) ? ((U + XA + 1) & ~1) : U;
+  static_assert(P != 1 || 2 * UB <= 256, "a TMA box side holds at most 256 elements");
   static constexpr unsigned box_bytes = (unsigned)U * UB * P * 8;
   static constexpr size_t win_bytes = ws_al1k(box_bytes);
   static constexpr size_t st_rs = 16;
@@ -626,7 +631,7 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
           unsigned char* dst = smem + (size_t)w * L::win_bytes;
           mbar_arrive_expect_tx(wfull + w, L::box_bytes);
           const int X0 = d0.xy & 0xffff, Y0 = d0.xy >> 16;
-          if constexpr (P == 1) tma_load_2d(dst, &gmap, 2 * X0, Y0, wfull + w);
+          if constexpr (P == 1) tma_load_2d(dst, &gmap, 2 * (X0 & ~1), Y0, wfull + w);
           else tma_load_3d(dst, &gmap, 0, X0, Y0, wfull + w);
         }
         tma_pending |= 1u << w;
@@ -737,7 +742,8 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
       if (h.flags & kWsFirst) {
         const int w = ic % NWIN;
         if (!mbar_wait(wfull + w, (ic / NWIN) & 1, abort_flag, err)) break;
-        win = reinterpret_cast<const float2*>(smem + (size_t)w * L::win_bytes);
+        // P = 1: the box starts at the even pixel at or below X0 (see the layout)
+        win = reinterpret_cast<const float2*>(smem + (size_t)w * L::win_bytes) + (P == 1 ? (h.xy & 1) : 0);
         curX = -1;
         prev_pk = -1;
         prev_row = -1;
@@ -865,10 +871,10 @@ constexpr WsCfg ws_cfg(int S) {
   return WsCfg{S, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 }
 
-template <int S, int P>
+template <int S, int P, int C = 2>
 awg_status run_grid_ws(const GridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr WsCfg c = ws_cfg(S);
-  constexpr int T = exact_cfg(S, 2).tile;
+  constexpr int T = exact_cfg(S, C).tile;
   using L = WsGridLayout<S, P, c.g_grid, T, c.st_grid, c.d_grid, c.nwin_grid>;
   static_assert(L::alloc <= 227 * 1024, "gridding stages do not fit");
   auto kern = k_grid_ws<S, P, c.g_grid, T, c.st_grid, c.d_grid, c.nwin_grid, c.minb_grid>;
@@ -887,10 +893,10 @@ awg_status run_grid_ws(const GridArgs& a, int slot, int sms, cudaStream_t st) {
 // The tensor map of the grid for the degridding windows (built by the caller, see launch.cu).
 awg_status make_grid_tensor_map(CUtensorMap* map, const void* grid, int N, int P, int U, int UB);
 
-template <int S, int P>
+template <int S, int P, int C = 2>
 awg_status run_degrid_ws(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
   constexpr WsCfg c = ws_cfg(S);
-  constexpr int T = exact_cfg(S, 2).tile;
+  constexpr int T = exact_cfg(S, C).tile;
   using L = WsDegridLayout<S, P, c.g_degrid, T, c.st_degrid, c.d_degrid, c.nwin_degrid>;
   static_assert(L::alloc <= 227 * 1024, "degridding stages do not fit");
   auto kern = k_degrid_ws<S, P, c.g_degrid, T, c.st_degrid, c.d_degrid, c.nwin_degrid, c.minb_degrid>;
@@ -912,11 +918,15 @@ awg_status run_degrid_ws(const DegridArgs& a, int slot, int sms, cudaStream_t st
 // Supports and pol counts of the warp-specialised kernels, in two halves (two translation units each).
 #define AWG_FOR_WS_A(M) M(8, 1) M(8, 2) M(8, 4) M(16, 1) M(16, 2) M(16, 4) M(24, 1) M(24, 2) M(24, 4) M(32, 1) M(32, 2) M(32, 4)
 #define AWG_FOR_WS_B(M) M(40, 1) M(40, 2) M(40, 4) M(48, 1) M(48, 2) M(48, 4) M(56, 1) M(56, 2) M(56, 4) M(64, 1) M(64, 2) M(64, 4)
-#define AWG_DECLARE_GRID_WS(S, P) extern template awg_status run_grid_ws<S, P>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_DECLARE_GRID_WS(S, P) extern template awg_status run_grid_ws<S, P, 2>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_DECLARE_DEGRID_WS(S, P) \
-  extern template awg_status run_degrid_ws<S, P>(const DegridArgs&, int, int, cudaStream_t);
-#define AWG_INSTANTIATE_GRID_WS(S, P) template awg_status run_grid_ws<S, P>(const GridArgs&, int, int, cudaStream_t);
+  extern template awg_status run_degrid_ws<S, P, 2>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_DECLARE_DEGRID_WS3(S, P) \
+  extern template awg_status run_degrid_ws<S, P, 3>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_WS(S, P) template awg_status run_grid_ws<S, P, 2>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_INSTANTIATE_DEGRID_WS(S, P) \
-  template awg_status run_degrid_ws<S, P>(const DegridArgs&, int, int, cudaStream_t);
+  template awg_status run_degrid_ws<S, P, 2>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_DEGRID_WS3(S, P) \
+  template awg_status run_degrid_ws<S, P, 3>(const DegridArgs&, int, int, cudaStream_t);
 
 }  // namespace awg

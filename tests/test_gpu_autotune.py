@@ -1,5 +1,5 @@
-"""The per-support kernel autotuner: it times the three compiled configurations of every
-exact-support kernel (two cp.async tilings and the warp-specialised pair) on a plan of the caller's
+"""The per-support kernel autotuner: it times the four compiled configurations of every
+exact-support kernel (two cp.async tilings, the warp-specialised pair, tensor-core gridding) on a plan of the caller's
 geometry, keeps the fastest one per support, invalidates older plans, and the tuned set still
 matches the oracle."""
 import numpy as np
@@ -27,8 +27,8 @@ def test_autotune_picks_per_support_and_keeps_parity():
     choice, ms = cf.autotune(uvw, freq, n_pol=4)
     present = set(int(s) for s in np.unique(cf.supports()))
     assert set(choice) == {s for s in present if s % 8 == 0}
-    assert all(c in (0, 1, 2) for c in choice.values())
-    assert all(min(t) > 0 and len(t) == 3 and ms[s][choice[s]] == min(t) for s, t in ms.items())
+    assert all(c in (0, 1, 2, 3) for c in choice.values())
+    assert all(min(t) > 0 and len(t) == 4 and ms[s][choice[s]] == min(t) for s, t in ms.items())
     N, P = wl.grid_n, wl.n_pol
     g = torch.zeros((N, N, P), dtype=torch.complex64, device="cuda")
     sw = torch.zeros(P, dtype=torch.float64, device="cuda")
@@ -57,4 +57,4 @@ def test_choose_rejects_supports_without_configurations():
     with pytest.raises(AwgError):
         cf.choose(7, 1)
     with pytest.raises(AwgError):
-        cf.choose(8, 3)
+        cf.choose(8, 4)

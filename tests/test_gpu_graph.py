@@ -12,19 +12,19 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("config", ["wproj", "awproj", "wproj_ws"])
+@pytest.mark.parametrize("config", ["wproj", "awproj", "wproj_ws", "wproj_mma"])
 def test_step_replays_from_cuda_graph(config):
     import paper_2508_17187_gb300 as awg
-    if config in ("wproj", "wproj_ws"):
+    if config in ("wproj", "wproj_ws", "wproj_mma"):
         wl = synth.make_workload("wproj", n_int=24, n_chan=8, grid_n=1024, n_wplanes=8, vis_device="cuda")
     else:
         wl = synth.make_workload("awproj", n_int=12, n_chan=8, grid_n=512, n_pa=3, n_sb=2, n_wplanes=4,
                                  max_support=32, oversampling=8, vis_device="cuda")
     op = oracle_params(wl)
     cf = awg.cf_set_create(**library_params(op))
-    if config == "wproj_ws":   # the warp-specialised kernels (their tensor maps are built at capture)
+    if config in ("wproj_ws", "wproj_mma"):   # warp-specialised / tensor-core kernels (tensor maps built at capture)
         for S in sorted(set(cf.supports().tolist())):
-            cf.choose(S, 2)
+            cf.choose(S, 2 if config == "wproj_ws" else 3)
     uvw = torch.as_tensor(wl.uvw_m).cuda()
     freq = torch.as_tensor(wl.freq_hz).cuda()
     pa = torch.as_tensor(wl.pa_bin).cuda() if wl.use_a else None

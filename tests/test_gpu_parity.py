@@ -335,12 +335,12 @@ def test_fused_kernels_random_low_rank_tables(awg, P, terms):
     _random_tables_case(awg, P, rank1=True, terms=terms, sups=[8, 16, 24, 32, 40, 48, 56, 64])
 
 
-@pytest.mark.parametrize("config", [0, 1, 2])
+@pytest.mark.parametrize("config", [0, 1, 2, 3])
 @pytest.mark.parametrize("P", [1, 2, 4])
 def test_every_support_separable_random_factors(awg, P, config):
     """Random outer-product tables with the same supports: the separable path, every exact-support
-    kernel (8, 16, ..., 64) in its three compiled configurations (2: the warp-specialised kernels)
-    and every class kernel for the supports in between."""
+    kernel (8, 16, ..., 64) in its four compiled configurations (2: the warp-specialised kernels,
+    3: tensor-core gridding) and every class kernel for the supports in between."""
     _random_tables_case(awg, P, rank1=True, config=config)
 
 

@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 U = 2.0 ** -24
 
 
-@pytest.mark.parametrize("separable,config", [(True, 0), (False, 0), (True, 2)])
+@pytest.mark.parametrize("separable,config", [(True, 0), (False, 0), (True, 2), (True, 3)])
 def test_every_pixel_within_its_rounding_bound(separable, config):
     import paper_2508_17187_gb300 as awg
     from paper_2508_17187_gb300 import _lib

@@ -9,6 +9,7 @@ so that whatever the first call left in the shared array cannot leak into the se
 the limits it rejects.  This file is named to be collected last.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -51,17 +52,23 @@ def _noalloc(lib, cf, uvw, freq, vis, wt, grid, sumwt, pa=None, sb=None):
 
 def _noalloc_armed(lib, *args, **kw):
     """The call with every library device allocation armed to fail: it must still succeed, and the
-    library's live allocation count must not move."""
-    live = lib.awg_debug_live_allocations()
-    torch_live = torch.cuda.memory_allocated()
-    assert lib.awg_debug_fail_allocations(0) == 0
+    library's live allocation count must not move.  The count is library-wide, so the garbage
+    collector (which may release other tests' plans and CF sets) is held off meanwhile."""
+    gc.collect()
+    gc.disable()
     try:
-        st = _noalloc(lib, *args, **kw)
+        live = lib.awg_debug_live_allocations()
+        torch_live = torch.cuda.memory_allocated()
+        assert lib.awg_debug_fail_allocations(0) == 0
+        try:
+            st = _noalloc(lib, *args, **kw)
+        finally:
+            lib.awg_debug_fail_allocations(-1)
+        assert st == 0, lib.awg_last_error()
+        assert lib.awg_debug_live_allocations() == live
+        assert torch.cuda.memory_allocated() == torch_live
     finally:
-        lib.awg_debug_fail_allocations(-1)
-    assert st == 0, lib.awg_last_error()
-    assert lib.awg_debug_live_allocations() == live
-    assert torch.cuda.memory_allocated() == torch_live
+        gc.enable()
     return st
 
 
