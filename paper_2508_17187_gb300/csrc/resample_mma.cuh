@@ -21,10 +21,11 @@
 // sqrt(770) 2^-23, a few 1e-6, whatever the flush mode.
 //
 // Roles (one persistent CTA per SM):
-//  * warp 0, the producer, stages chunks of J samples (records, factor rows by TMA bulk copies,
-//    w V times the phasor) into a ring of stages, as in the warp-specialised kernels;
-//  * the builder warps turn a stage into the A and B operands of the chunk (hi and lo parts) in the
-//    canonical no-swizzle K-major layout of the tensor cores, in one of two operand buffers;
+//  * warp 0, the producer, stages up to 32 samples at a time (records, factor rows by TMA bulk
+//    copies, w V times the phasor) into a ring of stages, as in the warp-specialised kernels;
+//  * the builder warps cut a stage into chunks of J samples and turn each chunk into the A and B
+//    operands (hi and lo parts) in the canonical no-swizzle K-major layout of the tensor cores, in
+//    a ring of operand buffers;
 //  * warp 1 owns the tensor memory; its lane 0 issues the MMAs of each chunk into the item's
 //    accumulator (two accumulators, so that one item's flush overlaps the next item's MMAs) and
 //    commits them to the barriers that free the operand buffer and, at the end of an item, hand
@@ -102,9 +103,12 @@ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
 
 // ------------------------------------------------------------------------------------- layout
 
-template <int S, int P, int TILE, int J, int D>
+// J samples per MMA chunk (K = 2 J), ST samples per producer stage (a stage is cut into ST / J
+// chunks), D stages, NOB operand buffers.
+template <int S, int P, int TILE, int J, int ST, int D, int NOB>
 struct MmaGridLayout {
-  static_assert(S % 2 == 0 && J % 4 == 0, "factor rows move in 16-byte units; K steps take 4 samples");
+  static_assert(S % 2 == 0, "factor rows move in 16-byte units");
+  static_assert(J % 8 == 0 && ST % J == 0 && ST <= 32, "chunks of whole K steps; a stage is one warp's samples");
   static constexpr int U = TILE + S - 1;                              // window side
   static constexpr int XQ = 128 / (2 * P);                            // pixels per 128-row tile
   static constexpr int UX = (U + XQ - 1) / XQ * XQ;                   // padded columns (x)
@@ -113,51 +117,69 @@ struct MmaGridLayout {
   static constexpr int MT = M / 128;                                  // 128-row tiles
   static constexpr int K = 2 * J;                                     // per chunk
   static constexpr int KS = K / 8;                                    // MMA k-steps per chunk
+  static constexpr int KQ = J / 2;                                    // 16-byte K groups per row
   static constexpr int NACC = (2 * MT * UN <= 512) ? 2 : 1;           // accumulators in tensor memory
   static constexpr int TCOLS0 = NACC * MT * UN;
   static constexpr int TCOLS = TCOLS0 <= 32 ? 32 : TCOLS0 <= 64 ? 64 : TCOLS0 <= 128 ? 128 : TCOLS0 <= 256 ? 256 : 512;
   static_assert(TCOLS0 <= 512, "the accumulator does not fit in tensor memory");
   static_assert(UN <= 256, "MMA N is at most 256");
+  static_assert((UX * P) % 8 == 0, "A rows are built in groups of 8 pixel-pols");
   // canonical K-major layout: LBO = 128 bytes (adjacent core matrices in K), SBO = (K / 4) * 128
   static constexpr unsigned LBO = 128, SBO = (K / 4) * 128;
   static constexpr size_t a_bytes = (size_t)M * K * 4;
   static constexpr size_t b_bytes = (size_t)UN * K * 4;
-  // operand buffer: A_hi, A_lo, B_hi, B_lo, then a small header (flags, window origin)
+  // operand buffer: A_hi, A_lo, B_hi, B_lo, then a small header (samples, flags, window origin)
   static constexpr size_t ob_ahi = 0, ob_alo = a_bytes, ob_bhi = 2 * a_bytes, ob_blo = 2 * a_bytes + b_bytes;
   static constexpr size_t ob_hdr = 2 * a_bytes + 2 * b_bytes;
   static constexpr size_t ob_bytes = ws_al1k(ob_hdr + 16);
-  // raw stage (producer -> builders)
+  // producer stage: header, first-tap offsets, fy rows, fx rows, w V (times the phasor) per pol
   static constexpr size_t st_pk = 16;
-  static constexpr size_t st_fy = st_pk + ws_al16(4 * J);
-  static constexpr size_t st_fx = st_fy + (size_t)J * S * 8;
-  static constexpr size_t st_wv = st_fx + (size_t)J * S * 8;
-  static constexpr size_t stage_bytes = ws_al16(st_wv + (size_t)J * P * 8);
-  static constexpr int NB_WARPS = 8;                                  // builders
+  static constexpr size_t st_fy = st_pk + ws_al16(4 * ST);
+  static constexpr size_t st_fx = st_fy + (size_t)ST * S * 8;
+  static constexpr size_t st_wv = st_fx + (size_t)ST * S * 8;
+  static constexpr size_t stage_bytes = ws_al16(st_wv + (size_t)ST * P * 8);
+  static constexpr int NB_WARPS = 10;                                 // builders
   static constexpr int NT = 32 * (2 + 4 + NB_WARPS);                  // producer, MMA, epilogue, builders
   static constexpr size_t off_ob = 0;
-  static constexpr size_t off_stage = 2 * ob_bytes;
+  static constexpr size_t off_stage = NOB * ob_bytes;
   static constexpr size_t off_bar = off_stage + D * stage_bytes;
-  // barriers: full[D], empty[D], ofull[2], oempty[2], afull[NACC], aempty[NACC], fin
-  static constexpr size_t off_misc = off_bar + 8 * (2 * D + 4 + 2 * NACC + 1);
+  // barriers: full[D], empty[D], ofull[NOB], oempty[NOB], afull[NACC], aempty[NACC], fin
+  static constexpr size_t off_misc = off_bar + 8 * (2 * D + 2 * NOB + 2 * NACC + 1);
   static constexpr size_t off_soff = ws_al16(off_misc + 32 + 4 * NACC);
   static constexpr size_t bytes = off_soff + 8 * (size_t)kSepOffCache;
   // at least 116 KB so that one CTA holds an SM (and its tensor memory) alone
   static constexpr size_t alloc = (bytes + 1024 > 116 * 1024 ? bytes + 1024 : 116 * 1024);
 };
 
-template <int S, int P, int TILE, int J, int D>
-__global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
+// Warp-elected arrival: the warp's lanes have finished their part (their earlier shared-memory
+// writes are ordered before lane 0's release by the warp barrier).
+__device__ __forceinline__ void warp_arrive(uint64_t* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
+// Warp-uniform bounded wait: every lane waits, and the warp goes on only if all of its lanes saw
+// the phase, so that a lane that gave up never leaves part of a warp at a warp-collective
+// instruction (tcgen05.ld, shuffles, warp barriers) after the wait.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag,
+                                          unsigned long long* err) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, err);
+  return __all_sync(0xffffffffu, ok);
+}
+
+template <int S, int P, int TILE, int J, int ST, int D, int NOB>
+__global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
     k_grid_mma(const GridArgs a, const int cls) {
-  using L = MmaGridLayout<S, P, TILE, J, D>;
-  constexpr int MT = L::MT, KS = L::KS, UN = L::UN, NACC = L::NACC;
+  using L = MmaGridLayout<S, P, TILE, J, ST, D, NOB>;
+  constexpr int MT = L::MT, KS = L::KS, KQ = L::KQ, UN = L::UN, NACC = L::NACC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   int64_t* s_off = reinterpret_cast<int64_t*>(smem + L::off_soff);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);
   uint64_t* empty = full + D;
   uint64_t* ofull = full + 2 * D;
-  uint64_t* oempty = ofull + 2;
-  uint64_t* afull = oempty + 2;
+  uint64_t* oempty = ofull + NOB;
+  uint64_t* afull = oempty + NOB;
   uint64_t* aempty = afull + NACC;
   uint64_t* fin = aempty + NACC;   // completion of every MMA issued, before the tensor memory is freed
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::off_misc);
@@ -173,15 +195,15 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
   if (tid == 0) {
     for (int d = 0; d < D; ++d) {
       mbar_init(full + d, 32);
-      mbar_init(empty + d, 32 * L::NB_WARPS);
+      mbar_init(empty + d, L::NB_WARPS);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(ofull + b, 32 * L::NB_WARPS);
+    for (int b = 0; b < NOB; ++b) {
+      mbar_init(ofull + b, L::NB_WARPS);
       mbar_init(oempty + b, 1);
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(afull + b, 2);   // the MMA thread's arrival (window origin written) + the commit
-      mbar_init(aempty + b, 128);
+      mbar_init(aempty + b, 4);  // the four epilogue warps
     }
     mbar_init(fin, 1);
     *abort_flag = 0;
@@ -204,7 +226,7 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
 #pragma unroll
     for (int p = 0; p < P; ++p) wsum[p] = 0.0;
     WsItemWalker walk;
-    walk.init(a.class_range[cls], a.class_range[cls + 1], cls, TILE, J, a.queue, a.items);
+    walk.init(a.class_range[cls], a.class_range[cls + 1], cls, TILE, ST, a.queue, a.items);
     const float2* sep2 = reinterpret_cast<const float2*>(a.sep);
     WsChunk d0 = walk.next();
     WsChunk d1 = walk.next();
@@ -219,7 +241,7 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
     while (d0.valid) {
       const int s = k % D;
       unsigned char* sg = smem + L::off_stage + (size_t)s * L::stage_bytes;
-      if (!mbar_wait(empty + s, ((k / D) & 1) ^ 1, abort_flag, err)) {
+      if (!warp_wait(empty + s, ((k / D) & 1) ^ 1, abort_flag, err)) {
         ok = false;
         break;
       }
@@ -260,7 +282,7 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
       x1 = x2;
       ++k;
     }
-    if (ok && mbar_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
+    if (ok && warp_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
       if (lane == 0) *reinterpret_cast<WsHeader*>(smem + L::off_stage + (size_t)(k % D) * L::stage_bytes) =
           WsHeader{-1, 0, 0, 0};
       mbar_arrive(full + k % D);
@@ -277,10 +299,10 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
       constexpr unsigned idesc = umma_idesc_tf32(128, UN);
       int item = 0;
       bool ok = true;
-      for (int k = 0;; ++k) {
-        const int ob = k & 1;
+      for (int q = 0;; ++q) {
+        const int ob = q % NOB;
         unsigned char* obuf = smem + L::off_ob + (size_t)ob * L::ob_bytes;
-        if (!mbar_wait(ofull + ob, (k >> 1) & 1, abort_flag, err)) {
+        if (!mbar_wait(ofull + ob, (q / NOB) & 1, abort_flag, err)) {
           ok = false;
           break;
         }
@@ -340,129 +362,161 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
   } else if (warp < 6) {
     // ------------------------------------------------------------------------------ epilogue
     const int q = warp & 3;   // tensor-memory lane quarter of this warp
+    const int mode = (a.flags & AWG_GRID_FP64) ? 2 : (a.flags & AWG_GRID_KAHAN) ? 1 : 0;
+    const size_t ystride = (size_t)a.N * P * 2;   // floats from one grid row to the next
     for (int item = 0;; ++item) {
       const int ab = item % NACC;
-      if (!mbar_wait(afull + ab, (item / NACC) & 1, abort_flag, err)) break;
+      if (!warp_wait(afull + ab, (item / NACC) & 1, abort_flag, err)) break;
       tc_fence_after();
       const int xy = acc_xy[ab];
       if (xy < 0) break;
       const int X0 = xy & 0xffff, Y0 = xy >> 16;
+      const int ny = min(L::U, a.N - Y0);   // window rows inside the grid
       for (int t = 0; t < MT; ++t) {
         // row m = 128 t + 32 q + lane = (x, p, c): x = m / 2P, p = (m / 2) mod P, c = m mod 2
         const int m = 128 * t + 32 * q + lane;
         const int x = m / (2 * P), p = (m >> 1) % P, c = m & 1;
         const int gx = X0 + x;
+        const bool col_ok = x < L::U && gx < a.N;
+        const size_t e0 = (((size_t)Y0 * a.N + gx) * P + p) * 2 + c;   // float index of (gx, Y0, p, c)
         for (int y0 = 0; y0 < UN; y0 += 16) {
           float v[16];
           tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(ab * MT * UN + t * UN + y0), v);
+          if (!col_ok || y0 >= ny) continue;
+          const size_t e = e0 + (size_t)y0 * ystride;
+          if (mode == 0) {
+            float* g = a.grid + e;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int gy = Y0 + y0 + i;
-            if (v[i] != 0.f && gx < a.N && gy < a.N) {
-              const size_t e = ((size_t)gy * a.N + gx) * P + p;   // complex element of the grid
-              if (a.flags & AWG_GRID_FP64) {
-                atomicAdd(reinterpret_cast<double*>(a.grid) + 2 * e + c, (double)v[i]);
-              } else if (a.flags & AWG_GRID_KAHAN) {
-                const float old = atomicAdd(a.grid + 2 * e + c, v[i]);
+            for (int i = 0; i < 16; ++i)
+              if (y0 + i < ny && v[i] != 0.f) atomicAdd(g + (size_t)i * ystride, v[i]);
+          } else if (mode == 1) {
+            float* g = a.grid + e;
+            float* glo = a.grid_lo + e;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (y0 + i < ny && v[i] != 0.f) {
+                const float old = atomicAdd(g + (size_t)i * ystride, v[i]);
                 const float sum = old + v[i], bb = sum - old;
                 const float er = (old - (sum - bb)) + (v[i] - bb);
-                if (er != 0.f) atomicAdd(a.grid_lo + 2 * e + c, er);
-              } else {
-                atomicAdd(a.grid + 2 * e + c, v[i]);
+                if (er != 0.f) atomicAdd(glo + (size_t)i * ystride, er);
               }
-            }
+          } else {
+            double* g = reinterpret_cast<double*>(a.grid) + e;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (y0 + i < ny && v[i] != 0.f) atomicAdd(g + (size_t)i * ystride, (double)v[i]);
           }
         }
       }
       tc_fence_before();
-      mbar_arrive(aempty + ab);
+      warp_arrive(aempty + ab);
     }
   } else {
     // ------------------------------------------------------------------------------ builders
+    // A task (pixel-pol xp, K group kq) writes rows (x, p, 0) and (x, p, 1) over samples 2 kq and
+    // 2 kq + 1; eight consecutive xp per K group, and lanes 4..7 of each eight write their c = 1
+    // row first, so that the 16-byte stores of a warp fall in all eight bank groups.  A B task
+    // (row y, K group kq) likewise with eight consecutive y.
     const int bt = tid - 6 * 32;   // 0 .. 32 NB_WARPS - 1
     constexpr int NBT = 32 * L::NB_WARPS;
-    for (int k = 0;; ++k) {
-      const int s = k % D, ob = k & 1;
+    int q = 0;   // chunks handed to the MMA thread so far
+    bool ok = true;
+    for (int k = 0; ok; ++k) {
+      const int s = k % D;
       unsigned char* sg = smem + L::off_stage + (size_t)s * L::stage_bytes;
-      unsigned char* obuf = smem + L::off_ob + (size_t)ob * L::ob_bytes;
-      if (!mbar_wait(full + s, (k / D) & 1, abort_flag, err)) break;
-      // the operand buffer is free once the MMAs that read it (chunk k - 2) are done
-      if (!mbar_wait(oempty + ob, ((k >> 1) & 1) ^ 1, abort_flag, err)) break;
+      if (!warp_wait(full + s, (k / D) & 1, abort_flag, err)) break;
       const WsHeader h = *reinterpret_cast<const WsHeader*>(sg);
-      if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(h.nst, h.flags, h.xy, 0);
-      if (h.nst >= 0) {
-        const int* pkv = reinterpret_cast<const int*>(sg + L::st_pk);
-        const float2* fyv = reinterpret_cast<const float2*>(sg + L::st_fy);
-        const float2* fxv = reinterpret_cast<const float2*>(sg + L::st_fx);
-        const float2* wvv = reinterpret_cast<const float2*>(sg + L::st_wv);
-        // A: one task per (x, p, sample pair): rows (x, p, 0) and (x, p, 1), 4 k values each
-        for (int task = bt; task < L::UX * P * (J / 2); task += NBT) {
-          const int kq = task % (J / 2);
-          const int xp = task / (J / 2);
-          const int x = xp / P, p = xp % P;
-          float v0[4], v1[4];   // rows c = 0 and c = 1, k = 4 kq .. 4 kq + 3
+      const int nsub = h.nst < 0 ? 1 : (h.nst + J - 1) / J;
+      const int* pkv = reinterpret_cast<const int*>(sg + L::st_pk);
+      const float2* fyv = reinterpret_cast<const float2*>(sg + L::st_fy);
+      const float2* fxv = reinterpret_cast<const float2*>(sg + L::st_fx);
+      const float2* wvv = reinterpret_cast<const float2*>(sg + L::st_wv);
+      for (int sub = 0; sub < nsub; ++sub, ++q) {
+        const int ob = q % NOB;
+        unsigned char* obuf = smem + L::off_ob + (size_t)ob * L::ob_bytes;
+        // the operand buffer is free once the MMAs that read it (chunk q - NOB) are done
+        if (!warp_wait(oempty + ob, ((q / NOB) & 1) ^ 1, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        if (h.nst < 0) {
+          if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(-1, 0, 0, 0);
+        } else {
+          const int j0 = sub * J, n = min(J, h.nst - j0);
+          const int fl = (sub == 0 ? (h.flags & kWsFirst) : 0) | (sub == nsub - 1 ? (h.flags & kWsLast) : 0);
+          if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(n, fl, h.xy, 0);
+          for (int task = bt; task < L::UX * P * KQ; task += NBT) {
+            const int xl = task & 7;
+            const int kq = (task >> 3) % KQ;
+            const int xp = (task / (8 * KQ)) * 8 + xl;
+            const int x = xp / P, p = xp % P;
+            float xr[2], xi[2];
 #pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            const int j = 2 * kq + h2;
-            float xr = 0.f, xi = 0.f;
-            if (j < h.nst) {
-              const int tx = x - (pkv[j] & 0xff);
-              if (tx >= 0 && tx < S) {
-                const float2 f = fxv[j * S + tx];
-                const float2 w = wvv[j * P + p];
-                xr = f.x * w.x + f.y * w.y;   // conj(fx) w V
-                xi = f.x * w.y - f.y * w.x;
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int j = 2 * kq + h2;
+              xr[h2] = 0.f;
+              xi[h2] = 0.f;
+              if (j < n) {
+                const int tx = x - (pkv[j0 + j] & 0xff);
+                if (tx >= 0 && tx < S) {
+                  const float2 f = fxv[(j0 + j) * S + tx];
+                  const float2 w = wvv[(j0 + j) * P + p];
+                  xr[h2] = f.x * w.x + f.y * w.y;   // conj(fx) w V
+                  xi[h2] = f.x * w.y - f.y * w.x;
+                }
               }
             }
-            v0[2 * h2] = xr;
-            v0[2 * h2 + 1] = xi;
-            v1[2 * h2] = xi;
-            v1[2 * h2 + 1] = -xr;
-          }
-          const int m0 = xp * 2;   // row (x, p, 0); (x, p, 1) is m0 + 1
+            const int cfirst = (xl >> 2) & 1;
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int m = m0 + c;
-            const float* vv = c ? v1 : v0;
+            for (int cc = 0; cc < 2; ++cc) {
+              const int c = cc ^ cfirst;
+              const int m = 2 * xp + c;
+              // row c = 0: (Re X, Im X) per sample; row c = 1: (Im X, -Re X)
+              const float e0 = c ? xi[0] : xr[0], e1 = c ? -xr[0] : xi[0];
+              const float e2 = c ? xi[1] : xr[1], e3 = c ? -xr[1] : xi[1];
+              float h0, h1, h2v, h3, l0, l1, l2, l3;
+              tf32_split(e0, h0, l0);
+              tf32_split(e1, h1, l1);
+              tf32_split(e2, h2v, l2);
+              tf32_split(e3, h3, l3);
+              const size_t off = (size_t)(m % 8) * 16 + (size_t)(m / 8) * L::SBO + (size_t)kq * L::LBO;
+              *reinterpret_cast<float4*>(obuf + L::ob_ahi + off) = make_float4(h0, h1, h2v, h3);
+              *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(l0, l1, l2, l3);
+            }
+          }
+          for (int task = bt; task < UN * KQ; task += NBT) {
+            const int yl = task & 7;
+            const int kq = (task >> 3) % KQ;
+            const int y = (task / (8 * KQ)) * 8 + yl;
+            float vv[4];
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int j = 2 * kq + h2;
+              float br = 0.f, bi = 0.f;
+              if (j < n) {
+                const int ty = y - ((pkv[j0 + j] >> 8) & 0xff);
+                if (ty >= 0 && ty < S) {
+                  const float2 f = fyv[(j0 + j) * S + ty];
+                  br = f.x;
+                  bi = f.y;
+                }
+              }
+              vv[2 * h2] = br;
+              vv[2 * h2 + 1] = bi;
+            }
             float hi[4], lo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) tf32_split(vv[i], hi[i], lo[i]);
-            const size_t off = (size_t)(m % 8) * 16 + (size_t)(m / 8) * L::SBO + (size_t)kq * L::LBO;
-            *reinterpret_cast<float4*>(obuf + L::ob_ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            const size_t off = (size_t)(y % 8) * 16 + (size_t)(y / 8) * L::SBO + (size_t)kq * L::LBO;
+            *reinterpret_cast<float4*>(obuf + L::ob_bhi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<float4*>(obuf + L::ob_blo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
           }
         }
-        // B: one task per (y, sample pair)
-        for (int task = bt; task < UN * (J / 2); task += NBT) {
-          const int kq = task % (J / 2);
-          const int y = task / (J / 2);
-          float vv[4];
-#pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            const int j = 2 * kq + h2;
-            float br = 0.f, bi = 0.f;
-            if (j < h.nst) {
-              const int ty = y - ((pkv[j] >> 8) & 0xff);
-              if (ty >= 0 && ty < S) {
-                const float2 f = fyv[j * S + ty];
-                br = f.x;
-                bi = f.y;
-              }
-            }
-            vv[2 * h2] = br;
-            vv[2 * h2 + 1] = bi;
-          }
-          float hi[4], lo[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) tf32_split(vv[i], hi[i], lo[i]);
-          const size_t off = (size_t)(y % 8) * 16 + (size_t)(y / 8) * L::SBO + (size_t)kq * L::LBO;
-          *reinterpret_cast<float4*>(obuf + L::ob_bhi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<float4*>(obuf + L::ob_blo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        }
+        fence_proxy_async_smem();   // the operands are read by the tensor cores (async proxy)
+        warp_arrive(ofull + ob);
       }
-      fence_proxy_async_smem();   // the operands are read by the tensor cores (async proxy)
-      mbar_arrive(empty + s);
-      mbar_arrive(ofull + ob);
+      if (!ok) break;
+      warp_arrive(empty + s);   // every chunk of the stage is built
       if (h.nst < 0) break;
     }
   }
@@ -476,29 +530,34 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, D>::NT, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)L::TCOLS));
 }
 
-// Tensor-core configuration per exact support: the tile of first-tap positions (window side
-// S + TILE - 1 at or just below a multiple of 16, so that little of the padded window is waste),
-// samples per chunk and stages.
+// Tensor-core configuration per exact support and pol count: the tile of first-tap positions
+// (window side S + TILE - 1 at or just below a multiple of 16, so that little of the padded window
+// is waste; it depends on S alone, the plan bins by it), samples per MMA chunk and per producer
+// stage, stages and operand buffers (as many as the shared memory holds).
 struct MmaCfg {
-  int S, tile, j, d;
+  int S, P, tile, j, st, d, nob;
 };
-constexpr MmaCfg kMmaCfg[8] = {
-    {8, 9, 8, 3}, {16, 17, 8, 3}, {24, 9, 8, 3}, {32, 17, 8, 3},
-    {40, 9, 8, 3}, {48, 17, 8, 3}, {56, 9, 8, 3}, {64, 9, 8, 3},
+constexpr MmaCfg kMmaCfg[24] = {
+    {8, 1, 9, 16, 32, 3, 4},   {8, 2, 9, 16, 32, 3, 4},   {8, 4, 9, 16, 32, 3, 4},   {16, 1, 17, 16, 32, 3, 4},
+    {16, 2, 17, 16, 32, 3, 4}, {16, 4, 17, 16, 32, 3, 2}, {24, 1, 9, 16, 32, 3, 4},  {24, 2, 9, 16, 32, 3, 4},
+    {24, 4, 9, 16, 32, 3, 2},  {32, 1, 17, 16, 32, 2, 4}, {32, 2, 17, 16, 32, 3, 2}, {32, 4, 17, 8, 32, 3, 3},
+    {40, 1, 9, 16, 32, 2, 4},  {40, 2, 9, 16, 32, 3, 2},  {40, 4, 9, 8, 32, 2, 3},   {48, 1, 17, 16, 32, 3, 3},
+    {48, 2, 17, 16, 32, 2, 2}, {48, 4, 17, 8, 32, 3, 2},  {56, 1, 9, 16, 32, 2, 3},  {56, 2, 9, 16, 32, 2, 2},
+    {56, 4, 9, 8, 32, 2, 2},   {64, 1, 9, 8, 32, 2, 3},   {64, 2, 9, 8, 32, 3, 2},   {64, 4, 9, 8, 16, 2, 2},
 };
-constexpr MmaCfg mma_cfg(int S) {
+constexpr MmaCfg mma_cfg(int S, int P) {
   for (const MmaCfg& e : kMmaCfg)
-    if (e.S == S) return e;
-  return MmaCfg{S, 0, 0, 0};
+    if (e.S == S && e.P == P) return e;
+  return MmaCfg{S, P, 0, 0, 0, 0, 0};
 }
 
 template <int S, int P>
 awg_status run_grid_mma(const GridArgs& a, int slot, int sms, cudaStream_t st) {
-  constexpr MmaCfg c = mma_cfg(S);
+  constexpr MmaCfg c = mma_cfg(S, P);
   static_assert(c.tile == exact_cfg(S, 3).tile, "the plan bins candidate 3 by this tile");
-  using L = MmaGridLayout<S, P, c.tile, c.j, c.d>;
+  using L = MmaGridLayout<S, P, c.tile, c.j, c.st, c.d, c.nob>;
   static_assert(L::alloc <= 227 * 1024, "tensor-core gridding stages do not fit");
-  auto kern = k_grid_mma<S, P, c.tile, c.j, c.d>;
+  auto kern = k_grid_mma<S, P, c.tile, c.j, c.st, c.d, c.nob>;
   static int ok = 0;
   if (!ok) {
     AWG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::alloc));
