@@ -68,12 +68,14 @@ awg_status grid_class(int c, int P, const GridArgs& a, int sms, cudaStream_t st)
   return set_error(AWG_ERR_UNSUPPORTED, "no gridding kernel for this class / pol count");
 }
 
-// The warp-specialised kernels take P-contiguous visibilities and grids (no Mueller element
-// passes or pol mixing), 16-byte aligned buffers, and grids of at most 32768 pixels (window
+// The warp-specialised and tensor-core kernels take P-contiguous visibilities and grids (no
+// Mueller element passes or pol mixing), 16-byte aligned buffers (the grid and its compensation
+// grid take 16-byte atomics), and grids of at most 32768 pixels (window
 // origins packed in 16 bits); other calls on candidate 2 run the cp.async kernels of its tiles.
 bool ws_grid_ok(const GridArgs& a, int P) {
   return a.mix == nullptr && a.vstride == P && a.voff == 0 && a.gstride == P && a.goff == 0 && a.N <= 32768 &&
-         ((uintptr_t)a.vis & 15) == 0 && ((uintptr_t)a.weight & 15) == 0 && ((uintptr_t)a.grid & 15) == 0;
+         ((uintptr_t)a.vis & 15) == 0 && ((uintptr_t)a.weight & 15) == 0 && ((uintptr_t)a.grid & 15) == 0 &&
+         ((uintptr_t)a.grid_lo & 15) == 0;
 }
 
 bool ws_degrid_ok(const DegridArgs& a, int P) {
