@@ -195,7 +195,7 @@ struct MmaNLayout {
   static constexpr size_t st_fx = st_fy + (size_t)ST * S * 8;
   static constexpr size_t st_wv = st_fx + (size_t)ST * S * 8;
   static constexpr size_t stage_bytes = ws_al16(st_wv + (size_t)ST * P * 8);
-  static constexpr int NB_WARPS = 10;
+  static constexpr int NB_WARPS = 14;
   static constexpr int NT = 32 * (2 + 4 + NB_WARPS);
   static constexpr size_t off_ob = 0;
   static constexpr size_t off_stage = NOB * ob_bytes;
@@ -823,6 +823,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
           const int j0 = sub * J, n = min(J, h.nst - j0);
           const int fl = (sub == 0 ? (h.flags & kWsFirst) : 0) | (sub == nsub - 1 ? (h.flags & kWsLast) : 0);
           if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(n, fl, h.xy, 0);
+#pragma unroll 2
           for (int task = bt; task < 128 * KQ; task += NBT) {
             const int kq = (task >> 3) % KQ;
             const int m = (task / (8 * KQ)) * 8 + (task & 7);
@@ -850,6 +851,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
             *reinterpret_cast<float4*>(obuf + L::ob_ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
           }
+#pragma unroll 2
           for (int task = bt; task < N * KQ; task += NBT) {
             const int kq = (task >> 3) % KQ;
             const int nn = (task / (8 * KQ)) * 8 + (task & 7);
@@ -899,7 +901,9 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
 // Tensor-core configuration per exact support and pol count: the tile of first-tap positions
 // (window side S + TILE - 1 at or just below a multiple of 16, so that little of the padded window
 // is waste; it depends on S alone, the plan bins by it), samples per MMA chunk and per producer
-// stage, stages and operand buffers (as many as the shared memory holds).
+// stage, stages and operand buffers.  Two operand buffers cover the MMAs of a chunk (they take far
+// less time than building the next one); the rest of the shared memory goes to stages, whose
+// samples in flight hide the latency of the factor-row copies.
 struct MmaCfg {
   int S, P, tile, j, st, d, nob;
 };
@@ -907,12 +911,12 @@ struct MmaCfg {
 constexpr MmaCfg kMmaCfg[3] = {{64, 1, 9, 8, 32, 2, 3}, {64, 2, 9, 8, 32, 3, 2}, {64, 4, 9, 8, 16, 2, 2}};
 // pols in N (k_grid_mma_n): windows of side <= 64
 constexpr MmaCfg kMmaNCfg[21] = {
-    {8, 1, 9, 16, 32, 4, 4},   {8, 2, 9, 16, 32, 4, 4},   {8, 4, 9, 16, 32, 4, 4},   {16, 1, 17, 16, 32, 4, 4},
-    {16, 2, 17, 16, 32, 2, 4}, {16, 4, 17, 16, 32, 2, 3}, {24, 1, 9, 16, 32, 4, 4},  {24, 2, 9, 16, 32, 2, 4},
-    {24, 4, 9, 16, 32, 2, 3},  {32, 1, 17, 16, 32, 2, 4}, {32, 2, 17, 16, 32, 3, 3}, {32, 4, 17, 16, 32, 3, 2},
-    {40, 1, 9, 16, 32, 2, 4},  {40, 2, 9, 16, 32, 2, 3},  {40, 4, 9, 16, 32, 2, 2},  {48, 1, 17, 16, 32, 3, 3},
-    {48, 2, 17, 16, 32, 3, 2}, {48, 4, 17, 8, 32, 2, 3},  {56, 1, 9, 16, 32, 2, 3},  {56, 2, 9, 16, 32, 3, 2},
-    {56, 4, 9, 8, 32, 2, 3},
+    {8, 1, 9, 16, 32, 8, 2},   {8, 2, 9, 16, 32, 8, 2},   {8, 4, 9, 16, 32, 8, 2},   {16, 1, 17, 16, 32, 8, 2},
+    {16, 2, 17, 16, 32, 8, 2}, {16, 4, 17, 16, 32, 8, 2}, {24, 1, 9, 16, 32, 8, 2},  {24, 2, 9, 16, 32, 8, 2},
+    {24, 4, 9, 16, 32, 6, 2},  {32, 1, 17, 16, 32, 8, 2}, {32, 2, 17, 16, 32, 6, 2}, {32, 4, 17, 16, 32, 3, 2},
+    {40, 1, 9, 16, 32, 6, 2},  {40, 2, 9, 16, 32, 5, 2},  {40, 4, 9, 16, 32, 2, 2},  {48, 1, 17, 16, 32, 5, 2},
+    {48, 2, 17, 16, 32, 3, 2}, {48, 4, 17, 8, 32, 4, 2},  {56, 1, 9, 16, 32, 4, 2},  {56, 2, 9, 16, 32, 3, 2},
+    {56, 4, 9, 8, 32, 4, 2},
 };
 constexpr MmaCfg mma_cfg(int S, int P) {
   for (const MmaCfg& e : kMmaCfg)
