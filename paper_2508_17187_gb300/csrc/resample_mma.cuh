@@ -798,6 +798,20 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
     // in all eight bank groups.
     const int bt = tid - 6 * 32;
     constexpr int NBT = 32 * L::NB_WARPS;
+    // A rows (x, c) with x >= U are zero for every sample (first taps lie in [0, TILE)): written
+    // once here in every operand buffer and never again.  The MMA thread reads a buffer only after
+    // every builder warp has arrived on it, so these stores come first.
+    constexpr int AR = 2 * L::U;   // A rows that are built per chunk
+    static_assert(AR % 8 == 0, "A rows are built in groups of eight");
+    for (int b = 0; b < NOB; ++b) {
+      unsigned char* obuf = smem + L::off_ob + (size_t)b * L::ob_bytes;
+      for (int i = AR * KQ + bt; i < 128 * KQ; i += NBT) {
+        const int kq = i % KQ, m = i / KQ;
+        const size_t off = (size_t)(m % 8) * 16 + (size_t)(m / 8) * L::SBO + (size_t)kq * L::LBO;
+        *reinterpret_cast<float4*>(obuf + L::ob_ahi + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
     int q = 0;
     bool ok = true;
     for (int k = 0; ok; ++k) {
@@ -824,7 +838,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
           const int fl = (sub == 0 ? (h.flags & kWsFirst) : 0) | (sub == nsub - 1 ? (h.flags & kWsLast) : 0);
           if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(n, fl, h.xy, 0);
 #pragma unroll 2
-          for (int task = bt; task < 128 * KQ; task += NBT) {
+          for (int task = bt; task < AR * KQ; task += NBT) {
             const int kq = (task >> 3) % KQ;
             const int m = (task / (8 * KQ)) * 8 + (task & 7);
             const int x = m >> 1, c = m & 1;
