@@ -21,8 +21,8 @@
 // sqrt(770) 2^-23, a few 1e-6, whatever the flush mode.
 //
 // Roles (one persistent CTA per SM):
-//  * warp 0, the producer, stages up to 32 samples at a time (records, factor rows by TMA bulk
-//    copies, w V times the phasor) into a ring of stages, as in the warp-specialised kernels;
+//  * warp 0, the producer, stages up to 32 samples at a time (records, factor rows by cp.async or
+//    bulk copies, w V times the phasor) into a ring of stages;
 //  * the builder warps cut a stage into chunks of J samples and turn each chunk into the A and B
 //    operands (hi and lo parts) in the canonical no-swizzle K-major layout of the tensor cores, in
 //    a ring of operand buffers;
@@ -250,14 +250,29 @@ __device__ __forceinline__ void mma_flush2(float* grid, float* grid_lo, size_t e
 }
 
 
+// 16-byte asynchronous copy global -> shared (L2 only), completion tracked per thread.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// A producer lane's two arrivals on a stage's full barrier (count 64 for the warp): one now
+// (release of its plain shared-memory stores) and one when its cp.async copies have landed (at
+// once when it has none).  Bulk copies add their bytes to the transaction count instead.
+__device__ __forceinline__ void stage_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+  mbar_arrive(bar);
+}
+
 // The producer warp of the tensor-core gridding kernels: walks the CTA's items in stages of up to
-// ST samples (one per lane): first-tap offsets in the window, the fx and fy factor rows (TMA bulk
-// copies completing on the stage's full barrier), w V times the phasor per pol; a stage with
+// ST samples (one per lane): first-tap offsets in the window, the fx and fy factor rows (16-byte
+// cp.async pieces for short rows, one bulk copy per row for long ones, completing on the stage's
+// full barrier), w V times the phasor per pol; a stage with
 // nst = -1 ends the work.  Adds the CTA's share of the sum of weights.
 template <int S, int P, int TILE, int ST, int D, class L>
 __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, unsigned char* smem, uint64_t* full,
                                              uint64_t* empty, const int64_t* offs, volatile int* abort_flag,
                                              unsigned long long* err, const int lane) {
+  constexpr bool kRowsByPieces = S < 32;   // else one bulk copy per factor row
   double wsum[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) wsum[p] = 0.0;
@@ -281,14 +296,16 @@ __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, u
       ok = false;
       break;
     }
+    long long fxo = 0, fyo = 0;
     if (lane < d0.nst) {
       const int X0 = d0.xy & 0xffff, Y0 = d0.xy >> 16;
       reinterpret_cast<int*>(sg + L::st_pk)[lane] = (r0.p0x - X0) | ((r0.p0y - Y0) << 8);
-      long long fxo, fyo;
       ws_rows<S>(offs, a.cf_shift, a.OS, r0, fxo, fyo);
-      fence_proxy_async_smem();
-      bulk_load(sg + L::st_fx + (size_t)lane * S * 8, sep2 + fxo, S * 8, full + s);
-      bulk_load(sg + L::st_fy + (size_t)lane * S * 8, sep2 + fyo, S * 8, full + s);
+      if constexpr (!kRowsByPieces) {
+        fence_proxy_async_smem();
+        bulk_load(sg + L::st_fx + (size_t)lane * S * 8, sep2 + fxo, S * 8, full + s);
+        bulk_load(sg + L::st_fy + (size_t)lane * S * 8, sep2 + fyo, S * 8, full + s);
+      }
       float2* dst = reinterpret_cast<float2*>(sg + L::st_wv) + lane * P;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
@@ -300,10 +317,30 @@ __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, u
         for (int p = 0; p < P; ++p) wsum[p] += (double)x0.w[p];
       }
     }
+    // short factor rows: 16-byte pieces spread over the lanes (one bulk copy per short row leaves
+    // this one warp issue-bound on the copies); each piece takes its row's source offset from the
+    // lane that holds the sample
+    constexpr int HP = S / 2;   // 16-byte pieces per row
+    const int npieces = kRowsByPieces ? d0.nst * HP : 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const long long mine = r ? fyo : fxo;
+      unsigned char* dstb = sg + (r ? L::st_fy : L::st_fx);
+      for (int id0 = 0; id0 < npieces; id0 += 32) {
+        const int id = id0 + lane;
+        const int j = id / HP;
+        const long long src = __shfl_sync(0xffffffffu, mine, j < 32 ? j : 31);
+        if (id < npieces) cp_async16(dstb + (size_t)j * S * 8 + 16 * (id - j * HP), sep2 + src + 2 * (id - j * HP));
+      }
+    }
     if (lane == 0) *reinterpret_cast<WsHeader*>(sg) = WsHeader{d0.nst, d0.flags, d0.xy, 0};
     if (!(a.withhold && k == 0)) {
-      if (lane == 0) mbar_arrive_expect_tx(full + s, (unsigned)(d0.nst * 2 * S * 8));
-      else mbar_arrive(full + s);
+      if (!kRowsByPieces && lane == 0) {
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full + s)) : "memory");
+        mbar_arrive_expect_tx(full + s, (unsigned)(d0.nst * 2 * S * 8));
+      } else {
+        stage_arrive(full + s);
+      }
     }
     const WsChunk d3 = walk.next();
     const SampleRec r3 = ws_load_rec(a.rec, d3, lane);
@@ -321,8 +358,9 @@ __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, u
   if (ok && warp_wait(empty + k % D, ((k / D) & 1) ^ 1, abort_flag, err)) {
     if (lane == 0) *reinterpret_cast<WsHeader*>(smem + L::off_stage + (size_t)(k % D) * L::stage_bytes) =
         WsHeader{-1, 0, 0, 0};
-    mbar_arrive(full + k % D);
+    stage_arrive(full + k % D);
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");   // no copy of this warp outlives the CTA
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     double v = wsum[p];
@@ -358,7 +396,7 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, ST, D, NOB>::NT, 
   const int64_t* offs = off_cached ? s_off : a.sep_off;
   if (tid == 0) {
     for (int d = 0; d < D; ++d) {
-      mbar_init(full + d, 32);
+      mbar_init(full + d, 64);   // the producer lanes, then their copies
       mbar_init(empty + d, L::NB_WARPS);
     }
     for (int b = 0; b < NOB; ++b) {
@@ -651,7 +689,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
   const int64_t* offs = off_cached ? s_off : a.sep_off;
   if (tid == 0) {
     for (int d = 0; d < D; ++d) {
-      mbar_init(full + d, 32);
+      mbar_init(full + d, 64);   // the producer lanes, then their copies
       mbar_init(empty + d, L::NB_WARPS);
     }
     for (int b = 0; b < NOB; ++b) {
