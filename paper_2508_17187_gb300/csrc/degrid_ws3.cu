@@ -1,8 +1,7 @@
 // Instantiations of the warp-specialised degridding kernels with the tiles of candidate 3 (the
-// tensor-core gridding configuration), all exact supports.
+// tensor-core configuration) for the supports whose windows are wider than one tensor-core tile.
 #include "resample_ws.cuh"
 
 namespace awg {
-AWG_FOR_WS_A(AWG_INSTANTIATE_DEGRID_WS3)
-AWG_FOR_WS_B(AWG_INSTANTIATE_DEGRID_WS3)
+AWG_FOR_WS3(AWG_INSTANTIATE_DEGRID_WS3)
 }  // namespace awg

@@ -6,7 +6,7 @@
 #include <atomic>
 #include <mutex>
 
-#include "resample_mma.cuh"
+#include "resample_mma_dg.cuh"
 
 namespace awg {
 
@@ -26,8 +26,9 @@ AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_GRID_EXACT, 3)
 AWG_FOR_EXACT_AND_POLS(AWG_DECLARE_DEGRID_EXACT, 3)
 AWG_FOR_WS_A(AWG_DECLARE_GRID_MMA)
 AWG_FOR_WS_B(AWG_DECLARE_GRID_MMA)
-AWG_FOR_WS_A(AWG_DECLARE_DEGRID_WS3)
-AWG_FOR_WS_B(AWG_DECLARE_DEGRID_WS3)
+AWG_FOR_WS3(AWG_DECLARE_DEGRID_WS3)
+AWG_FOR_MMA_DG_A(AWG_DECLARE_DEGRID_MMA)
+AWG_FOR_MMA_DG_B(AWG_DECLARE_DEGRID_MMA)
 AWG_FOR_WS_A(AWG_DECLARE_GRID_WS)
 AWG_FOR_WS_B(AWG_DECLARE_GRID_WS)
 AWG_FOR_WS_A(AWG_DECLARE_DEGRID_WS)
@@ -166,11 +167,15 @@ awg_status degrid_slot_sep(int S, int cand, int slot, int P, const DegridArgs& a
       AWG_FOR_WS_B(AWG_CASE)
 #undef AWG_CASE
     }
-    if (cand == 3 && ws_degrid_ok(a, P)) {
+    if (cand == 3 && ws_degrid_ok(a, P)) {   // tensor cores where the window fits one tile row
+#define AWG_CASE(SS, PP) \
+  if (S == SS && P == PP) return run_degrid_mma<SS, PP>(a, slot, sms, st);
+      AWG_FOR_MMA_DG_A(AWG_CASE)
+      AWG_FOR_MMA_DG_B(AWG_CASE)
+#undef AWG_CASE
 #define AWG_CASE(SS, PP) \
   if (S == SS && P == PP) return run_degrid_ws<SS, PP, 3>(a, slot, sms, st);
-      AWG_FOR_WS_A(AWG_CASE)
-      AWG_FOR_WS_B(AWG_CASE)
+      AWG_FOR_WS3(AWG_CASE)
 #undef AWG_CASE
     }
 #define AWG_CASE(SS, PP, CC) \
@@ -296,18 +301,18 @@ static EncodeTiledFn encode_tiled_fn() {
   return fn;
 }
 
-// The grid c64 [N][N][P] as a TMA tensor of FP32 values whose box is one U x U window: P >= 2 a
-// 3-D tensor (2P values of a pixel, x, y) with box (2P, U, U); P = 1 a 2-D tensor (2N values of a
-// row, y) with box (2 UB, U), UB = U rounded up to even, so that a box row is a whole number of
-// 16-byte units.  Out-of-grid parts of a box read as zero.
-awg_status make_grid_tensor_map(CUtensorMap* map, const void* grid, int N, int P, int U, int UB) {
+// The grid c64 [N][N][P] as a TMA tensor of FP32 values whose box is `rows` rows of a window U
+// pixels wide: P >= 2 a 3-D tensor (2P values of a pixel, x, y) with box (2P, U, rows); P = 1 a
+// 2-D tensor (2N values of a row, y) with box (2 UB, rows), UB even, so that a box row is a whole
+// number of 16-byte units.  Out-of-grid parts of a box read as zero.
+awg_status make_grid_tensor_map(CUtensorMap* map, const void* grid, int N, int P, int U, int UB, int rows) {
   EncodeTiledFn enc = encode_tiled_fn();
   if (!enc) return set_error(AWG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   CUresult r;
   if (P >= 2) {
     const cuuint64_t dims[3] = {(cuuint64_t)(2 * P), (cuuint64_t)N, (cuuint64_t)N};
     const cuuint64_t strides[2] = {(cuuint64_t)(2 * P * 4), (cuuint64_t)N * 2 * P * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)(2 * P), (cuuint32_t)U, (cuuint32_t)U};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * P), (cuuint32_t)U, (cuuint32_t)rows};
     const cuuint32_t es[3] = {1, 1, 1};
     r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(grid), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -315,7 +320,7 @@ awg_status make_grid_tensor_map(CUtensorMap* map, const void* grid, int N, int P
   } else {
     const cuuint64_t dims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)N};
     const cuuint64_t strides[1] = {(cuuint64_t)N * 2 * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * UB), (cuuint32_t)U};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * UB), (cuuint32_t)rows};
     const cuuint32_t es[2] = {1, 1};
     r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(grid), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

@@ -891,7 +891,7 @@ awg_status run_grid_ws(const GridArgs& a, int slot, int sms, cudaStream_t st) {
 }
 
 // The tensor map of the grid for the degridding windows (built by the caller, see launch.cu).
-awg_status make_grid_tensor_map(CUtensorMap* map, const void* grid, int N, int P, int U, int UB);
+awg_status make_grid_tensor_map(CUtensorMap* map, const void* grid, int N, int P, int U, int UB, int rows);
 
 template <int S, int P, int C = 2>
 awg_status run_degrid_ws(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
@@ -907,7 +907,7 @@ awg_status run_degrid_ws(const DegridArgs& a, int slot, int sms, cudaStream_t st
     if (bps < 1) return set_error(AWG_ERR_CUDA, "warp-specialised degridding kernel does not fit on an SM");
   }
   CUtensorMap map;
-  awg_status s = make_grid_tensor_map(&map, a.grid, a.N, P, L::U, L::UB);
+  awg_status s = make_grid_tensor_map(&map, a.grid, a.N, P, L::U, L::UB, L::U);
   if (s != AWG_OK) return s;
   kern<<<sms * bps, L::NT, L::alloc, st>>>(a, slot, map);
   AWG_CUDA_TRY(cudaGetLastError());
@@ -918,6 +918,8 @@ awg_status run_degrid_ws(const DegridArgs& a, int slot, int sms, cudaStream_t st
 // Supports and pol counts of the warp-specialised kernels, in two halves (two translation units each).
 #define AWG_FOR_WS_A(M) M(8, 1) M(8, 2) M(8, 4) M(16, 1) M(16, 2) M(16, 4) M(24, 1) M(24, 2) M(24, 4) M(32, 1) M(32, 2) M(32, 4)
 #define AWG_FOR_WS_B(M) M(40, 1) M(40, 2) M(40, 4) M(48, 1) M(48, 2) M(48, 4) M(56, 1) M(56, 2) M(56, 4) M(64, 1) M(64, 2) M(64, 4)
+// supports whose candidate-3 windows are wider than 64 (degridding on the warp-specialised kernel)
+#define AWG_FOR_WS3(M) M(64, 1) M(64, 2) M(64, 4)
 #define AWG_DECLARE_GRID_WS(S, P) extern template awg_status run_grid_ws<S, P, 2>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_DECLARE_DEGRID_WS(S, P) \
   extern template awg_status run_degrid_ws<S, P, 2>(const DegridArgs&, int, int, cudaStream_t);

@@ -1,8 +1,9 @@
 """The warp-specialised kernels (configuration 2: a producer warp stages chunks into a ring of
 shared-memory stages handed over on mbarriers, consumer warps multiply and add; degridding loads
 each item's grid window with one TMA tile copy and a reduce warp finishes the sums) and the
-tensor-core gridding (configuration 3: each item's window as a 3xTF32 tcgen05 product of operands
-built per chunk, accumulated in tensor memory; degridding by the warp-specialised kernel) against
+tensor-core kernels (configuration 3: each item's window as a 3xTF32 tcgen05 product of operands
+built per chunk, accumulated in tensor memory; degridding as a tcgen05 product of the samples' y
+factors with TMA-loaded window slices, reduced over x in the epilogue) against
 the FP64 oracle on W-projection workloads: every exact support, 1, 2 and 4 pols, the flush modes, a
 phase shift, plan reuse across calls, and the bounded waits reporting a withheld hand-over as
 AWG_ERR_TIMEOUT.  Gates as in test_gpu_parity (1e-5 relative RMS)."""
@@ -151,7 +152,7 @@ def test_ws_phase_shift(awg, config):
     assert rel_rms(out.cpu().numpy().reshape(n, P), d_o) < 1e-5
 
 
-@pytest.mark.parametrize("op_name,config", [("grid", 2), ("degrid", 2), ("grid", 3)])
+@pytest.mark.parametrize("op_name,config", [("grid", 2), ("degrid", 2), ("grid", 3), ("degrid", 3)])
 def test_ws_withheld_handover_times_out_and_context_survives(awg, op_name, config):
     """awg_debug_ws_withhold: the producer of every CTA withholds its first hand-over; the consumers'
     bounded waits give up (2 s), the launch ends, plan_check reports AWG_ERR_TIMEOUT, and the next
