@@ -61,7 +61,10 @@ def parse():
                     help="with --config awproj: full-polarisation A-terms (sparse Mueller CFs; 4 PA bins x 4 "
                          "sub-bands so that the 12-element CF set builds in seconds)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default kernel configuration of every support instead of timing both")
+                    help="keep the default kernel configuration of every support instead of timing them all")
+    ap.add_argument("--kernel-config", default=None, metavar="S:C,...",
+                    help="fix the kernel configuration C (0-3) of support S instead of autotuning, e.g. to "
+                         "profile a reduced workload with the kernels the full one tunes to")
     ap.add_argument("--minor-cycle", action="store_true",
                     help="time the Hogbom minor cycle on a 4096^2 image (one JSON line, HBM roofline)")
     ap.add_argument("--calibrate", action="store_true",
@@ -877,7 +880,13 @@ def main():
     chan_sb = torch.as_tensor(wl.chan_subband, device=dev) if wl.use_a else None
     vis, wt = wl.vis, wl.weight
     tuned, t_tune, tune_ms = None, None, None
-    if not args.no_autotune:
+    if args.kernel_config:
+        tuned = {}
+        for item in args.kernel_config.split(","):
+            sup, kcfg = (int(v) for v in item.split(":"))
+            cf.choose(sup, kcfg)
+            tuned[str(sup)] = kcfg
+    elif not args.no_autotune:
         t_tune = time.perf_counter()
         tuned, tune_ms = cf.autotune(uvw, freq, pa_bin, chan_sb, n_pol=wl.n_pol)
         tune_ms = {S: [round(t, 3) for t in v] for S, v in tune_ms.items()}
@@ -1122,7 +1131,11 @@ def main():
                                    f"({fma['launches']} launches of {fma['launch_ms']:.0f} ms)",
                      "peak_burst": fma["burst_tflops"],
                      "peak_nominal": nominal_tf,
-                     "peak_nominal_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)"},
+                     "peak_nominal_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)",
+                     "note": "achieved = the method's FLOP (8 P sum S^2 per operator) over the operator's time, against "
+                             "the FP32 FMA pipe; supports on configuration 3 run the product on the tensor cores "
+                             "(3xTF32 splits of padded windows: several times the method's FLOP on the tensor pipe)",
+                     "kernel_config_per_support": tuned},
         "clocks": {k: cs[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "gpu_launches": int(launches),
         "e2e": e2e,
