@@ -591,6 +591,9 @@ def forward_model_bench(args):
     vis, wt = wl.vis, wl.weight
     cf = awg.cf_set_create(**cf_kwargs(wl))
     uvw, freq = torch.as_tensor(wl.uvw_m, device="cuda"), torch.as_tensor(wl.freq_hz, device="cuda")
+    tuned = None
+    if not args.no_autotune:
+        tuned, _ = cf.autotune(uvw, freq, n_pol=P)
     plan = awg.plan_create(cf, uvw, freq)
     kept, dropped, sum_taps = plan.stats()
     fm = ag.ForwardModel(cf, plan, n_pol=P)
@@ -677,7 +680,9 @@ def forward_model_bench(args):
                                    f"{P} pol), W-projection supports 8-{wl.max_support}; one step = {n_cycles} "
                                    "major cycles (2 D + 1 G each)",
                        "kept_samples": kept, "dropped_samples": dropped, "mean_taps": sum_taps / max(kept, 1),
-                       "step_size": gain, "l2": "flushed: a 256 MB write before every timed repetition"},
+                       "step_size": gain, "l2": "flushed: a 256 MB write before every timed repetition",
+                       "kernel_config_per_support": tuned,
+                       "residual": "formed by degridding in place (AWG_DEGRID_SUBTRACT)"},
             "visibilities_per_s": vis_per_step / (ms / 1e3),
             "ms_per_major_cycle": ms / n_cycles,
             "gradient_ms": grad_ms,

@@ -57,6 +57,11 @@ enum {
   AWG_GRID_FP64 = 2   /* grid (and grid_lo unused) is complex128 [N][N][P]; flush adds in FP64 */
 };
 
+/* degrid_visibilities flags. */
+enum {
+  AWG_DEGRID_SUBTRACT = 1 /* residual: vis_out holds V on entry and receives V - D(grid) */
+};
+
 /*
  * Parameters of a CF set (Tab. AWP-CFSETUP switches plus the imaging geometry).
  * CF index: cf = (pa_bin * n_subbands + subband) * n_signed + ks, with n_signed = 2 n_wplanes - 1
@@ -314,7 +319,11 @@ awg_status grid_visibilities(awg_cf_set cf, awg_plan plan, const void* vis, cons
  * Degridding D (Eq. ME-MOD-GRIDDED, Eq. VMod): for every sample s and pol p,
  *   vis_out[s][p] = sum_{ty,tx} CF_cf[oy][ox][ty][tx] * grid[p0y+ty][p0x+tx][p] (* conj(phasor)),
  * overwritten; dropped samples get 0.  grid: device c64 [N][N][P]; vis_out: device c64 [R][C][P].
- * D is the adjoint of G with unit weights: <G V, X> = <V, D X>.  Errors: INVALID_ARG, CUDA.
+ * With flags = AWG_DEGRID_SUBTRACT the call forms the residual of Eq. ResIm in place: vis_out
+ * holds the observed visibilities on entry and each kept sample receives vis_out - D(grid), the
+ * difference taken where the model value is formed (no second pass over the visibilities);
+ * dropped samples keep their input.  D is the adjoint of G with unit weights: <G V, X> = <V, D X>.
+ * Errors: INVALID_ARG (including unknown flags), CUDA.
  */
 awg_status degrid_visibilities(awg_cf_set cf, awg_plan plan, const void* grid, void* vis_out,
                                int32_t n_pol, int32_t flags, void* stream);

@@ -14,6 +14,7 @@ STATUS_NAMES = {0: "AWG_OK", 1: "AWG_ERR_INVALID_ARG", 2: "AWG_ERR_UNSUPPORTED",
                 4: "AWG_ERR_CUDA", 5: "AWG_ERR_TIMEOUT"}
 AWG_CF_FP32, AWG_CF_BF16 = 0, 1
 AWG_GRID_KAHAN, AWG_GRID_FP64 = 1, 2
+AWG_DEGRID_SUBTRACT = 1
 
 EXPORTED = ["cf_set_create", "cf_set_create_from_table", "cf_set_destroy", "cf_set_info", "cf_set_fused_terms", "cf_set_get_params", "cf_set_save", "cf_set_load",
             "cf_set_get_supports",

@@ -10,11 +10,12 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import AWG_CF_BF16, AWG_CF_FP32, AWG_GRID_FP64, AWG_GRID_KAHAN, CfParams, check
+from ._lib import AWG_CF_BF16, AWG_CF_FP32, AWG_DEGRID_SUBTRACT, AWG_GRID_FP64, AWG_GRID_KAHAN, CfParams, check
 
 __all__ = ["CFSet", "Plan", "CleanWorkspace", "cf_set_create", "cf_set_create_from_table", "plan_create",
            "clean_hogbom", "gcal_solve", "grid_visibilities",
-           "degrid_visibilities", "grid_normalize", "AWG_CF_FP32", "AWG_CF_BF16", "AWG_GRID_KAHAN", "AWG_GRID_FP64"]
+           "degrid_visibilities", "grid_normalize", "AWG_CF_FP32", "AWG_CF_BF16", "AWG_GRID_KAHAN", "AWG_GRID_FP64",
+           "AWG_DEGRID_SUBTRACT"]
 
 
 def _stream_ptr(stream) -> ctypes.c_void_p:
@@ -332,14 +333,18 @@ def grid_visibilities(cf: CFSet, plan: Plan, vis: torch.Tensor, weight: torch.Te
                                         _ptr(sumwt), int(flags), _stream_ptr(stream)), "grid_visibilities")
 
 
-def degrid_visibilities(cf: CFSet, plan: Plan, grid: torch.Tensor, vis_out: torch.Tensor, stream=None):
-    """D (Eq. ME-MOD-GRIDDED): vis_out = sum CF * grid (overwritten; dropped samples get 0)."""
+def degrid_visibilities(cf: CFSet, plan: Plan, grid: torch.Tensor, vis_out: torch.Tensor, stream=None,
+                        subtract: bool = False):
+    """D (Eq. ME-MOD-GRIDDED): vis_out = sum CF * grid (overwritten; dropped samples get 0).  With
+    subtract, vis_out holds the observed visibilities and receives the residual V - D(grid) of Eq.
+    ResIm in place (dropped samples keep their input)."""
     R, C = plan.n_rows, plan.n_chan
     P = _pols(grid)
     N = cf.grid_n
     _need(grid, "grid", torch.complex64, (N, N, P))
     _need(vis_out, "vis_out", torch.complex64, (R, C, P))
-    check(_lib.load().degrid_visibilities(cf.handle, plan.handle, _ptr(grid), _ptr(vis_out), P, 0,
+    flags = AWG_DEGRID_SUBTRACT if subtract else 0
+    check(_lib.load().degrid_visibilities(cf.handle, plan.handle, _ptr(grid), _ptr(vis_out), P, flags,
                                           _stream_ptr(stream)), "degrid_visibilities")
 
 

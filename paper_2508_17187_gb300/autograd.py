@@ -76,10 +76,12 @@ def chi2(model_vis: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor) -> to
 
 
 def residual_image(fm: ForwardModel, image: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor) -> torch.Tensor:
-    """Eq. ResIm for one partition: F^H G W (V - D F I), normalised by the weights and the taper."""
+    """Eq. ResIm for one partition: F^H G W (V - D F I), normalised by the weights and the taper.
+    The residual V - D F I is formed by the degridding itself (AWG_DEGRID_SUBTRACT), in one pass."""
     cf, plan = fm.cf, fm.plan
     N, P = cf.grid_n, fm.P
-    res = (vis - fm(image)).contiguous()
+    res = vis.contiguous().clone()
+    api.degrid_visibilities(cf, plan, image_to_grid(image, fm.inv_taper2d).contiguous(), res, subtract=True)
     g = torch.zeros((N, N, P), dtype=torch.complex64, device=vis.device)
     sw = torch.zeros(P, dtype=torch.float64, device=vis.device)
     api.grid_visibilities(cf, plan, res, weight, g, sw)

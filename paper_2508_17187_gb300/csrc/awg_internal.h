@@ -267,8 +267,9 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
 // Compute launches (grid.cu, degrid.cu, normalize.cu).
 awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float* weight, int P,
                        void* grid, void* grid_lo, double* sumwt, int flags, cudaStream_t st);
+// subtract: vis_out -= D(grid) for kept samples, dropped samples untouched (AWG_DEGRID_SUBTRACT).
 awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vis_out, int P,
-                         cudaStream_t st);
+                         cudaStream_t st, bool subtract = false);
 // Times every candidate of the exact-support kernels on a plan of the given geometry (unit data)
 // and keeps the fastest per support in cf->cand; choice[S] = the pick or -1, ms_out (optional)
 // [kNumCand][kMaxSupport + 1] the grid + degrid milliseconds of each.

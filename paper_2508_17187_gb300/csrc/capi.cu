@@ -1179,9 +1179,10 @@ awg_status degrid_visibilities(awg_cf_set hc, awg_plan hp, const void* grid, voi
   PlanImpl* pl = (PlanImpl*)hp;
   if (pl->cf != cf) return set_error(AWG_ERR_INVALID_ARG, "plan was made for another cf set");
   if (n_pol != 1 && n_pol != 2 && n_pol != 4) return set_error(AWG_ERR_INVALID_ARG, "n_pol must be 1, 2 or 4");
-  if (flags != 0) return set_error(AWG_ERR_INVALID_ARG, "degrid_visibilities takes no flags");
+  if ((flags & ~AWG_DEGRID_SUBTRACT) != 0)
+    return set_error(AWG_ERR_INVALID_ARG, "degrid_visibilities flags: 0 or AWG_DEGRID_SUBTRACT");
   if (!grid || (pl->n > 0 && !vis_out)) return set_error(AWG_ERR_INVALID_ARG, "grid and vis_out must not be NULL");
-  return launch_degrid(cf, pl, grid, vis_out, n_pol, (cudaStream_t)stream);
+  return launch_degrid(cf, pl, grid, vis_out, n_pol, (cudaStream_t)stream, (flags & AWG_DEGRID_SUBTRACT) != 0);
 }
 
 awg_status grid_normalize(awg_cf_set hc, void* image, int32_t n_pol, const double* sumwt, int32_t direction,

@@ -258,7 +258,8 @@ __global__ void k_zero_dropped(const int32_t* __restrict__ drop, const unsigned 
 }
 
 // vis_out[s] = sum over the rank terms of sample s (the CF's outer-product terms); pol p of sample
-// s lands at s ostride + ooff + p, added to what is there when accumulate is set.
+// s lands at s ostride + ooff + p, added to (accumulate 1) or subtracted from (accumulate -1) what
+// is there.
 __global__ void k_sum_terms(const float2* __restrict__ part, float2* __restrict__ vis_out, int64_t n, int rank,
                             int P, int ostride, int ooff, int accumulate) {
   const int64_t total = n * P;
@@ -275,8 +276,7 @@ __global__ void k_sum_terms(const float2* __restrict__ part, float2* __restrict_
     float2* o = vis_out + s * ostride + ooff + p;
     if (accumulate) {
       const float2 prev = *o;
-      acc.x += prev.x;
-      acc.y += prev.y;
+      acc = accumulate > 0 ? make_float2(prev.x + acc.x, prev.y + acc.y) : make_float2(prev.x - acc.x, prev.y - acc.y);
     }
     *o = acc;
   }
@@ -478,19 +478,21 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
 }
 
 // Per-term values summed, then dropped samples zeroed (after the kernels of launch_degrid).
-static awg_status degrid_finish(PlanImpl* pl, void* vis_out, int P, int sms, cudaStream_t st) {
+static awg_status degrid_finish(PlanImpl* pl, void* vis_out, int P, int sms, cudaStream_t st, bool subtract) {
   if (pl->rank > 1) {   // dropped samples' rows are stale here and are zeroed next
-    k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, P, P, 0, 0);
+    k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, P, P, 0, subtract ? -1 : 0);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   }
+  if (subtract) return AWG_OK;   // dropped samples keep their input
   k_zero_dropped<<<sms * 4, 256, 0, st>>>(pl->d_drop, pl->d_counters, (float*)vis_out, P);
   AWG_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return AWG_OK;
 }
 
-awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vis_out, int P, cudaStream_t st) {
+awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vis_out, int P, cudaStream_t st,
+                         bool subtract) {
   if (cudaSetDevice(pl->device) != cudaSuccess) return set_error(AWG_ERR_CUDA, "cudaSetDevice failed");
   awg_status s = check_version(cf, pl);
   if (s != AWG_OK) return s;
@@ -498,13 +500,14 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
   if (pl->n == 0) return AWG_OK;
   DegridArgs a = degrid_args(cf, pl, grid, vis_out, P);
   a.withhold = g_ws_withhold.exchange(0);
+  if (subtract && pl->rank == 1) a.accumulate = -1;   // rank > 1: the per-term sums subtract
   const int sms = sm_count(pl->device);
   const bool bf16 = cf->p.cf_dtype == AWG_CF_BF16;
   if (cf->n_mb > 1 && cf->mb_elements) {
     // full-polarisation set stored per element: vis pol p = sum over elements (p, q) of CF_pq
     // applied to grid pol q; dropped samples keep the zeros written first
     if (P != 4) return set_error(AWG_ERR_INVALID_ARG, "a full-polarisation CF set needs 4 pols");
-    AWG_CUDA_TRY(cudaMemsetAsync(vis_out, 0, sizeof(float2) * 4 * (size_t)pl->n, st));
+    if (!subtract) AWG_CUDA_TRY(cudaMemsetAsync(vis_out, 0, sizeof(float2) * 4 * (size_t)pl->n, st));
     for (int e = 0; e < cf->n_elem; ++e) {
       DegridArgs ae = a;
       ae.cf_shift = (int64_t)e * cf->n_base * pl->rank;
@@ -519,7 +522,7 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
         ae.vis_out = (float*)vis_out;
         ae.vstride = 4;
         ae.voff = cf->elem_p[e];
-        ae.accumulate = 1;
+        ae.accumulate = subtract ? -1 : 1;
       }
       AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
       for (int i = cf->slots.n - 1; i >= 0; --i) {
@@ -527,13 +530,15 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
         if (s != AWG_OK) return s;
       }
       if (pl->rank > 1) {
-        k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, 1, 4, cf->elem_p[e], 1);
+        k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, 1, 4, cf->elem_p[e],
+                                             subtract ? -1 : 1);
         AWG_CUDA_TRY(cudaGetLastError());
         count_launches(1);
       }
     }
     // rows of dropped samples were never written by the kernels, but the sums above added their
-    // stale per-term rows: zero them again
+    // stale per-term rows: zero them again (with subtract they keep their input)
+    if (subtract) return AWG_OK;
     k_zero_dropped<<<sms * 4, 256, 0, st>>>(pl->d_drop, pl->d_counters, (float*)vis_out, 4);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
@@ -566,7 +571,7 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
       }
     }
   }
-  return degrid_finish(pl, vis_out, P, sms, st);
+  return degrid_finish(pl, vis_out, P, sms, st, subtract);
 }
 
 __global__ void k_fill_ones(float* vis, float* weight, int64_t n_vis) {

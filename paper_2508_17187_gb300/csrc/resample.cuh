@@ -84,7 +84,7 @@ struct DegridArgs {
   int rank;              // records per sample (term k of sample s writes vis_out row s * rank + k)
   int64_t cf_shift;      // as in GridArgs; the output row r goes to vis_out at r vstride + voff,
   int vstride, voff, gstride, goff;
-  int accumulate;        // 1: add to vis_out instead of writing it
+  int accumulate;        // 0: write vis_out, 1: add to it, -1: subtract from it (residuals)
   // Full-polarisation base passes (fused separable kernels, P = 4): with Y_q the CF applied to
   // grid pol q, output pol p = sum_q mix[4 p + q] Y_q when mix != NULL (else Y_p); only the pols
   // set in pmask are written.
@@ -474,7 +474,8 @@ __global__ void __launch_bounds__(NT) k_degrid(const DegridArgs a, const int cls
           if (j < nst) {
             const float2 ph = s_ph[j];   // multiply by conj(phasor)
             const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
-            a.vis_out[(size_t)s_src[j] * 2 * P + comp] = out;
+            float* o = a.vis_out + (size_t)s_src[j] * 2 * P + comp;
+            *o = a.accumulate == 0 ? out : a.accumulate > 0 ? *o + out : *o - out;
           }
         }
         buf ^= 1;

@@ -383,9 +383,12 @@ __global__ void __launch_bounds__(MmaDgLayout<S, P, TILE, KY, D, NZ, NOB>::NT, 1
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const float orr = vr[p] * ph.x + vi[p] * ph.y, oi = vi[p] * ph.x - vr[p] * ph.y;   // V conj(ph)
-          if (a.accumulate) {
+          if (a.accumulate > 0) {
             o[2 * p] += orr;
             o[2 * p + 1] += oi;
+          } else if (a.accumulate < 0) {   // residual: V - D(grid)
+            o[2 * p] -= orr;
+            o[2 * p + 1] -= oi;
           } else {
             o[2 * p] = orr;
             o[2 * p + 1] = oi;

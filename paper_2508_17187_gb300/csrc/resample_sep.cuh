@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
                 const float2 ph = cap_ph[q];
                 const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
                 float* o = a.vis_out + ((size_t)cap_src[q] * a.vstride + a.voff) * 2 + comp;
-                *o = a.accumulate ? *o + out : out;
+                *o = a.accumulate == 0 ? out : a.accumulate > 0 ? *o + out : *o - out;
               }
             } else {
               const float2 ph = cap_ph[q];
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(NT, sep_min_blocks(SepLayout<SMAX, TILE, P, ST
               }
               if (cap_src[q] >= 0 && ((a.pmask >> (comp >> 1)) & 1)) {
                 float* o = a.vis_out + ((size_t)cap_src[q] * a.vstride + a.voff) * 2 + comp;
-                *o = a.accumulate ? *o + out : out;
+                *o = a.accumulate == 0 ? out : a.accumulate > 0 ? *o + out : *o - out;
               }
             }
           }

@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(WsDegridLayout<S, P, G, TILE, ST, D, NWIN>::NT
           const float2 ph = phv[j];
           const float out = (comp & 1) ? (v * ph.x - partner * ph.y) : (v * ph.x + partner * ph.y);
           float* o = a.vis_out + ((size_t)srcv[j] * a.vstride + a.voff) * 2 + comp;
-          *o = a.accumulate ? *o + out : out;
+          *o = a.accumulate == 0 ? out : a.accumulate > 0 ? *o + out : *o - out;
         }
       }
       mbar_arrive(empty + k % D);
