@@ -12,13 +12,13 @@
 // pixels (UX: a multiple of 128 / 2P so that the rows fill 128-row MMA tiles; UN: a multiple of
 // 16); the padding is zero work that the tensor cores do anyway.
 //
-// Precision: the operands are FP32 values split into a TF32 head and a TF32 remainder (both
-// rounded to nearest); each k-step runs A_lo B_hi + A_hi B_lo + A_hi B_hi (the 3xTF32 scheme),
-// which keeps the relative error of a product near 2^-22 (the dropped A_lo B_lo term and the
-// remainders' rounding).  The sum over an item's samples runs in the FP32 accumulator of the
-// tensor memory, one accumulation per MMA (3 K/8 per chunk): over an item of 1024 samples that
-// is about 770 additions, whose rounding puts the relative RMS error of a window near
-// sqrt(770) 2^-23, a few 1e-6, whatever the flush mode.
+// Precision: the operands are FP32 values split into a TF32 head (rounded to nearest) and the FP32
+// remainder, which the tensor cores truncate to TF32; each k-step runs A_lo B_hi + A_hi B_lo +
+// A_hi B_hi (the 3xTF32 scheme), which keeps the relative error of a product near 2^-21 (the
+// dropped A_lo B_lo term and the remainders' truncation).  The sum over an item's samples runs in
+// the FP32 accumulator of the tensor memory, one accumulation per MMA (3 K/8 per chunk): over an
+// item of 1024 samples that is about 770 additions, whose rounding puts the relative RMS error of
+// a window near sqrt(770) 2^-23, a few 1e-6, whatever the flush mode.
 //
 // Roles (one persistent CTA per SM):
 //  * warp 0, the producer, stages up to 32 samples at a time (records, factor rows by cp.async or
@@ -91,14 +91,14 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// TF32 head of x and of the remainder x - head, both rounded to nearest (the tensor cores would
-// otherwise truncate the remainder's low 13 bits).
+// TF32 head of x and the FP32 remainder x - head.  TF32 keeps the sign, the 8 exponent bits and the
+// top 10 mantissa bits of an FP32 value: adding half a unit of the 11th mantissa bit to the bit
+// pattern and clearing the low 13 bits rounds the magnitude to nearest, ties away from zero
+// (a carry into the exponent is the correct result), on the integer pipe rather than through a
+// conversion.  The tensor cores read the remainder's top 19 bits (truncation: below 2^-21 of x).
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  unsigned h, l;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  hi = __uint_as_float(h);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
-  lo = __uint_as_float(l);
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+  lo = x - hi;
 }
 
 // ------------------------------------------------------------------------------------- layout
@@ -134,9 +134,12 @@ struct MmaGridLayout {
   static constexpr size_t ob_bytes = ws_al1k(ob_hdr + 16);
   // producer stage: header, first-tap offsets, fy rows, fx rows, w V (times the phasor) per pol
   static constexpr size_t st_pk = 16;
+  // staged factor rows RS = S + 2 values apart: the rows of consecutive samples start 8 banks apart,
+  // so that the builders' reads of several samples' rows do not collide (rows stay 16-byte aligned)
+  static constexpr int RS = S + 2;
   static constexpr size_t st_fy = st_pk + ws_al16(4 * ST);
-  static constexpr size_t st_fx = st_fy + (size_t)ST * S * 8;
-  static constexpr size_t st_wv = st_fx + (size_t)ST * S * 8;
+  static constexpr size_t st_fx = st_fy + (size_t)ST * RS * 8;
+  static constexpr size_t st_wv = st_fx + (size_t)ST * RS * 8;
   static constexpr size_t stage_bytes = ws_al16(st_wv + (size_t)ST * P * 8);
   static constexpr int NB_WARPS = 10;                                 // builders
   static constexpr int NT = 32 * (2 + 4 + NB_WARPS);                  // producer, MMA, epilogue, builders
@@ -191,9 +194,12 @@ struct MmaNLayout {
   static constexpr size_t ob_hdr = 2 * a_bytes + 2 * b_bytes;
   static constexpr size_t ob_bytes = ws_al1k(ob_hdr + 16);
   static constexpr size_t st_pk = 16;
+  // staged factor rows RS = S + 2 values apart: the rows of consecutive samples start 8 banks apart,
+  // so that the builders' reads of several samples' rows do not collide (rows stay 16-byte aligned)
+  static constexpr int RS = S + 2;
   static constexpr size_t st_fy = st_pk + ws_al16(4 * ST);
-  static constexpr size_t st_fx = st_fy + (size_t)ST * S * 8;
-  static constexpr size_t st_wv = st_fx + (size_t)ST * S * 8;
+  static constexpr size_t st_fx = st_fy + (size_t)ST * RS * 8;
+  static constexpr size_t st_wv = st_fx + (size_t)ST * RS * 8;
   static constexpr size_t stage_bytes = ws_al16(st_wv + (size_t)ST * P * 8);
   static constexpr int NB_WARPS = 14;
   static constexpr int NT = 32 * (2 + 4 + NB_WARPS);
@@ -303,8 +309,8 @@ __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, u
       ws_rows<S>(offs, a.cf_shift, a.OS, r0, fxo, fyo);
       if constexpr (!kRowsByPieces) {
         fence_proxy_async_smem();
-        bulk_load(sg + L::st_fx + (size_t)lane * S * 8, sep2 + fxo, S * 8, full + s);
-        bulk_load(sg + L::st_fy + (size_t)lane * S * 8, sep2 + fyo, S * 8, full + s);
+        bulk_load(sg + L::st_fx + (size_t)lane * L::RS * 8, sep2 + fxo, S * 8, full + s);
+        bulk_load(sg + L::st_fy + (size_t)lane * L::RS * 8, sep2 + fyo, S * 8, full + s);
       }
       float2* dst = reinterpret_cast<float2*>(sg + L::st_wv) + lane * P;
 #pragma unroll
@@ -330,7 +336,7 @@ __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, u
         const int id = id0 + lane;
         const int j = id / HP;
         const long long src = __shfl_sync(0xffffffffu, mine, j < 32 ? j : 31);
-        if (id < npieces) cp_async16(dstb + (size_t)j * S * 8 + 16 * (id - j * HP), sep2 + src + 2 * (id - j * HP));
+        if (id < npieces) cp_async16(dstb + (size_t)j * L::RS * 8 + 16 * (id - j * HP), sep2 + src + 2 * (id - j * HP));
       }
     }
     if (lane == 0) *reinterpret_cast<WsHeader*>(sg) = WsHeader{d0.nst, d0.flags, d0.xy, 0};
@@ -591,7 +597,7 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, ST, D, NOB>::NT, 
               if (j < n) {
                 const int tx = x - (pkv[j0 + j] & 0xff);
                 if (tx >= 0 && tx < S) {
-                  const float2 f = fxv[(j0 + j) * S + tx];
+                  const float2 f = fxv[(j0 + j) * L::RS + tx];
                   const float2 w = wvv[(j0 + j) * P + p];
                   xr[h2] = f.x * w.x + f.y * w.y;   // conj(fx) w V
                   xi[h2] = f.x * w.y - f.y * w.x;
@@ -628,7 +634,7 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, ST, D, NOB>::NT, 
               if (j < n) {
                 const int ty = y - ((pkv[j0 + j] >> 8) & 0xff);
                 if (ty >= 0 && ty < S) {
-                  const float2 f = fyv[(j0 + j) * S + ty];
+                  const float2 f = fyv[(j0 + j) * L::RS + ty];
                   br = f.x;
                   bi = f.y;
                 }
@@ -888,7 +894,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
               if (j < n) {
                 const int tx = x - (pkv[j0 + j] & 0xff);
                 if (tx >= 0 && tx < S) {
-                  const float2 f = fxv[(j0 + j) * S + tx];
+                  const float2 f = fxv[(j0 + j) * L::RS + tx];
                   fr = f.x;
                   fi = f.y;
                 }
@@ -916,7 +922,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
               if (j < n) {
                 const int ty = y - ((pkv[j0 + j] >> 8) & 0xff);
                 if (ty >= 0 && ty < S) {
-                  const float2 f = fyv[(j0 + j) * S + ty];
+                  const float2 f = fyv[(j0 + j) * L::RS + ty];
                   const float2 w = wvv[(j0 + j) * P + p];
                   br = f.x * w.x + f.y * w.y;   // conj(fy) w V
                   bi = f.x * w.y - f.y * w.x;
@@ -965,8 +971,8 @@ constexpr MmaCfg kMmaCfg[3] = {{64, 1, 9, 8, 32, 2, 3}, {64, 2, 9, 8, 32, 3, 2},
 constexpr MmaCfg kMmaNCfg[21] = {
     {8, 1, 9, 16, 32, 8, 2},   {8, 2, 9, 16, 32, 8, 2},   {8, 4, 9, 16, 32, 8, 2},   {16, 1, 17, 16, 32, 8, 2},
     {16, 2, 17, 16, 32, 8, 2}, {16, 4, 17, 16, 32, 8, 2}, {24, 1, 9, 16, 32, 8, 2},  {24, 2, 9, 16, 32, 8, 2},
-    {24, 4, 9, 16, 32, 6, 2},  {32, 1, 17, 16, 32, 8, 2}, {32, 2, 17, 16, 32, 6, 2}, {32, 4, 17, 16, 32, 3, 2},
-    {40, 1, 9, 16, 32, 6, 2},  {40, 2, 9, 16, 32, 5, 2},  {40, 4, 9, 16, 32, 2, 2},  {48, 1, 17, 16, 32, 5, 2},
+    {24, 4, 9, 16, 32, 6, 2},  {32, 1, 17, 16, 32, 7, 2}, {32, 2, 17, 16, 32, 6, 2}, {32, 4, 17, 16, 32, 3, 2},
+    {40, 1, 9, 16, 32, 6, 2},  {40, 2, 9, 16, 32, 5, 2},  {40, 4, 9, 16, 32, 2, 2},  {48, 1, 17, 16, 32, 4, 2},
     {48, 2, 17, 16, 32, 3, 2}, {48, 4, 17, 8, 32, 4, 2},  {56, 1, 9, 16, 32, 4, 2},  {56, 2, 9, 16, 32, 3, 2},
     {56, 4, 9, 8, 32, 4, 2},
 };

@@ -58,7 +58,8 @@ struct MmaDgLayout {
   static constexpr size_t st_ph = st_src + 4 * ST;
   static constexpr size_t st_fxo = st_ph + 8 * ST;
   static constexpr size_t st_fy = st_fxo + 8 * ST;
-  static constexpr size_t stage_bytes = ws_al16(st_fy + (size_t)ST * S * 8);
+  static constexpr int RS = S + 2;   // fy rows RS values apart (bank spread, as for gridding)
+  static constexpr size_t stage_bytes = ws_al16(st_fy + (size_t)ST * RS * 8);
   static constexpr int NB_WARPS = 14;
   static constexpr int NT = 32 * (2 + 4 + NB_WARPS);
   static constexpr size_t off_ob = 0;
@@ -129,7 +130,7 @@ __device__ __forceinline__ void mma_dg_producer(const DegridArgs& a, const int c
         reinterpret_cast<long long*>(sg + L::st_fxo)[i] = fxo;
         if constexpr (!kRowsByPieces) {
           fence_proxy_async_smem();
-          bulk_load(sg + L::st_fy + (size_t)i * S * 8, sep2 + fyo[h], S * 8, full + s);
+          bulk_load(sg + L::st_fy + (size_t)i * L::RS * 8, sep2 + fyo[h], S * 8, full + s);
         }
       }
     }
@@ -146,7 +147,7 @@ __device__ __forceinline__ void mma_dg_producer(const DegridArgs& a, const int c
         const long long s1 = __shfl_sync(0xffffffffu, fyo[1], jl);
         if (id < npieces) {
           const int w = id - j * HP;
-          cp_async16(sg + L::st_fy + (size_t)j * S * 8 + 16 * w, sep2 + (j < 32 ? s0 : s1) + 2 * w);
+          cp_async16(sg + L::st_fy + (size_t)j * L::RS * 8 + 16 * w, sep2 + (j < 32 ? s0 : s1) + 2 * w);
         }
       }
     }
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(MmaDgLayout<S, P, TILE, KY, D, NZ, NOB>::NT, 1
             if (j < h.nst) {
               const int ty = KY * sl + 2 * kq + h2 - ((pkv[j] >> 8) & 0xff);
               if (ty >= 0 && ty < S) {
-                const float2 f = fyv[j * S + ty];
+                const float2 f = fyv[j * L::RS + ty];
                 fr = f.x;
                 fi = f.y;
               }
@@ -505,7 +506,7 @@ struct MmaDgCfg {
 constexpr MmaDgCfg kMmaDgCfg[21] = {
     {8, 1, 9, 16, 4, 3, 3},   {8, 2, 9, 16, 4, 3, 3},   {8, 4, 9, 16, 4, 3, 3},   {16, 1, 17, 16, 4, 3, 3},
     {16, 2, 17, 16, 4, 3, 3}, {16, 4, 17, 16, 4, 3, 2}, {24, 1, 9, 16, 4, 3, 3},  {24, 2, 9, 16, 3, 3, 3},
-    {24, 4, 9, 16, 3, 3, 2},  {32, 1, 17, 16, 3, 3, 3}, {32, 2, 17, 16, 4, 3, 2}, {32, 4, 17, 8, 3, 3, 3},
+    {24, 4, 9, 16, 3, 3, 2},  {32, 1, 17, 16, 3, 3, 3}, {32, 2, 17, 16, 4, 2, 2}, {32, 4, 17, 8, 3, 3, 3},
     {40, 1, 9, 16, 3, 3, 3},  {40, 2, 9, 16, 3, 3, 2},  {40, 4, 9, 8, 2, 3, 3},   {48, 1, 17, 16, 2, 2, 3},
     {48, 2, 17, 16, 2, 2, 2}, {48, 4, 17, 8, 2, 3, 2},  {56, 1, 9, 16, 3, 3, 2},  {56, 2, 9, 16, 2, 2, 2},
     {56, 4, 9, 8, 2, 3, 2},
