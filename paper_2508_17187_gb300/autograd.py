@@ -75,20 +75,35 @@ def chi2(model_vis: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor) -> to
     return (weight.double() * (r.real.double() ** 2 + r.imag.double() ** 2)).sum()
 
 
-def residual_image(fm: ForwardModel, image: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor) -> torch.Tensor:
-    """Eq. ResIm for one partition: F^H G W (V - D F I), normalised by the weights and the taper.
-    The residual V - D F I is formed by the degridding itself (AWG_DEGRID_SUBTRACT), in one pass."""
+def residual_vis(fm: ForwardModel, image: torch.Tensor, vis: torch.Tensor) -> torch.Tensor:
+    """The data residual V - D F I of Eq. ResIm, formed by the degridding itself
+    (AWG_DEGRID_SUBTRACT) in one pass over the visibilities."""
+    res = vis.contiguous().clone()
+    api.degrid_visibilities(fm.cf, fm.plan, image_to_grid(image, fm.inv_taper2d).contiguous(), res, subtract=True)
+    return res
+
+
+def chi2_of_residual(res: torch.Tensor, weight: torch.Tensor) -> torch.Tensor:
+    """Eq. Chisq from a data residual: sum w |res|^2 (FP64 accumulation, as chi2)."""
+    return (weight.double() * (res.real.double() ** 2 + res.imag.double() ** 2)).sum()
+
+
+def image_of_residual(fm: ForwardModel, res: torch.Tensor, weight: torch.Tensor) -> torch.Tensor:
+    """F^H G W res, normalised by the weights and the taper: the residual image of a data residual."""
     cf, plan = fm.cf, fm.plan
     N, P = cf.grid_n, fm.P
-    res = vis.contiguous().clone()
-    api.degrid_visibilities(cf, plan, image_to_grid(image, fm.inv_taper2d).contiguous(), res, subtract=True)
-    g = torch.zeros((N, N, P), dtype=torch.complex64, device=vis.device)
-    sw = torch.zeros(P, dtype=torch.float64, device=vis.device)
-    api.grid_visibilities(cf, plan, res, weight, g, sw)
+    g = torch.zeros((N, N, P), dtype=torch.complex64, device=res.device)
+    sw = torch.zeros(P, dtype=torch.float64, device=res.device)
+    api.grid_visibilities(cf, plan, res.contiguous(), weight, g, sw)
     im = torch.fft.fftshift(torch.fft.ifft2(torch.fft.ifftshift(g, dim=(0, 1)), dim=(0, 1)), dim=(0, 1)) * (N * N)
     im = im.contiguous()
     api.grid_normalize(cf, im, sw, direction=0)
     return im.real
+
+
+def residual_image(fm: ForwardModel, image: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor) -> torch.Tensor:
+    """Eq. ResIm for one partition: F^H G W (V - D F I), normalised by the weights and the taper."""
+    return image_of_residual(fm, residual_vis(fm, image, vis), weight)
 
 
 def inner_mask(N: int, device="cuda") -> torch.Tensor:
@@ -119,8 +134,8 @@ def major_cycle(fm: ForwardModel, vis: torch.Tensor, weight: torch.Tensor, n_ite
                 gain: Optional[float] = None, image: Optional[torch.Tensor] = None,
                 mask: Optional[torch.Tensor] = None):
     """Eq. ModelUpdate, I <- I + gain * mask * residual image, with the StepSize component's step
-    gain = 1 / lambda_max of the masked normal operator unless given; returns (image, chi2 per
-    iteration).  The default mask keeps the model inside the inner half of the field: near the edge
+    gain = 1 / lambda_max of the masked normal operator unless given; returns (image, chi2 after each
+    iteration).  Each iteration degrids once (the residual V - D F I, in place) and grids once.  The default mask keeps the model inside the inner half of the field: near the edge
     the taper correction divides by T(x)T(y) -> 0 on the way in and again on the way out."""
     N, P = fm.cf.grid_n, fm.P
     if image is None:
@@ -129,10 +144,13 @@ def major_cycle(fm: ForwardModel, vis: torch.Tensor, weight: torch.Tensor, n_ite
         mask = inner_mask(N, vis.device)
     if gain is None:
         gain = 1.0 / largest_eigenvalue(fm, weight, mask)
+    # one degridding per cycle: the data residual of the updated image gives its chi^2 and the next
+    # cycle's residual image
     hist = []
-    for _ in range(n_iter):
-        with torch.no_grad():
-            r = residual_image(fm, image, vis, weight)
-            image = image + gain * mask * r
-            hist.append(float(chi2(fm(image), vis, weight)))
+    with torch.no_grad():
+        res = residual_vis(fm, image, vis)
+        for _ in range(n_iter):
+            image = image + gain * mask * image_of_residual(fm, res, weight)
+            res = residual_vis(fm, image, vis)
+            hist.append(float(chi2_of_residual(res, weight)))
     return image, hist
