@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
           const int j0 = sub * J, n = min(J, h.nst - j0);
           const int fl = (sub == 0 ? (h.flags & kWsFirst) : 0) | (sub == nsub - 1 ? (h.flags & kWsLast) : 0);
           if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(n, fl, h.xy, 0);
-#pragma unroll 2
+#pragma unroll 4
           for (int task = bt; task < AR * KQ; task += NBT) {
             const int kq = (task >> 3) % KQ;
             const int m = (task / (8 * KQ)) * 8 + (task & 7);
@@ -909,7 +909,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
             *reinterpret_cast<float4*>(obuf + L::ob_ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
           }
-#pragma unroll 2
+#pragma unroll 4
           for (int task = bt; task < N * KQ; task += NBT) {
             const int kq = (task >> 3) % KQ;
             const int nn = (task / (8 * KQ)) * 8 + (task & 7);

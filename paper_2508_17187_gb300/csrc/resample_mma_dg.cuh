@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(MmaDgLayout<S, P, TILE, KY, D, NZ, NOB>::NT, 1
         unsigned char* obuf = smem + L::off_ob + (size_t)ob * L::ob_bytes;
         const float2* slice = reinterpret_cast<const float2*>(smem + L::off_slice + (size_t)z * L::slice_bytes);
         if (bt == 0) *reinterpret_cast<int4*>(obuf + L::ob_hdr) = make_int4(h.nst, sl, 0, 0);
-#pragma unroll 2
+#pragma unroll 4
         for (int task = bt; task < 128 * KQ; task += NBT) {
           const int kq = (task >> 3) % KQ;
           const int m = (task / (8 * KQ)) * 8 + (task & 7);
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(MmaDgLayout<S, P, TILE, KY, D, NZ, NOB>::NT, 1
           *reinterpret_cast<float4*>(obuf + L::ob_ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
           *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
-#pragma unroll 2
+#pragma unroll 4
         for (int task = bt; task < N * KQ; task += NBT) {
           const int kq = (task >> 3) % KQ;
           const int nn = (task / (8 * KQ)) * 8 + (task & 7);
