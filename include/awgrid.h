@@ -174,8 +174,10 @@ awg_status cf_set_fused_terms(awg_cf_set cf, int32_t* terms);
  * scratch of about (R C n_pol) 20 B plus one grid and two plans, and frees it before returning.
  * choice_out: host int32 [65] or NULL, the chosen configuration (0, 1, 2 or 3) per support, -1
  * where none was timed; ms_out: host float [4][65] or NULL, grid + degrid milliseconds of each
- * configuration per support (0 where not timed).  Full-table CF sets have nothing to tune
- * (choices -1).  Errors: INVALID_ARG, OOM, CUDA.
+ * configuration per support (0 where not timed).  Fused multi-term sets (cf_set_fused_terms > 0)
+ * have configurations 0 and 1 of the fused kernels (the tiles and staging of the cp.async
+ * configurations), which are timed the same way; full-table and full-polarisation sets have
+ * nothing to tune (choices -1).  Errors: INVALID_ARG, OOM, CUDA.
  */
 awg_status cf_set_autotune(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const double* freq_hz, int32_t n_chan,
                            const int32_t* pa_bin, const int32_t* chan_subband, int32_t n_pol, void* stream,
@@ -183,7 +185,9 @@ awg_status cf_set_autotune(awg_cf_set cf, const double* uvw_m, int64_t n_rows, c
 
 /* Select configuration `config` (0, 1, 2 or 3) of the separable kernels for one support of the
  * W-projection schedule by hand (what cf_set_autotune does by timing); plans created before the
- * call are invalid afterwards.  Errors: INVALID_ARG (no configurations for that support). */
+ * call are invalid afterwards.  Fused multi-term sets take 0 or 1, full-polarisation sets 0.
+ * Errors: INVALID_ARG (no configurations for that support), UNSUPPORTED (a configuration the
+ * set's kernels do not have). */
 awg_status cf_set_choose(awg_cf_set cf, int32_t support, int32_t config);
 
 /* Mueller elements of a full-polarisation CF set (use_pol): *n_elem (0 otherwise) and, when not

@@ -623,7 +623,9 @@ awg_status cf_set_choose(awg_cf_set h, int32_t support, int32_t config) {
   if (support < 1 || support > kMaxSupport || !has_exact(support))
     return set_error(AWG_ERR_INVALID_ARG, "support " + std::to_string(support) + " has no kernel configurations");
   if (config < 0 || config >= kNumCand) return set_error(AWG_ERR_INVALID_ARG, "config must be 0, 1, 2 or 3");
-  if (cf->fused && config != 0) return set_error(AWG_ERR_UNSUPPORTED, "fused kernels have one configuration");
+  if (cf->fused && (config > 1 || (config == 1 && cf->n_mb > 1)))
+    return set_error(AWG_ERR_UNSUPPORTED, cf->n_mb > 1 ? "pol-mixing kernels have one configuration"
+                                                       : "fused kernels have configurations 0 and 1");
   cf->cand[support] = (int8_t)config;
   fill_slots(cf);
   return AWG_OK;

@@ -1,0 +1,6 @@
+// Instantiations of the fused degridding kernels for CF sets of 3 outer-product terms, configuration 1.
+#include "resample_sep.cuh"
+
+namespace awg {
+AWG_FOR_FUSED(AWG_INSTANTIATE_DEGRID_FUSED_C1, 3)
+}  // namespace awg

@@ -1,0 +1,6 @@
+// Instantiations of the fused gridding kernels for CF sets of 2 outer-product terms, configuration 1.
+#include "resample_sep.cuh"
+
+namespace awg {
+AWG_FOR_FUSED(AWG_INSTANTIATE_GRID_FUSED_C1, 2)
+}  // namespace awg

@@ -39,6 +39,12 @@ AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED, 4)
 AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 2)
 AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 3)
 AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED, 4)
+AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED_C1, 2)
+AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED_C1, 3)
+AWG_FOR_FUSED(AWG_DECLARE_GRID_FUSED_C1, 4)
+AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED_C1, 2)
+AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED_C1, 3)
+AWG_FOR_FUSED(AWG_DECLARE_DEGRID_FUSED_C1, 4)
 AWG_FOR_FUSED_MIX(AWG_DECLARE_GRID_FUSED_MIX, 2)
 AWG_FOR_FUSED_MIX(AWG_DECLARE_GRID_FUSED_MIX, 3)
 AWG_FOR_FUSED_MIX(AWG_DECLARE_GRID_FUSED_MIX, 4)
@@ -120,8 +126,10 @@ awg_status grid_slot_sep(int S, int cand, int slot, int P, const GridArgs& a, in
 
 // Fused kernels: one record per sample of a CF set of rk outer-product terms (the pol-mixing
 // instances when a.mix is set).
-awg_status grid_slot_fused(int S, int rk, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
+// cand: the support's configuration (0 or 1; the plan binned the support by its tile).
+awg_status grid_slot_fused(int S, int rk, int cand, int slot, int P, const GridArgs& a, int sms, cudaStream_t st) {
   if (a.mix != nullptr) {
+    if (cand != 0) return set_error(AWG_ERR_UNSUPPORTED, "pol-mixing kernels have one configuration");
 #define AWG_CASE(SS, PP, RR) \
   if (S == SS && P == PP && rk == RR) return run_grid_fused<SS, PP, RR, true>(a, slot, sms, st);
     AWG_FOR_FUSED_MIX(AWG_CASE, 2)
@@ -129,6 +137,15 @@ awg_status grid_slot_fused(int S, int rk, int slot, int P, const GridArgs& a, in
     AWG_FOR_FUSED_MIX(AWG_CASE, 4)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no pol-mixing gridding kernel for this support / pol count / rank");
+  }
+  if (cand == 1) {
+#define AWG_CASE(SS, PP, RR) \
+  if (S == SS && P == PP && rk == RR) return run_grid_fused<SS, PP, RR, false, 1>(a, slot, sms, st);
+    AWG_FOR_FUSED(AWG_CASE, 2)
+    AWG_FOR_FUSED(AWG_CASE, 3)
+    AWG_FOR_FUSED(AWG_CASE, 4)
+#undef AWG_CASE
+    return set_error(AWG_ERR_UNSUPPORTED, "no fused gridding kernel for this support / pol count / rank");
   }
 #define AWG_CASE(SS, PP, RR) \
   if (S == SS && P == PP && rk == RR) return run_grid_fused<SS, PP, RR>(a, slot, sms, st);
@@ -139,8 +156,10 @@ awg_status grid_slot_fused(int S, int rk, int slot, int P, const GridArgs& a, in
   return set_error(AWG_ERR_UNSUPPORTED, "no fused gridding kernel for this support / pol count / rank");
 }
 
-awg_status degrid_slot_fused(int S, int rk, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
+// cand: the support's configuration (0 or 1; the plan binned the support by its tile).
+awg_status degrid_slot_fused(int S, int rk, int cand, int slot, int P, const DegridArgs& a, int sms, cudaStream_t st) {
   if (a.mix != nullptr) {
+    if (cand != 0) return set_error(AWG_ERR_UNSUPPORTED, "pol-mixing kernels have one configuration");
 #define AWG_CASE(SS, PP, RR) \
   if (S == SS && P == PP && rk == RR) return run_degrid_fused<SS, PP, RR, true>(a, slot, sms, st);
     AWG_FOR_FUSED_MIX(AWG_CASE, 2)
@@ -148,6 +167,15 @@ awg_status degrid_slot_fused(int S, int rk, int slot, int P, const DegridArgs& a
     AWG_FOR_FUSED_MIX(AWG_CASE, 4)
 #undef AWG_CASE
     return set_error(AWG_ERR_UNSUPPORTED, "no pol-mixing degridding kernel for this support / pol count / rank");
+  }
+  if (cand == 1) {
+#define AWG_CASE(SS, PP, RR) \
+  if (S == SS && P == PP && rk == RR) return run_degrid_fused<SS, PP, RR, false, 1>(a, slot, sms, st);
+    AWG_FOR_FUSED(AWG_CASE, 2)
+    AWG_FOR_FUSED(AWG_CASE, 3)
+    AWG_FOR_FUSED(AWG_CASE, 4)
+#undef AWG_CASE
+    return set_error(AWG_ERR_UNSUPPORTED, "no fused degridding kernel for this support / pol count / rank");
   }
 #define AWG_CASE(SS, PP, RR) \
   if (S == SS && P == PP && rk == RR) return run_degrid_fused<SS, PP, RR>(a, slot, sms, st);
@@ -462,7 +490,7 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
     AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
     if (cf->separable) {
       for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
-        s = cf->fused ? grid_slot_fused(cf->slots.S[i], cf->fused, i, P, ak, sms, st)
+        s = cf->fused ? grid_slot_fused(cf->slots.S[i], cf->fused, cf->cand[cf->slots.S[i]], i, P, ak, sms, st)
                       : grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, st);
         if (s != AWG_OK) return s;
       }
@@ -559,7 +587,7 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
     AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
     if (cf->separable) {
       for (int i = cf->slots.n - 1; i >= 0; --i) {
-        s = cf->fused ? degrid_slot_fused(cf->slots.S[i], cf->fused, i, P, ak, sms, st)
+        s = cf->fused ? degrid_slot_fused(cf->slots.S[i], cf->fused, cf->cand[cf->slots.S[i]], i, P, ak, sms, st)
                       : degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, st);
         if (s != AWG_OK) return s;
       }
@@ -589,7 +617,9 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
   for (int S = 0; S <= kMaxSupport; ++S) choice[S] = -1;
   if (ms_out)
     for (int i = 0; i < kNumCand * (kMaxSupport + 1); ++i) ms_out[i] = 0.f;
-  if (!cf->separable || cf->fused) return AWG_OK;   // full tables and fused kernels: one configuration
+  // full tables and pol-mixing sets have one configuration; fused sets have two (0 and 1)
+  if (!cf->separable || (cf->fused && cf->n_mb > 1)) return AWG_OK;
+  const int n_cand = cf->fused ? 2 : kNumCand;
   const int N = cf->p.grid_n;
   const int64_t n = n_rows * (int64_t)n_chan;
   // unit visibilities and weights (a value-independent timing; zeros would skip the flushes)
@@ -619,7 +649,7 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
   float best[kMaxSupport + 1];
   for (int S = 0; S <= kMaxSupport; ++S) best[S] = 3.4e38f;
   int8_t pick[kMaxSupport + 1] = {};
-  for (int c = 0; c < kNumCand && s == AWG_OK; ++c) {
+  for (int c = 0; c < n_cand && s == AWG_OK; ++c) {
     for (int S = 1; S <= kMaxSupport; ++S)
       if (has_exact(S)) cf->cand[S] = (int8_t)c;
     fill_slots(cf);
@@ -649,7 +679,7 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
             break;
           }
           cudaEventRecord(ev[0], st);
-          s = grid_slot_sep(S, c, i, P, ga, sms, st);
+          s = cf->fused ? grid_slot_fused(S, cf->fused, c, i, P, ga, sms, st) : grid_slot_sep(S, c, i, P, ga, sms, st);
           cudaEventRecord(ev[1], st);
           if (s != AWG_OK) break;
           if ((e = cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st)) != cudaSuccess) {
@@ -657,7 +687,8 @@ awg_status autotune_supports(CfSetImpl* cf, const double* uvw, int64_t n_rows, c
             break;
           }
           cudaEventRecord(ev[2], st);
-          s = degrid_slot_sep(S, c, i, P, da, sms, st);
+          s = cf->fused ? degrid_slot_fused(S, cf->fused, c, i, P, da, sms, st)
+                        : degrid_slot_sep(S, c, i, P, da, sms, st);
           cudaEventRecord(ev[3], st);
           if (s != AWG_OK) break;
           if ((e = cudaEventSynchronize(ev[3])) != cudaSuccess) {

@@ -935,9 +935,9 @@ constexpr int fused_stage0(int S, int P, int RK, bool grid, int base) {
   return P == 4 && RK == 4 && ((grid && S == 40) || (!grid && S == 32)) ? 2 * base : base;
 }
 
-template <int S, int P, int RK, bool MIX = false>
+template <int S, int P, int RK, bool MIX = false, int C = 0>
 awg_status run_grid_fused(const GridArgs& a, int slot, int sms, cudaStream_t st) {
-  constexpr ExactCfg e = exact_cfg(S, 0);
+  constexpr ExactCfg e = exact_cfg(S, C);
   constexpr int nt = S * e.g_grid;
   constexpr int stage = fused_stage<S, e.tile, P, RK, fused_stage0(S, P, RK, true, e.stage)>();
   using L = SepLayout<S, e.tile, P, stage, RK>;
@@ -955,9 +955,9 @@ awg_status run_grid_fused(const GridArgs& a, int slot, int sms, cudaStream_t st)
   return AWG_OK;
 }
 
-template <int S, int P, int RK, bool MIX = false>
+template <int S, int P, int RK, bool MIX = false, int C = 0>
 awg_status run_degrid_fused(const DegridArgs& a, int slot, int sms, cudaStream_t st) {
-  constexpr ExactCfg e = exact_cfg(S, 0);
+  constexpr ExactCfg e = exact_cfg(S, C);
   constexpr int nt = S * e.g_degrid;
   constexpr int stage = fused_stage<S, e.tile, P, RK, fused_stage0(S, P, RK, false, e.stage)>();
   using L = SepLayout<S, e.tile, P, stage, RK>;
@@ -983,6 +983,15 @@ awg_status run_degrid_fused(const DegridArgs& a, int slot, int sms, cudaStream_t
   extern template awg_status run_grid_fused<S, P, RK>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_DECLARE_DEGRID_FUSED(S, P, RK) \
   extern template awg_status run_degrid_fused<S, P, RK>(const DegridArgs&, int, int, cudaStream_t);
+// configuration 1 (the tiles and staging of exact-support candidate 1) of the fused kernels
+#define AWG_DECLARE_GRID_FUSED_C1(S, P, RK) \
+  extern template awg_status run_grid_fused<S, P, RK, false, 1>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_DECLARE_DEGRID_FUSED_C1(S, P, RK) \
+  extern template awg_status run_degrid_fused<S, P, RK, false, 1>(const DegridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_GRID_FUSED_C1(S, P, RK) \
+  template awg_status run_grid_fused<S, P, RK, false, 1>(const GridArgs&, int, int, cudaStream_t);
+#define AWG_INSTANTIATE_DEGRID_FUSED_C1(S, P, RK) \
+  template awg_status run_degrid_fused<S, P, RK, false, 1>(const DegridArgs&, int, int, cudaStream_t);
 #define AWG_INSTANTIATE_GRID_FUSED(S, P, RK) \
   template awg_status run_grid_fused<S, P, RK>(const GridArgs&, int, int, cudaStream_t);
 #define AWG_INSTANTIATE_DEGRID_FUSED(S, P, RK) \
