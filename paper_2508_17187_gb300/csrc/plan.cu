@@ -19,6 +19,8 @@
 namespace awg {
 namespace {
 
+constexpr int kIndexScCache = 4096;   // channels whose f / c k_index keeps in shared memory (32 KB)
+
 struct IndexParams {
   int64_t n;
   int rank;   // records per sample (terms per CF of a separable set)
@@ -44,12 +46,20 @@ __global__ void k_index(IndexParams ip, const double* __restrict__ uvw, const do
                         const int32_t* __restrict__ sup_of_cf, SlotTable st, SampleRec* __restrict__ rec_tmp,
                         int32_t* __restrict__ key_out, int32_t* __restrict__ bcount, int32_t* __restrict__ drop,
                         unsigned long long* __restrict__ counters) {
+  // f / c per channel, the same correctly rounded quotient for every row: formed once per block
+  // in shared memory when the channels fit (kIndexScCache), else per sample
+  extern __shared__ double s_sc[];
+  const bool sc_cached = ip.C <= kIndexScCache;
+  if (sc_cached) {
+    for (int c = threadIdx.x; c < ip.C; c += blockDim.x) s_sc[c] = __ddiv_rn(freq[c], kCLight);
+    __syncthreads();
+  }
   unsigned long long kept = 0, taps = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ip.n; s += stride) {
     const int64_t r = s / ip.C;
     const int c = (int)(s - r * ip.C);
-    const double sc = __ddiv_rn(freq[c], kCLight);
+    const double sc = sc_cached ? s_sc[c] : __ddiv_rn(freq[c], kCLight);
     const double u = __dmul_rn(uvw[3 * r], sc);
     const double v = __dmul_rn(uvw[3 * r + 1], sc);
     const double w = __dmul_rn(uvw[3 * r + 2], sc);
@@ -445,7 +455,8 @@ awg_status plan_build(PlanImpl* pl, const double* uvw, const double* freq, const
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
   if (pl->n > 0) {
     const int blocks = (int)std::min<int64_t>((pl->n + 255) / 256, (int64_t)sms * 8);
-    k_index<<<blocks, 256, 0, st>>>(ip, uvw, freq, pa_bin, chan_sb, cf->d_sup, cf->slots, pl->d_rec_tmp, pl->d_key,
+    const size_t sc_bytes = ip.C <= kIndexScCache ? sizeof(double) * (size_t)ip.C : 0;
+    k_index<<<blocks, 256, sc_bytes, st>>>(ip, uvw, freq, pa_bin, chan_sb, cf->d_sup, cf->slots, pl->d_rec_tmp, pl->d_key,
                                     pl->d_bcount, pl->d_drop, pl->d_counters);
     AWG_CUDA_TRY(cudaGetLastError());
     count_launches(1);
