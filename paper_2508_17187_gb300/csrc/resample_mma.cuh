@@ -278,7 +278,7 @@ template <int S, int P, int TILE, int ST, int D, class L>
 __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, unsigned char* smem, uint64_t* full,
                                              uint64_t* empty, const int64_t* offs, volatile int* abort_flag,
                                              unsigned long long* err, const int lane) {
-  constexpr bool kRowsByPieces = S < 32;   // else one bulk copy per factor row
+  constexpr bool kRowsByPieces = S <= 40;   // else one bulk copy per factor row (measured faster there)
   double wsum[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) wsum[p] = 0.0;
@@ -323,20 +323,18 @@ __device__ __forceinline__ void mma_producer(const GridArgs& a, const int cls, u
         for (int p = 0; p < P; ++p) wsum[p] += (double)x0.w[p];
       }
     }
-    // short factor rows: 16-byte pieces spread over the lanes (one bulk copy per short row leaves
-    // this one warp issue-bound on the copies); each piece takes its row's source offset from the
-    // lane that holds the sample
-    constexpr int HP = S / 2;   // 16-byte pieces per row
-    const int npieces = kRowsByPieces ? d0.nst * HP : 0;
+    // factor rows of up to 320 bytes: each lane copies its sample's two rows in 16-byte
+    // cp.async pieces (one bulk copy per row leaves this one warp issue-bound on the copies)
+    if constexpr (kRowsByPieces) {
+      constexpr int HP = S / 2;   // 16-byte pieces per row
+      if (lane < d0.nst) {
+        unsigned char* dx_ = sg + L::st_fx + (size_t)lane * L::RS * 8;
+        unsigned char* dy_ = sg + L::st_fy + (size_t)lane * L::RS * 8;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const long long mine = r ? fyo : fxo;
-      unsigned char* dstb = sg + (r ? L::st_fy : L::st_fx);
-      for (int id0 = 0; id0 < npieces; id0 += 32) {
-        const int id = id0 + lane;
-        const int j = id / HP;
-        const long long src = __shfl_sync(0xffffffffu, mine, j < 32 ? j : 31);
-        if (id < npieces) cp_async16(dstb + (size_t)j * L::RS * 8 + 16 * (id - j * HP), sep2 + src + 2 * (id - j * HP));
+        for (int w = 0; w < HP; ++w) {
+          cp_async16(dx_ + 16 * w, sep2 + fxo + 2 * w);
+          cp_async16(dy_ + 16 * w, sep2 + fyo + 2 * w);
+        }
       }
     }
     if (lane == 0) *reinterpret_cast<WsHeader*>(sg) = WsHeader{d0.nst, d0.flags, d0.xy, 0};
