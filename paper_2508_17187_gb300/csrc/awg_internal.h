@@ -49,7 +49,8 @@ __host__ __device__ constexpr int class_of_support(int S) {
 // where two CTAs still fit (candidate 1 of supports 24-56: 1-3% on the W-projection workload).
 // Every support has kNumCand compiled candidates; candidate 0 is the default and cf_set_autotune
 // picks per support by timing.  Candidate 2 is the warp-specialised pair of kernels, candidate 3
-// tensor-core gridding with warp-specialised degridding.  The supports listed here and
+// the tensor-core pair (the warp-specialised degridding kernel where a window is wider than 64).
+// Fused multi-term kernels take the tiles of candidates 0 and 1.  The supports listed here and
 // AWG_FOR_EXACT_AND_POLS must agree.
 struct ExactCfg {
   int S, g_grid, g_degrid, tile, stage;
@@ -89,9 +90,9 @@ constexpr ExactCfg kExactCand[kNumCand][8] = {
         {64, 8, 8, 8, 4},
     },
     {
-        // candidate 3: gridding on the tensor cores (resample_mma.cuh), degridding by the
-        // warp-specialised kernel, with these tiles (window side S + tile - 1 at or just below a
-        // multiple of 16); the cp.async kernels compiled with the same tiles serve the rest
+        // candidate 3: the tensor-core kernels (resample_mma.cuh, resample_mma_dg.cuh) with these
+        // tiles (window side S + tile - 1 at or just below a multiple of 16); the cp.async kernels
+        // compiled with the same tiles serve the calls those cannot take
         {8, 8, 8, 9, 8},
         {16, 8, 8, 17, 8},
         {24, 8, 8, 9, 8},
