@@ -160,13 +160,14 @@ awg_status cf_set_fused_terms(awg_cf_set cf, int32_t* terms);
  * CTA and samples staged per chunk; 2 is the warp-specialised pair (a producer warp stages chunks
  * into a ring of shared-memory stages handed over on mbarriers, consumer warps only multiply and
  * add, a flush warp (gridding) or reduce warp (degridding) finishes each item, and degridding
- * loads each item's grid window with one TMA tile copy); 3 grids on the tensor cores (tcgen05,
- * 3xTF32 products, FP32 accumulation in tensor memory: a window is the product of the item's
- * x-factor rows times w V and its y-factor rows, relative RMS error a few 1e-6 against the FP64
- * result) with tiles of odd side so that a window fills the MMA shape, and degrids with the
- * warp-specialised kernel on those tiles.  For each configuration this builds a plan of the given
- * geometry (uvw_m, freq_hz,
- * pa_bin, chan_subband: device arrays as for plan_create, typically the data to be imaged or a
+ * loads each item's grid window with one TMA tile copy); 3 runs both operators on the tensor
+ * cores (tcgen05, 3xTF32 products, FP32 accumulation in tensor memory: a gridding window is the
+ * product of the item's x-factor rows and its y-factor rows times w V; degridding forms the
+ * samples' y-factor rows times TMA-loaded window slices and finishes the x sum per sample;
+ * relative RMS error a few 1e-6 against the FP64 result) with tiles of odd side so that a window
+ * fills the MMA shape (support 64, whose window is wider than 64 pixels, degrids with the
+ * warp-specialised kernel on those tiles).  For each configuration this builds a plan of the
+ * given geometry (uvw_m, freq_hz, pa_bin, chan_subband: device arrays as for plan_create, typically the data to be imaged or a
  * slice of it), grids and degrids unit visibilities with n_pol pols once, then times every
  * support's gridding and degridding launch three times (CUDA events on `stream`), and keeps the
  * fastest configuration per support in the CF set.  Plans created before the call are invalid
