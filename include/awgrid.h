@@ -247,7 +247,12 @@ awg_status cf_set_copy_factors(awg_cf_set cf, int32_t cf_index, int32_t term, fl
  * G multiplies w V by exp(+2 pi i (u dl + v dm + w dn)), dn = sqrt(1 - dl^2 - dm^2) - 1, D by its
  * conjugate (the phase term of Eq. CIJ); the plan forms every sample's phasor once per build and
  * the kernels read it.  The plan allocates device memory (about 44 bytes per sample and CF term,
- * 8 more per sample with a phase term) and keeps pointers to no caller buffer.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * 8 more per sample with a phase term) and keeps pointers to no caller buffer.  It also owns two
+ * CUDA streams and three events: the per-support launches of one gridding or degridding call
+ * alternate between those streams, ordered by the events after the work queued on the call's
+ * `stream` and before the work queued on it afterwards (so calls stay stream-ordered and
+ * graph-capturable), and a support's launch starts on the SMs that the previous one has finished
+ * with.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
  */
 awg_status plan_create(awg_cf_set cf, const double* uvw_m, int64_t n_rows, const double* freq_hz,
                        int32_t n_chan, const int32_t* pa_bin, const int32_t* chan_subband,

@@ -215,7 +215,19 @@ struct PlanImpl {
   float2* d_phasor = nullptr;     // per-sample phasor [n] of the phase term (when has_phase)
   int global_phase = 0;           // a plan-wide phase shift was given to plan_create
   cudaStream_t last_stream = nullptr;
+  // Side streams of the per-support launches (created with the plan; all null in a plan that
+  // owns none, whose launches then stay on the caller's stream): the launches of one operator
+  // alternate between them, forked from the caller's stream by fork_ev and joined back by
+  // join_ev, so that a support's launch starts on the SMs the previous one has finished with.
+  static constexpr int kSideStreams = 2;
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kSideStreams] = {};
 };
+
+// Creates / destroys a plan's side streams and events (launch.cu).
+awg_status plan_make_side_streams(PlanImpl* pl);
+void plan_free_side_streams(PlanImpl* pl);
 
 // Count of kernel launches made by the library (awg_kernel_launches).
 void count_launches(int n);

@@ -942,6 +942,7 @@ awg_status cf_set_copy_factors(awg_cf_set h, int32_t ci, int32_t term, float* fx
 
 static awg_status plan_free(PlanImpl* pl) {
   if (!pl) return AWG_OK;
+  plan_free_side_streams(pl);
   dev_free(pl->d_rec);
   dev_free(pl->d_rec_tmp);
   dev_free(pl->d_part);
@@ -1034,7 +1035,12 @@ awg_status plan_create(awg_cf_set h, const double* uvw_m, int64_t n_rows, const 
     plan_free(pl);
     return cuda_error(e, "plan_create allocation");
   }
-  awg_status s = plan_build(pl, uvw_m, freq_hz, pa_bin, chan_subband, (cudaStream_t)stream);
+  awg_status s = plan_make_side_streams(pl);
+  if (s != AWG_OK) {
+    plan_free(pl);
+    return s;
+  }
+  s = plan_build(pl, uvw_m, freq_hz, pa_bin, chan_subband, (cudaStream_t)stream);
   if (s != AWG_OK) {
     plan_free(pl);
     return s;

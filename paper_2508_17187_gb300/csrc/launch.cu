@@ -439,6 +439,63 @@ static DegridArgs degrid_args(const CfSetImpl* cf, const PlanImpl* pl, const voi
   return a;
 }
 
+awg_status plan_make_side_streams(PlanImpl* pl) {
+  for (int k = 0; k < PlanImpl::kSideStreams; ++k) {
+    AWG_CUDA_TRY(cudaStreamCreateWithFlags(&pl->side[k], cudaStreamNonBlocking));
+    AWG_CUDA_TRY(cudaEventCreateWithFlags(&pl->join_ev[k], cudaEventDisableTiming));
+  }
+  AWG_CUDA_TRY(cudaEventCreateWithFlags(&pl->fork_ev, cudaEventDisableTiming));
+  return AWG_OK;
+}
+
+void plan_free_side_streams(PlanImpl* pl) {
+  // work still queued on a side stream completes first (the caller's stream waits for it)
+  for (int k = 0; k < PlanImpl::kSideStreams; ++k) {
+    if (pl->side[k]) cudaStreamDestroy(pl->side[k]);
+    if (pl->join_ev[k]) cudaEventDestroy(pl->join_ev[k]);
+    pl->side[k] = nullptr;
+    pl->join_ev[k] = nullptr;
+  }
+  if (pl->fork_ev) cudaEventDestroy(pl->fork_ev);
+  pl->fork_ev = nullptr;
+}
+
+// The per-support launches of one operator, spread over the plan's side streams: fork() orders
+// them after the work already queued on the caller's stream, next() gives the stream of the next
+// launch (the two side streams in turn, so at most two supports are in flight), and the
+// destructor (or join()) makes the caller's stream wait for all of them.  Two launches in flight
+// together share no state but the grid, to which gridding adds with atomics and from which
+// degridding only reads: each launch has its own work-queue head and writes its own samples.  In
+// a plan without side streams every launch stays on the caller's stream.
+class SlotStreams {
+ public:
+  SlotStreams(PlanImpl* pl, cudaStream_t st) : pl_(pl), st_(st) {}
+  ~SlotStreams() { join(); }
+  awg_status fork() {
+    if (!pl_->fork_ev) return AWG_OK;
+    AWG_CUDA_TRY(cudaEventRecord(pl_->fork_ev, st_));
+    forked_ = true;   // from here on the side streams are joined back, even after an error
+    for (int k = 0; k < PlanImpl::kSideStreams; ++k) AWG_CUDA_TRY(cudaStreamWaitEvent(pl_->side[k], pl_->fork_ev, 0));
+    return AWG_OK;
+  }
+  cudaStream_t next() { return forked_ ? pl_->side[n_++ % PlanImpl::kSideStreams] : st_; }
+  awg_status join() {
+    if (!forked_) return AWG_OK;
+    forked_ = false;
+    for (int k = 0; k < PlanImpl::kSideStreams; ++k) {
+      AWG_CUDA_TRY(cudaEventRecord(pl_->join_ev[k], pl_->side[k]));
+      AWG_CUDA_TRY(cudaStreamWaitEvent(st_, pl_->join_ev[k], 0));
+    }
+    return AWG_OK;
+  }
+
+ private:
+  PlanImpl* pl_;
+  cudaStream_t st_;
+  bool forked_ = false;
+  int n_ = 0;
+};
+
 static awg_status check_version(const CfSetImpl* cf, const PlanImpl* pl) {
   if (pl->slots_version != cf->slots_version)
     return set_error(AWG_ERR_INVALID_ARG, "the CF set was retuned after this plan was made; create a new plan");
@@ -468,10 +525,13 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
       ae.goff = cf->elem_q[e];
       ae.sumwt = cf->elem_p[e] == cf->elem_q[e] ? sumwt + cf->elem_q[e] : nullptr;
       AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+      SlotStreams ss(pl, st);
+      if ((s = ss.fork()) != AWG_OK) return s;
       for (int i = cf->slots.n - 1; i >= 0; --i) {
-        s = grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, 1, ae, sms, st);
+        s = grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, 1, ae, sms, ss.next());
         if (s != AWG_OK) return s;
       }
+      if ((s = ss.join()) != AWG_OK) return s;
     }
     return AWG_OK;
   }
@@ -489,11 +549,15 @@ awg_status launch_grid(CfSetImpl* cf, PlanImpl* pl, const void* vis, const float
     }
     AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
     if (cf->separable) {
+      SlotStreams ss(pl, st);
+      if ((s = ss.fork()) != AWG_OK) return s;
       for (int i = cf->slots.n - 1; i >= 0; --i) {   // largest supports first
-        s = cf->fused ? grid_slot_fused(cf->slots.S[i], cf->fused, cf->cand[cf->slots.S[i]], i, P, ak, sms, st)
-                      : grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, st);
+        const cudaStream_t si = ss.next();
+        s = cf->fused ? grid_slot_fused(cf->slots.S[i], cf->fused, cf->cand[cf->slots.S[i]], i, P, ak, sms, si)
+                      : grid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, si);
         if (s != AWG_OK) return s;
       }
+      if ((s = ss.join()) != AWG_OK) return s;
       continue;
     }
     for (int c = kNumClasses - 1; c >= 0; --c) {   // largest supports first
@@ -553,10 +617,13 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
         ae.accumulate = subtract ? -1 : 1;
       }
       AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
+      SlotStreams ss(pl, st);
+      if ((s = ss.fork()) != AWG_OK) return s;
       for (int i = cf->slots.n - 1; i >= 0; --i) {
-        s = degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, 1, ae, sms, st);
+        s = degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, 1, ae, sms, ss.next());
         if (s != AWG_OK) return s;
       }
+      if ((s = ss.join()) != AWG_OK) return s;
       if (pl->rank > 1) {
         k_sum_terms<<<sms * 8, 256, 0, st>>>(pl->d_part, (float2*)vis_out, pl->n, pl->rank, 1, 4, cf->elem_p[e],
                                              subtract ? -1 : 1);
@@ -586,11 +653,15 @@ awg_status launch_degrid(CfSetImpl* cf, PlanImpl* pl, const void* grid, void* vi
     }
     AWG_CUDA_TRY(cudaMemsetAsync(pl->d_queue, 0, sizeof(int32_t) * kMaxSupport, st));
     if (cf->separable) {
+      SlotStreams ss(pl, st);
+      if ((s = ss.fork()) != AWG_OK) return s;
       for (int i = cf->slots.n - 1; i >= 0; --i) {
-        s = cf->fused ? degrid_slot_fused(cf->slots.S[i], cf->fused, cf->cand[cf->slots.S[i]], i, P, ak, sms, st)
-                      : degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, st);
+        const cudaStream_t si = ss.next();
+        s = cf->fused ? degrid_slot_fused(cf->slots.S[i], cf->fused, cf->cand[cf->slots.S[i]], i, P, ak, sms, si)
+                      : degrid_slot_sep(cf->slots.S[i], cf->cand[cf->slots.S[i]], i, P, ak, sms, si);
         if (s != AWG_OK) return s;
       }
+      if ((s = ss.join()) != AWG_OK) return s;
     } else {
       for (int c = kNumClasses - 1; c >= 0; --c) {
         if (!class_present(cf, c)) continue;
