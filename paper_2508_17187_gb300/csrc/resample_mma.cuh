@@ -212,6 +212,18 @@ struct MmaNLayout {
   static constexpr size_t alloc = (bytes + 1024 > 116 * 1024 ? bytes + 1024 : 116 * 1024);
 };
 
+// The builders' A and B tasks of one chunk form one list, A tasks first, dealt to the NBT builder
+// threads in turn: thread t takes list entries t, t + NBT, ...  Its first B task is then the first
+// such entry at or past the TA A tasks, less TA, so the threads left with one A task fewer take the
+// next B tasks and no thread holds two more tasks than another.  TA and NBT are multiples of 32,
+// so every warp still takes 32 consecutive tasks of each kind.
+template <int TA, int NBT>
+__device__ __forceinline__ int b_first(int t) {
+  static_assert(TA % 32 == 0 && NBT % 32 == 0, "whole warps of tasks");
+  constexpr int R = TA % NBT;
+  return t >= R ? t - R : t + NBT - R;
+}
+
 // Adds one complex value pair to the grid: 16 bytes at `g` (pols p, p + 1 of a pixel, P >= 2) in the
 // flush mode of grid_visibilities (0 plain, 1 compensated with the error into glo, 2 FP64 grid).
 __device__ __forceinline__ void mma_flush4(float* grid, float* grid_lo, size_t e, int mode, float4 v) {
@@ -620,7 +632,7 @@ __global__ void __launch_bounds__(MmaGridLayout<S, P, TILE, J, ST, D, NOB>::NT, 
               *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(l0, l1, l2, l3);
             }
           }
-          for (int task = bt; task < UN * KQ; task += NBT) {
+          for (int task = b_first<L::UX * P * KQ, NBT>(bt); task < UN * KQ; task += NBT) {
             const int yl = task & 7;
             const int kq = (task >> 3) % KQ;
             const int y = (task / (8 * KQ)) * 8 + yl;
@@ -908,7 +920,7 @@ __global__ void __launch_bounds__(MmaNLayout<S, P, TILE, J, ST, D, NOB>::NT, 1)
             *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
           }
 #pragma unroll 4
-          for (int task = bt; task < N * KQ; task += NBT) {
+          for (int task = b_first<AR * KQ, NBT>(bt); task < N * KQ; task += NBT) {
             const int kq = (task >> 3) % KQ;
             const int nn = (task / (8 * KQ)) * 8 + (task & 7);
             const int y = nn / P, p = nn % P;

@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(MmaDgLayout<S, P, TILE, KY, D, NZ, NOB>::NT, 1
           *reinterpret_cast<float4*>(obuf + L::ob_alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
 #pragma unroll 4
-        for (int task = bt; task < N * KQ; task += NBT) {
+        for (int task = b_first<128 * KQ, NBT>(bt); task < N * KQ; task += NBT) {
           const int kq = (task >> 3) % KQ;
           const int nn = (task / (8 * KQ)) * 8 + (task & 7);
           const int x = nn / P, p = nn % P;
