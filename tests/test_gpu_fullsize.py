@@ -1,9 +1,10 @@
-"""Full-size parity on the headline W-projection workload, in the launch configuration the bench
-times (351 baselines x 2000 integrations x 64 channels x 4 pols, 4096^2 grid, 64 w-planes, OS 20,
-separable CF storage).  The oracle cannot grid 180M visibilities in seconds, so it checks what it
-can compute on its own: every sample's keep/drop decision and tap count (bit exact), a band of 16
-grid rows through the dense centre of the uv plane (all samples that touch it), and the degridded
-values of 20,000 random samples against the oracle's D of the same GPU grid."""
+"""Full-size parity on the headline W-projection workload (351 baselines x 2000 integrations x 64
+channels x 4 pols, 4096^2 grid, 64 w-planes, OS 20, separable CF storage), with the default kernel
+configuration and with the configurations the autotuner picks, which are the ones the bench
+times.  The oracle cannot grid 180M visibilities in seconds, so it checks what it can compute on
+its own: every sample's keep/drop decision and tap count (bit exact), a band of 16 grid rows
+through the dense centre of the uv plane (all samples that touch it), and the degridded values of
+20,000 random samples against the oracle's D of the same GPU grid."""
 import numpy as np
 import pytest
 
@@ -17,7 +18,8 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-def test_wproj_full_size_sampled_parity():
+@pytest.mark.parametrize("tuned", [False, True], ids=["default", "autotuned"])
+def test_wproj_full_size_sampled_parity(tuned):
     import paper_2508_17187_gb300 as awg
     from paper_2508_17187_gb300 import _lib
     _lib.load()
@@ -28,6 +30,9 @@ def test_wproj_full_size_sampled_parity():
     assert cf.separable
     uvw = torch.as_tensor(wl.uvw_m).cuda()
     freq = torch.as_tensor(wl.freq_hz).cuda()
+    if tuned:
+        picks, _ = cf.autotune(uvw, freq, n_pol=P)
+        assert 3 in set(picks.values())   # the tensor-core configuration is among those tested
     plan = awg.plan_create(cf, uvw, freq)
     grid = torch.zeros((N, N, P), dtype=torch.complex64, device="cuda")
     sumwt = torch.zeros(P, dtype=torch.float64, device="cuda")
